@@ -1,0 +1,178 @@
+/*
+ * dg.h -- C ABI of the GB300 nodal interior-penalty DG solver for the 2D
+ * compressible Navier-Stokes equations on triangles (arXiv 2508.17917).
+ *
+ * The library evaluates the semi-discrete right-hand side of the paper's
+ * discretisation (Sec. 2.2, Eq. dg_on_K) fused with the five-stage 2N-storage
+ * Runge-Kutta update (Sec. 2.3, Algorithm 1) in hand-written CUDA kernels
+ * for sm_103a, plus the wall force integral, the CFL time step and the
+ * rigid-body Newmark step of the coupled loop (Sec. 2.4, Algorithm 3).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - State layout (API and device): U[k][c][i], k = element, c = conserved
+ *   field (rho, rho v1, rho v2, eps) with eps the total energy per volume
+ *   (Sec. 2.1), i = element-local node; FP64, contiguous, K*4*Np doubles.
+ * - Node numbering: the warp-and-blend nodes of degree p on the reference
+ *   triangle {(-1,-1), (1,-1), (-1,1)}; node (n, m) has barycentric weight
+ *   n/p on vertex (-1,1) and m/p on vertex (1,-1) before warping, numbered
+ *   with n outer (row s = -1 first) and m inner (increasing r).
+ *   Np = (p+1)(p+2)/2, 1 <= p <= 6.
+ * - Mesh: EToV[k] lists the vertices of element k counter-clockwise; face f
+ *   joins EToV[k][f] and EToV[k][(f+1)%3].  EToE/EToF give the neighbour
+ *   element and its face; a boundary face names itself.  bc[k][f]: 0 interior
+ *   or periodic, 1 moving adiabatic no-slip wall, 2 far field (Sec. 2.2,
+ *   boundary term).  Periodic meshes repeat vertices on the wrapped edges so
+ *   that each element is an ordinary affine triangle.
+ * - Ownership: input arrays are copied before the call returns; the caller
+ *   keeps device pointers passed with on_device = 1 alive until the work
+ *   queued on the context's stream has finished.  The library owns all the
+ *   device memory it allocates and frees it in dg_destroy.
+ * - Streams: every device operation of a context is queued on the stream
+ *   given to dg_create (a cudaStream_t, or NULL for the legacy default
+ *   stream).  Calls that return host values (dg_get_state with host output,
+ *   dg_compute_dt, dg_wall_forces, dg_check_finite) synchronise that stream.
+ * - Errors: every call returns a dg_status; on failure the context keeps a
+ *   message readable with dg_last_error.  No exception crosses the ABI.
+ *   There is no CPU fallback: without a usable GB300 the device calls
+ *   return DG_ECUDA.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_ctx dg_ctx;
+
+typedef enum {
+    DG_OK = 0,
+    DG_EINVAL = -1,        /* bad argument: null pointer, size out of range   */
+    DG_EMESH = -2,         /* mesh rejected: orientation, J <= 0, reciprocity */
+    DG_ECUDA = -3,         /* CUDA runtime error (message has the details)    */
+    DG_ENONFINITE = -4,    /* non-finite value found where finite is needed   */
+    DG_ETIMEOUT = -5,      /* a bounded device wait gave up                   */
+    DG_EUNSUPPORTED = -6   /* valid request the library does not implement    */
+} dg_status;
+
+enum { DG_PRECISION_FP64 = 0, DG_PRECISION_MIXED = 1 };
+enum { DG_BC_INTERIOR = 0, DG_BC_WALL = 1, DG_BC_FARFIELD = 2 };
+enum { DG_SOURCE_NONE = 0, DG_SOURCE_MANUFACTURED = 1 };
+
+typedef struct {
+    int p;                       /* polynomial degree, 1..6 (Sec. 2.2)                   */
+    int precision;               /* DG_PRECISION_FP64 or DG_PRECISION_MIXED              */
+    double gamma, Pr, mu;        /* adiabatic index, Prandtl number, viscosity (Sec. 2.1) */
+    double theta;                /* IP variant (Eq. ip_flux); only 0 (IIP) is supported  */
+    double C1;                   /* penalty constant of Eq. penalty_final                */
+    double rho_inf, u_inf, v_inf, p_inf;   /* far-field state (Sec. 2.2, boundary term) */
+    int adiabatic_zero_heatflux; /* 1: wall energy flux keeps only v_w.(tau n)           */
+} dg_params;
+
+/* Create a context on the current CUDA device.  `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream).  Builds the reference
+ * operators of degree params->p (Sec. 2.2, weak matrices) and uploads them.
+ * Errors: DG_EINVAL (null, p out of range, gamma <= 1, mu < 0, ...),
+ * DG_EUNSUPPORTED (theta != 0), DG_ECUDA.  *out is NULL on failure. */
+dg_status dg_create(const dg_params *params, void *cuda_stream, dg_ctx **out);
+
+/* Free the context and all its device memory.  NULL is accepted. */
+dg_status dg_destroy(dg_ctx *ctx);
+
+/* Upload a mesh (host arrays; Sec. 2.2 affine maps T_K, connectivity E^e).
+ * vx, vy: Nv vertex coordinates.  EToV, EToE, EToF, bc: K*3 int32, layout as
+ * above.  Computes the per-element metric (rx, ry, sx, sy, J), face normals
+ * and face Jacobians, matches the face nodes of every interior face with the
+ * reversed node order of its neighbour and checks that the matched nodes
+ * differ by one constant translation (zero, or a period).  Allocates the
+ * state buffers and sets the state to zero.
+ * Errors: DG_EINVAL (null, K < 1, Nv < 3), DG_EMESH (index out of range,
+ * clockwise or degenerate element, faces not reciprocal, face nodes that do
+ * not match), DG_ECUDA. */
+dg_status dg_set_mesh(dg_ctx *ctx, int64_t Nv, const double *vx, const double *vy,
+                      int64_t K, const int32_t *EToV, const int32_t *EToE,
+                      const int32_t *EToF, const int32_t *bc);
+
+/* Copy the state in ([K][4][Np] FP64; host pointer if on_device == 0, device
+ * pointer otherwise) and clear the Runge-Kutta register.
+ * Errors: DG_EINVAL (null, no mesh yet), DG_ECUDA. */
+dg_status dg_set_state(dg_ctx *ctx, const double *U, int on_device);
+
+/* Copy the state out ([K][4][Np] FP64).  Host output synchronises the stream.
+ * Errors: DG_EINVAL, DG_ECUDA. */
+dg_status dg_get_state(dg_ctx *ctx, double *U, int on_device);
+
+/* dU/dt = M^-1 R(t, U) of Eq. dg_on_K for the current state, with mesh
+ * velocity vw (Sec. 2.1 term v_w (x) U), written to dUdt ([K][4][Np] FP64,
+ * host or device).  Uses the context's precision.
+ * Errors: DG_EINVAL, DG_ECUDA. */
+dg_status dg_rhs(dg_ctx *ctx, double t, const double vw[2], double *dUdt, int on_device);
+
+/* One time step of Algorithm 1 (five stages, Carpenter-Kennedy 2N-storage
+ * coefficients) from t to t + dt with mesh velocity vw held fixed (Algorithm
+ * 3).  Asynchronous: queued on the context's stream.
+ * Errors: DG_EINVAL (no mesh, dt not finite), DG_ECUDA. */
+dg_status dg_lsrk_step(dg_ctx *ctx, double t, double dt, const double vw[2]);
+
+/* Several steps of dg_lsrk_step with a fixed dt, queued back to back. */
+dg_status dg_lsrk_steps(dg_ctx *ctx, double t, double dt, const double vw[2], int nsteps);
+
+/* dt = cfl / max_K Lambda_K with Lambda_K of Eq. rayleigh_bound (Appendix A)
+ * evaluated in FP64 for the current state and mesh velocity vw.  Readings:
+ * C_inv,2 = p^4 / rho_K^2 with rho_K the inradius, G_K the largest Gbar_e over
+ * the faces of K, sigma_K and C_inv,K the largest over its faces, beta_K the
+ * largest |b_ns|_2 over its nodes (Eq. cfl_general), beta'_K = 0.
+ * Synchronises the stream.  Errors: DG_EINVAL, DG_ENONFINITE, DG_ECUDA. */
+dg_status dg_compute_dt(dg_ctx *ctx, double cfl, const double vw[2], double *dt);
+
+/* Force and moment of the fluid on all wall faces (bc == 1): traction
+ * p n - tau n integrated with the face mass matrix, n the element's outward
+ * normal; moment about xc.  out = (Fx, Fy, Mz) in FP64 (Sec. 2.4, Eq.
+ * lift_drag).  Synchronises the stream.  Errors: DG_EINVAL, DG_ECUDA. */
+dg_status dg_wall_forces(dg_ctx *ctx, const double xc[2], double out[3]);
+
+/* One Newmark step (beta = 1/4, gamma = 1/2) of M y'' + C y' + K y = F
+ * (Eq. 1dof_oscillator), host only, no context needed.  coeff = (M, C, K);
+ * state = (y, y', y'') in/out; *v_b = (y_new - y_old)/dt, the mesh velocity
+ * of Algorithm 3.  Errors: DG_EINVAL (null, dt <= 0, singular system). */
+dg_status dg_rigid_step(const double coeff[3], double F, double dt, double state[3],
+                        double *v_b);
+
+/* *ok = 1 if every entry of the state is finite, else 0.  Synchronises.
+ * Errors: DG_EINVAL, DG_ECUDA. */
+dg_status dg_check_finite(dg_ctx *ctx, int *ok);
+
+/* Add a nodal source to every residual evaluation (Sec. 3.1).  kind
+ * DG_SOURCE_MANUFACTURED takes params = (kappa, C2) and adds the source of
+ * the manufactured steady solution U = (w, w, w, w^2), w = sin(kappa(x+y)) + C2,
+ * evaluated at the nodes; DG_SOURCE_NONE removes it.
+ * Errors: DG_EINVAL (no mesh, unknown kind, null params). */
+dg_status dg_set_source(dg_ctx *ctx, int kind, const double *params);
+
+/* Node coordinates of the current mesh, x and y each [K][Np] FP64 host
+ * arrays (affine map T_K of Sec. 2.2).  Errors: DG_EINVAL. */
+dg_status dg_node_coords(const dg_ctx *ctx, double *x, double *y);
+
+/* Reference operators of degree p built by the library (host only, no GPU
+ * needed): nodes r, s [Np]; Dr, Ds [Np][Np] row-major; LIFT [Np][3*(p+1)]
+ * with face-node columns in counter-clockwise order; Fmask [3][p+1] the
+ * volume index of each face node, counter-clockwise along each face.  Any
+ * output may be NULL.  Errors: DG_EINVAL (p out of range). */
+dg_status dg_reference_operators(int p, double *r, double *s, double *Dr, double *Ds,
+                                 double *LIFT, int32_t *Fmask);
+
+/* Number of the library's kernels launched by this context so far. */
+int64_t dg_kernel_launches(const dg_ctx *ctx);
+
+/* Message of the last failing call on ctx (empty string if none).  The
+ * pointer stays valid until the next call on ctx. */
+const char *dg_last_error(const dg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_H */

@@ -1,0 +1,283 @@
+"""ctypes binding of libdg.so: same names as include/dg.h, marshalling only.
+
+Host arrays are numpy float64/int32 arrays; device arrays are torch CUDA
+tensors (their data pointer is passed with on_device = 1).  Streams are
+passed as the integer handle of a torch.cuda.Stream (``stream.cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+__all__ = ["DG_OK", "DG_PRECISION_FP64", "DG_PRECISION_MIXED", "DG_SOURCE_NONE",
+           "DG_SOURCE_MANUFACTURED", "DgParams", "DGError", "lib", "library_path",
+           "dg_create", "dg_destroy", "dg_set_mesh", "dg_set_state", "dg_get_state", "dg_rhs",
+           "dg_lsrk_step", "dg_lsrk_steps", "dg_compute_dt", "dg_wall_forces", "dg_rigid_step",
+           "dg_check_finite", "dg_set_source", "dg_node_coords", "dg_reference_operators",
+           "dg_kernel_launches", "dg_last_error", "Solver", "EXPORTED"]
+
+DG_OK = 0
+DG_PRECISION_FP64, DG_PRECISION_MIXED = 0, 1
+DG_SOURCE_NONE, DG_SOURCE_MANUFACTURED = 0, 1
+STATUS = {0: "DG_OK", -1: "DG_EINVAL", -2: "DG_EMESH", -3: "DG_ECUDA", -4: "DG_ENONFINITE",
+          -5: "DG_ETIMEOUT", -6: "DG_EUNSUPPORTED"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "libdg.so")
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+
+
+class DgParams(C.Structure):
+    _fields_ = [("p", C.c_int), ("precision", C.c_int), ("gamma", C.c_double), ("Pr", C.c_double),
+                ("mu", C.c_double), ("theta", C.c_double), ("C1", C.c_double),
+                ("rho_inf", C.c_double), ("u_inf", C.c_double), ("v_inf", C.c_double),
+                ("p_inf", C.c_double), ("adiabatic_zero_heatflux", C.c_int)]
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+
+
+# name -> (restype, argtypes)
+EXPORTED = {
+    "dg_create": (C.c_int, [C.POINTER(DgParams), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "dg_destroy": (C.c_int, [C.c_void_p]),
+    "dg_set_mesh": (C.c_int, [C.c_void_p, C.c_int64, _dp, _dp, C.c_int64, _ip, _ip, _ip, _ip]),
+    "dg_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "dg_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "dg_rhs": (C.c_int, [C.c_void_p, C.c_double, _dp, C.c_void_p, C.c_int]),
+    "dg_lsrk_step": (C.c_int, [C.c_void_p, C.c_double, C.c_double, _dp]),
+    "dg_lsrk_steps": (C.c_int, [C.c_void_p, C.c_double, C.c_double, _dp, C.c_int]),
+    "dg_compute_dt": (C.c_int, [C.c_void_p, C.c_double, _dp, _dp]),
+    "dg_wall_forces": (C.c_int, [C.c_void_p, _dp, _dp]),
+    "dg_rigid_step": (C.c_int, [_dp, C.c_double, C.c_double, _dp, _dp]),
+    "dg_check_finite": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "dg_set_source": (C.c_int, [C.c_void_p, C.c_int, _dp]),
+    "dg_node_coords": (C.c_int, [C.c_void_p, _dp, _dp]),
+    "dg_reference_operators": (C.c_int, [C.c_int, _dp, _dp, _dp, _dp, _dp, _ip]),
+    "dg_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "dg_last_error": (C.c_char_p, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libdg.so; raises ImportError if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(library_path):
+            raise ImportError(f"libdg.so not built ({library_path}); run "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(library_path)
+        for name, (res, args) in EXPORTED.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _arr_ptr(x):
+    """(pointer, on_device) of a numpy array or torch tensor of float64."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be contiguous float64")
+        return x.ctypes.data_as(C.c_void_p), 0
+    if hasattr(x, "data_ptr"):
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise ValueError("device tensors must be contiguous float64")
+        return C.c_void_p(x.data_ptr()), 1 if x.is_cuda else 0
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _check(st, ctx=None):
+    if st != DG_OK:
+        msg = lib().dg_last_error(ctx).decode() if ctx else ""
+        raise DGError(st, msg)
+
+
+def _vw(vw):
+    return _f64(vw if vw is not None else (0.0, 0.0))
+
+
+# ---- one Python function per C entry point --------------------------------
+
+def dg_create(params: DgParams, stream=0):
+    out = C.c_void_p()
+    _check(lib().dg_create(C.byref(params), C.c_void_p(int(stream or 0)), C.byref(out)))
+    return out
+
+
+def dg_destroy(ctx):
+    return lib().dg_destroy(ctx)
+
+
+def dg_set_mesh(ctx, vx, vy, EToV, EToE, EToF, bc):
+    vx, vy = _f64(vx), _f64(vy)
+    EToV, EToE, EToF, bc = _i32(EToV), _i32(EToE), _i32(EToF), _i32(bc)
+    _check(lib().dg_set_mesh(ctx, vx.size, _dptr(vx), _dptr(vy), EToV.shape[0],
+                             EToV.ctypes.data_as(_ip), EToE.ctypes.data_as(_ip),
+                             EToF.ctypes.data_as(_ip), bc.ctypes.data_as(_ip)), ctx)
+
+
+def dg_set_state(ctx, U):
+    ptr, dev = _arr_ptr(U)
+    _check(lib().dg_set_state(ctx, ptr, dev), ctx)
+
+
+def dg_get_state(ctx, U):
+    ptr, dev = _arr_ptr(U)
+    _check(lib().dg_get_state(ctx, ptr, dev), ctx)
+
+
+def dg_rhs(ctx, t, vw, out):
+    ptr, dev = _arr_ptr(out)
+    _check(lib().dg_rhs(ctx, float(t), _dptr(_vw(vw)), ptr, dev), ctx)
+
+
+def dg_lsrk_step(ctx, t, dt, vw=None):
+    _check(lib().dg_lsrk_step(ctx, float(t), float(dt), _dptr(_vw(vw))), ctx)
+
+
+def dg_lsrk_steps(ctx, t, dt, vw, nsteps):
+    _check(lib().dg_lsrk_steps(ctx, float(t), float(dt), _dptr(_vw(vw)), int(nsteps)), ctx)
+
+
+def dg_compute_dt(ctx, cfl, vw=None):
+    out = np.zeros(1)
+    _check(lib().dg_compute_dt(ctx, float(cfl), _dptr(_vw(vw)), _dptr(out)), ctx)
+    return float(out[0])
+
+
+def dg_wall_forces(ctx, xc=(0.0, 0.0)):
+    out = np.zeros(3)
+    _check(lib().dg_wall_forces(ctx, _dptr(_f64(xc)), _dptr(out)), ctx)
+    return out
+
+
+def dg_rigid_step(coeff, F, dt, state):
+    """Returns (new_state, v_b); `state` is not modified."""
+    st = _f64(state).copy()
+    vb = np.zeros(1)
+    _check(lib().dg_rigid_step(_dptr(_f64(coeff)), float(F), float(dt), _dptr(st), _dptr(vb)))
+    return st, float(vb[0])
+
+
+def dg_check_finite(ctx):
+    ok = C.c_int(0)
+    _check(lib().dg_check_finite(ctx, C.byref(ok)), ctx)
+    return bool(ok.value)
+
+
+def dg_set_source(ctx, kind, params=None):
+    pa = _f64(params if params is not None else (0.0, 0.0))
+    _check(lib().dg_set_source(ctx, int(kind), _dptr(pa)), ctx)
+
+
+def dg_node_coords(ctx, K, Np):
+    x = np.zeros((K, Np))
+    y = np.zeros((K, Np))
+    _check(lib().dg_node_coords(ctx, _dptr(x), _dptr(y)), ctx)
+    return x, y
+
+
+def dg_reference_operators(p):
+    Np, Nfp = (p + 1) * (p + 2) // 2, p + 1
+    r, s = np.zeros(Np), np.zeros(Np)
+    Dr, Ds = np.zeros((Np, Np)), np.zeros((Np, Np))
+    LIFT = np.zeros((Np, 3 * Nfp))
+    Fmask = np.zeros((3, Nfp), dtype=np.int32)
+    _check(lib().dg_reference_operators(int(p), _dptr(r), _dptr(s), _dptr(Dr), _dptr(Ds), _dptr(LIFT),
+                                        Fmask.ctypes.data_as(_ip)))
+    return dict(r=r, s=s, Dr=Dr, Ds=Ds, LIFT=LIFT, Fmask=Fmask)
+
+
+def dg_kernel_launches(ctx):
+    return int(lib().dg_kernel_launches(ctx))
+
+
+def dg_last_error(ctx):
+    return lib().dg_last_error(ctx).decode()
+
+
+class Solver:
+    """A context with a mesh: the C calls as methods (no extra logic)."""
+
+    def __init__(self, mesh, p, precision="fp64", stream=0, gamma=1.4, Pr=0.72, mu=1e-3,
+                 C1=0.01, rho_inf=1.0, u_inf=1.0, v_inf=0.0, p_inf=1.0,
+                 adiabatic_zero_heatflux=1):
+        prec = {"fp64": DG_PRECISION_FP64, "mixed": DG_PRECISION_MIXED}[precision]
+        self.params = DgParams(p, prec, gamma, Pr, mu, 0.0, C1, rho_inf, u_inf, v_inf, p_inf,
+                               int(adiabatic_zero_heatflux))
+        self.p, self.K = p, mesh.K
+        self.Np = (p + 1) * (p + 2) // 2
+        self.ctx = dg_create(self.params, stream)
+        dg_set_mesh(self.ctx, mesh.vx, mesh.vy, mesh.EToV, mesh.EToE, mesh.EToF, mesh.bc)
+
+    def __del__(self):
+        ctx = getattr(self, "ctx", None)
+        if ctx is not None and _lib is not None:
+            dg_destroy(ctx)
+            self.ctx = None
+
+    @property
+    def shape(self):
+        return (self.K, 4, self.Np)
+
+    def node_coords(self):
+        return dg_node_coords(self.ctx, self.K, self.Np)
+
+    def set_state(self, U):
+        dg_set_state(self.ctx, U if not isinstance(U, np.ndarray) else _f64(U))
+
+    def get_state(self, out=None):
+        out = np.zeros(self.shape) if out is None else out
+        dg_get_state(self.ctx, out)
+        return out
+
+    def rhs(self, t=0.0, vw=None, out=None):
+        out = np.zeros(self.shape) if out is None else out
+        dg_rhs(self.ctx, t, vw, out)
+        return out
+
+    def step(self, t, dt, vw=None):
+        dg_lsrk_step(self.ctx, t, dt, vw)
+
+    def steps(self, t, dt, nsteps, vw=None):
+        dg_lsrk_steps(self.ctx, t, dt, vw, nsteps)
+
+    def dt(self, cfl, vw=None):
+        return dg_compute_dt(self.ctx, cfl, vw)
+
+    def wall_forces(self, xc=(0.0, 0.0)):
+        return dg_wall_forces(self.ctx, xc)
+
+    def check_finite(self):
+        return dg_check_finite(self.ctx)
+
+    def set_source(self, kind, params=None):
+        dg_set_source(self.ctx, kind, params)
+
+    @property
+    def launches(self):
+        return dg_kernel_launches(self.ctx)

@@ -1,0 +1,225 @@
+// aux_kernels.cu -- time step, wall forces and finiteness kernels (FP64).
+#include <math.h>
+
+#include "dg_stage.cuh"
+#include "launch.h"
+
+namespace dg {
+namespace {
+
+__device__ __forceinline__ void load_node(const double *U, int Np, long long k, int i, double u[4])
+{
+#pragma unroll
+    for (int c = 0; c < 4; ++c) u[c] = U[(k * 4 + c) * Np + i];
+}
+
+// One thread per element: Lambda_K of Eq. rayleigh_bound,
+//   Lambda_K = 3/2 C_inv,2(K) G_K + (d+1) C_inv,K (3 sigma_K + beta_K) + beta'_K,
+// with C_inv,2 = p^4 / rho_K^2 (rho_K the inradius 2|K| / perimeter), G_K the
+// largest Gbar_e over the faces of K, sigma_K, C_inv,K the largest over its
+// faces, beta_K = max over nodes of |b_ns|_2, (b_ns)_j = |v_j - v_w,j| + c
+// (Eq. cfl_general), beta'_K = 0.
+__global__ void dt_lambda_kernel(AuxMesh m, Phys<double> ph, double C1, double *lam)
+{
+    long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (k >= m.K) return;
+    const int p = m.p, Np = (p + 1) * (p + 2) / 2, Nfp = p + 1;
+    const double *g = m.geo + k * 16;
+    const int4 cn = m.conn[k];
+    double GK = 0, sigK = 0, ciK = 0, perim = 0;
+    const double pp = (p + 1.0) * (p + 2.0);
+    for (int f = 0; f < 3; ++f) {
+        long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
+        int f2 = (cn.w >> (2 * f)) & 3;
+        int bt = (cn.w >> (8 + 2 * f)) & 3;
+        double n1 = g[G_NX + f], n2 = g[G_NY + f], fs = g[G_FS + f];
+        double gbar = 0;
+        for (int i = 0; i < Nfp; ++i) {
+            int vm = m.fmask[f * Nfp + i];
+            double u[4];
+            load_node(m.U, Np, k, vm, u);
+            double a = penalty_norm(u[0], u[1] / u[0], u[2] / u[0], u[3] / u[0], n1, n2, ph);
+            double b;
+            if (bt == BCT_INTERIOR) {
+                double w[4];
+                load_node(m.U, Np, nb, m.fmask[f2 * Nfp + (Nfp - 1 - i)], w);
+                b = penalty_norm(w[0], w[1] / w[0], w[2] / w[0], w[3] / w[0], n1, n2, ph);
+            } else if (bt == BCT_FARFIELD) {
+                const double *w = ph.Uinf;
+                b = penalty_norm(w[0], w[1] / w[0], w[2] / w[0], w[3] / w[0], n1, n2, ph);
+            } else {
+                double pw = pressure<double>(u, u[3], ph.gm1);
+                double eb = (pw / ph.gm1 + 0.5 * u[0] * (ph.vw1 * ph.vw1 + ph.vw2 * ph.vw2)) / u[0];
+                b = penalty_norm(u[0], ph.vw1, ph.vw2, eb, n1, n2, ph);
+            }
+            gbar = fmax(gbar, fmax(a, b));
+        }
+        double ci = pp * fs * 0.5;
+        double cmax = ci;
+        if (bt == BCT_INTERIOR) cmax = fmax(ci, pp * m.geo[nb * 16 + G_FS + f2] * 0.5);
+        double sig = 3.0 * C1 * gbar * cmax;
+        GK = fmax(GK, gbar);
+        sigK = fmax(sigK, sig);
+        ciK = fmax(ciK, ci);
+        perim += 2.0 * fs * g[G_J];     // |e| = 2 sJ = 2 Fscale J
+    }
+    double area = 2.0 * g[G_J];
+    double rhoK = 2.0 * area / perim;
+    double cinv2 = double(p) * p * p * p / (rhoK * rhoK);
+    double beta = 0;
+    for (int i = 0; i < Np; ++i) {
+        double u[4];
+        load_node(m.U, Np, k, i, u);
+        double pr = pressure<double>(u, u[3], ph.gm1);
+        double c = sqrt(ph.gamma * pr / u[0]);
+        double b1 = fabs(u[1] / u[0] - ph.vw1) + c, b2 = fabs(u[2] / u[0] - ph.vw2) + c;
+        beta = fmax(beta, sqrt(b1 * b1 + b2 * b2));
+    }
+    lam[k] = 1.5 * cinv2 * GK + 3.0 * ciK * (3.0 * sigK + beta);
+}
+
+// Single-block maximum; non-finite entries propagate as NaN.
+__global__ void max_reduce_kernel(const double *x, long long n, double *out)
+{
+    __shared__ double s[1024];
+    double m = 0.0;
+    bool bad = false;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        double v = x[i];
+        if (!isfinite(v)) bad = true;
+        m = fmax(m, v);
+    }
+    s[threadIdx.x] = bad ? NAN : m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            double a = s[threadIdx.x], b = s[threadIdx.x + w];
+            s[threadIdx.x] = (isnan(a) || isnan(b)) ? NAN : fmax(a, b);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+// One thread per wall face: traction p n - tau n at the face nodes (interior
+// trace, n the element's outward normal), integrated with the LGL weights
+// scaled by sJ; moment about (xc, yc).
+__global__ void wall_force_kernel(AuxMesh m, Phys<double> ph, const int2 *faces, const double *face_xy,
+                                  const double *wface, int nwall, double xc, double yc, double *partial)
+{
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwall) return;
+    const int p = m.p, Np = (p + 1) * (p + 2) / 2, Nfp = p + 1;
+    const long long k = faces[w].x;
+    const int f = faces[w].y;
+    const double *g = m.geo + k * 16;
+    const double rx = g[G_RX], ry = g[G_RY], sx = g[G_SX], sy = g[G_SY];
+    const double n1 = g[G_NX + f], n2 = g[G_NY + f], sJ = g[G_FS + f] * g[G_J];
+    double F0 = 0, F1 = 0, Mz = 0;
+    for (int i = 0; i < Nfp; ++i) {
+        int vm = m.fmask[f * Nfp + i];
+        double ur[4] = {0, 0, 0, 0}, us[4] = {0, 0, 0, 0}, u[4];
+        for (int j = 0; j < Np; ++j) {
+            double dr = m.Dr[vm * Np + j], ds = m.Ds[vm * Np + j];
+            for (int c = 0; c < 4; ++c) {
+                double uj = m.U[(k * 4 + c) * Np + j];
+                ur[c] += dr * uj;
+                us[c] += ds * uj;
+            }
+        }
+        double gx[4], gy[4];
+        for (int c = 0; c < 4; ++c) {
+            gx[c] = rx * ur[c] + sx * us[c];
+            gy[c] = ry * ur[c] + sy * us[c];
+        }
+        load_node(m.U, Np, k, vm, u);
+        double vx[4], vy[4];
+        visc_flux(u, gx, gy, ph, vx, vy);
+        double pr = pressure<double>(u, u[3], ph.gm1);
+        double tx = pr * n1 - (vx[1] * n1 + vy[1] * n2);
+        double ty = pr * n2 - (vx[2] * n1 + vy[2] * n2);
+        double x = face_xy[(static_cast<long long>(w) * Nfp + i) * 2] - xc;
+        double y = face_xy[(static_cast<long long>(w) * Nfp + i) * 2 + 1] - yc;
+        double wq = sJ * wface[i];
+        F0 += wq * tx;
+        F1 += wq * ty;
+        Mz += wq * (x * ty - y * tx);
+    }
+    partial[w * 3 + 0] = F0;
+    partial[w * 3 + 1] = F1;
+    partial[w * 3 + 2] = Mz;
+}
+
+// Deterministic single-block sum of n triples.
+__global__ void sum3_kernel(const double *partial, int n, double *out)
+{
+    __shared__ double s[3][256];
+    double a[3] = {0, 0, 0};
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        for (int c = 0; c < 3; ++c) a[c] += partial[i * 3 + c];
+    for (int c = 0; c < 3; ++c) s[c][threadIdx.x] = a[c];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < 3; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) out[c] = s[c][0];
+}
+
+__global__ void nonfinite_kernel(const double *x, long long n, int *flag)
+{
+    long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+    bool bad = false;
+    for (; i < n; i += stride) bad |= !isfinite(x[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) *flag = 1;
+}
+
+}  // namespace
+
+cudaError_t launch_dt_lambda(const AuxMesh &m, const Phys<double> &ph, double C1, double *lam,
+                             cudaStream_t st)
+{
+    int threads = 128;
+    long long blocks = (m.K + threads - 1) / threads;
+    dt_lambda_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(m, ph, C1, lam);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_max_reduce(const double *lam, long long K, double *out, cudaStream_t st)
+{
+    max_reduce_kernel<<<1, 1024, 0, st>>>(lam, K, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wall_force_faces(const AuxMesh &m, const Phys<double> &ph, const int2 *faces,
+                                    const double *face_xy, const double *wface, int nwall,
+                                    double xc, double yc, double *partial, cudaStream_t st)
+{
+    int threads = 128;
+    int blocks = (nwall + threads - 1) / threads;
+    wall_force_kernel<<<blocks, threads, 0, st>>>(m, ph, faces, face_xy, wface, nwall, xc, yc, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum3(const double *partial, int n, double *out, cudaStream_t st)
+{
+    sum3_kernel<<<1, 256, 0, st>>>(partial, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nonfinite(const double *x, long long n, int *flag, cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long want = (n + 255) / 256;
+    long long blocks = want < 4LL * sms ? want : 4LL * sms;
+    if (blocks < 1) blocks = 1;
+    nonfinite_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(x, n, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace dg

@@ -1,0 +1,587 @@
+// dg_api.cu -- implementation of the C ABI declared in include/dg.h.
+//
+// Host side of the library: parameter checks, mesh validation, the affine
+// geometry of every element (Sec. 2.2, maps T_K), face matching, device
+// buffers and the sequencing of the stage kernels into Algorithm 1.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dg.h"
+#include "dg_stage.cuh"
+#include "launch.h"
+#include "refops.h"
+
+namespace {
+
+// Carpenter & Kennedy (1994), five-stage fourth-order 2N-storage scheme:
+// the coefficients A_i, B_i, c_i of Algorithm 1.
+const double kRkA[5] = {0.0,
+                        -567301805773.0 / 1357537059087.0,
+                        -2404267990393.0 / 2016746695238.0,
+                        -3550918686646.0 / 2091501179385.0,
+                        -1275806237668.0 / 842570457699.0};
+const double kRkB[5] = {1432997174477.0 / 9575080441755.0,
+                        5161836677717.0 / 13612068292357.0,
+                        1720146321549.0 / 2090206949498.0,
+                        3134564353537.0 / 4481467310338.0,
+                        2277821191437.0 / 14882151754819.0};
+const double kRkC[5] = {0.0,
+                        1432997174477.0 / 9575080441755.0,
+                        2526269341429.0 / 6820363962896.0,
+                        2006345519317.0 / 3224310063776.0,
+                        2802321613138.0 / 2924317926251.0};
+
+template <typename T>
+struct DevBuf {
+    T *ptr = nullptr;
+    size_t n = 0;
+    cudaError_t alloc(size_t count)
+    {
+        release();
+        n = count;
+        if (count == 0) return cudaSuccess;
+        return cudaMalloc(reinterpret_cast<void **>(&ptr), count * sizeof(T));
+    }
+    void release()
+    {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        n = 0;
+    }
+};
+
+}  // namespace
+
+struct dg_ctx {
+    dg_params prm{};
+    cudaStream_t stream = nullptr;
+    dg::RefOps ops;
+    std::string err;
+    int64_t launches = 0;
+    // mesh (host copies kept for coordinates)
+    long long K = 0;
+    std::vector<double> vx, vy;
+    std::vector<int32_t> EToV;
+    std::vector<double> geo64h;
+    // device
+    DevBuf<double> K0a, K0b, K1, rtmp, geo64, ops64, Dr64, Ds64, src, lam, scal, fpart, fxy, wface;
+    DevBuf<float> geo32, ops32;
+    DevBuf<int4> conn;
+    DevBuf<int> fmask, flag;
+    DevBuf<int2> wall;
+    int nwall = 0;
+    bool cur_is_a = true;
+    dg::LaunchShape shape;
+    int source_kind = DG_SOURCE_NONE;
+
+    double *cur() { return cur_is_a ? K0a.ptr : K0b.ptr; }
+    double *other() { return cur_is_a ? K0b.ptr : K0a.ptr; }
+    ~dg_ctx()
+    {
+        for (auto *b : {&K0a, &K0b, &K1, &rtmp, &geo64, &ops64, &Dr64, &Ds64, &src, &lam, &scal, &fpart, &fxy, &wface})
+            b->release();
+        geo32.release();
+        ops32.release();
+        conn.release();
+        fmask.release();
+        flag.release();
+        wall.release();
+    }
+};
+
+namespace {
+
+dg_status fail(dg_ctx *c, dg_status st, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return st;
+}
+
+dg_status cuda_fail(dg_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, DG_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define DG_CUDA(ctx, expr)                                        \
+    do {                                                          \
+        cudaError_t e_ = (expr);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr);  \
+    } while (0)
+
+template <typename real>
+dg::Phys<real> make_phys(const dg_params &p, const double vw[2])
+{
+    dg::Phys<real> ph;
+    ph.gamma = real(p.gamma);
+    ph.gm1 = real(p.gamma - 1.0);
+    ph.mu = real(p.mu);
+    ph.gPr = real(p.gamma / p.Pr);
+    ph.vw1 = real(vw ? vw[0] : 0.0);
+    ph.vw2 = real(vw ? vw[1] : 0.0);
+    double E = p.p_inf / (p.gamma - 1.0) + 0.5 * p.rho_inf * (p.u_inf * p.u_inf + p.v_inf * p.v_inf);
+    ph.Uinf[0] = real(p.rho_inf);
+    ph.Uinf[1] = real(p.rho_inf * p.u_inf);
+    ph.Uinf[2] = real(p.rho_inf * p.v_inf);
+    ph.Uinf[3] = real(E);
+    ph.pinf = real(p.p_inf);
+    ph.adiabatic = p.adiabatic_zero_heatflux;
+    return ph;
+}
+
+size_t ndof(const dg_ctx *c) { return static_cast<size_t>(c->K) * 4 * c->ops.Np; }
+
+// Manufactured steady solution of Sec. 3.1: source S = div F_c - div F_v at
+// (x, y) for U = (w, w, w, w^2), w = sin(kappa (x+y)) + C2 (velocity (1,1),
+// p = (gamma-1)(w^2 - w), only the heat-flux row of F_v is non-zero).
+void manufactured_source(double x, double y, double kappa, double C2, const dg_params &p, double S[4])
+{
+    const double phi = kappa * (x + y), g1 = p.gamma - 1.0;
+    const double w = std::sin(phi) + C2, dw = kappa * std::cos(phi);
+    const double dp = g1 * (2.0 * w - 1.0) * dw;           // d/dx p = d/dy p
+    S[0] = 2.0 * dw;                                         // d(rho v1)/dx + d(rho v2)/dy
+    S[1] = 2.0 * dw + dp;                                    // d(w + p)/dx + d(w)/dy
+    S[2] = S[1];
+    const double dEp = dp + 2.0 * w * dw;                    // d(p + eps)/dx
+    const double heat = 2.0 * p.mu * p.gamma / p.Pr * kappa * kappa * std::sin(phi);
+    S[3] = 2.0 * dEp + heat;                                 // minus div of heat flux -mu g/Pr kappa^2 sin
+}
+
+dg_status run_stage(dg_ctx *c, int s, double t, double dt, const double vw[2], int mode,
+                    const double *in, double *out, double *rout)
+{
+    dg::StageParams sp{};
+    sp.K0in = in;
+    sp.K0out = out;
+    sp.K1 = c->K1.ptr;
+    sp.Rout = rout;
+    sp.conn = c->conn.ptr;
+    sp.fmask = c->fmask.ptr;
+    sp.src = (c->source_kind != DG_SOURCE_NONE) ? c->src.ptr : nullptr;
+    sp.K = c->K;
+    sp.A = (s >= 0) ? kRkA[s] : 0.0;
+    sp.B = (s >= 0) ? kRkB[s] : 0.0;
+    sp.dt = dt;
+    sp.gm1 = c->prm.gamma - 1.0;
+    sp.C1 = c->prm.C1;
+    sp.mode = mode;
+    sp.first_stage = (s == 0) ? 1 : 0;
+    (void)t;
+    cudaError_t e;
+    if (c->prm.precision == DG_PRECISION_FP64) {
+        sp.geo = c->geo64.ptr;
+        sp.ops = c->ops64.ptr;
+        e = dg::launch_stage_fp64(c->prm.p, c->shape, sp, make_phys<double>(c->prm, vw), c->stream);
+    } else {
+        sp.geo = c->geo32.ptr;
+        sp.ops = c->ops32.ptr;
+        e = dg::launch_stage_mixed(c->prm.p, c->shape, sp, make_phys<float>(c->prm, vw), c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
+    c->launches += 1;
+    return DG_OK;
+}
+
+dg::AuxMesh aux_mesh(dg_ctx *c)
+{
+    dg::AuxMesh m;
+    m.U = c->cur();
+    m.geo = c->geo64.ptr;
+    m.conn = c->conn.ptr;
+    m.Dr = c->Dr64.ptr;
+    m.Ds = c->Ds64.ptr;
+    m.fmask = c->fmask.ptr;
+    m.K = c->K;
+    m.p = c->prm.p;
+    return m;
+}
+
+}  // namespace
+
+extern "C" {
+
+dg_status dg_reference_operators(int p, double *r, double *s, double *Dr, double *Ds, double *LIFT,
+                                 int32_t *Fmask)
+{
+    dg::RefOps o;
+    if (!dg::build_reference_operators(p, o)) return DG_EINVAL;
+    if (r) std::copy(o.r.begin(), o.r.end(), r);
+    if (s) std::copy(o.s.begin(), o.s.end(), s);
+    if (Dr) std::copy(o.Dr.begin(), o.Dr.end(), Dr);
+    if (Ds) std::copy(o.Ds.begin(), o.Ds.end(), Ds);
+    if (LIFT) std::copy(o.LIFT.begin(), o.LIFT.end(), LIFT);
+    if (Fmask)
+        for (size_t i = 0; i < o.Fmask.size(); ++i) Fmask[i] = o.Fmask[i];
+    return DG_OK;
+}
+
+dg_status dg_create(const dg_params *params, void *cuda_stream, dg_ctx **out)
+{
+    if (!out) return DG_EINVAL;
+    *out = nullptr;
+    if (!params) return DG_EINVAL;
+    const dg_params &p = *params;
+    if (p.p < 1 || p.p > 6 || !(p.gamma > 1.0) || !(p.Pr > 0.0) || !(p.mu >= 0.0) || !(p.C1 >= 0.0) ||
+        !(p.rho_inf > 0.0) || !(p.p_inf > 0.0) ||
+        (p.precision != DG_PRECISION_FP64 && p.precision != DG_PRECISION_MIXED))
+        return DG_EINVAL;
+    if (p.theta != 0.0) return DG_EUNSUPPORTED;
+    dg_ctx *c = new dg_ctx();
+    c->prm = p;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (!dg::build_reference_operators(p.p, c->ops)) {
+        delete c;
+        return DG_EINVAL;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        delete c;
+        return DG_ECUDA;
+    }
+    const int Np = c->ops.Np, NF = 3 * c->ops.Nfp;
+    std::vector<double> o64;
+    o64.insert(o64.end(), c->ops.Dr.begin(), c->ops.Dr.end());
+    o64.insert(o64.end(), c->ops.Ds.begin(), c->ops.Ds.end());
+    o64.insert(o64.end(), c->ops.LIFT.begin(), c->ops.LIFT.end());
+    std::vector<float> o32(o64.begin(), o64.end());
+    if (c->ops64.alloc(o64.size()) != cudaSuccess || c->ops32.alloc(o32.size()) != cudaSuccess ||
+        c->Dr64.alloc(Np * Np) != cudaSuccess || c->Ds64.alloc(Np * Np) != cudaSuccess ||
+        c->fmask.alloc(NF) != cudaSuccess || c->flag.alloc(1) != cudaSuccess ||
+        c->scal.alloc(4) != cudaSuccess || c->wface.alloc(c->ops.Nfp) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return DG_ECUDA;
+    }
+    cudaMemcpy(c->ops64.ptr, o64.data(), o64.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->ops32.ptr, o32.data(), o32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->Dr64.ptr, c->ops.Dr.data(), Np * Np * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->Ds64.ptr, c->ops.Ds.data(), Np * Np * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->fmask.ptr, c->ops.Fmask.data(), NF * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->wface.ptr, c->ops.wface.data(), c->ops.Nfp * sizeof(double), cudaMemcpyHostToDevice);
+    if (cudaGetLastError() != cudaSuccess) {
+        delete c;
+        return DG_ECUDA;
+    }
+    *out = c;
+    return DG_OK;
+}
+
+dg_status dg_destroy(dg_ctx *ctx)
+{
+    delete ctx;
+    return DG_OK;
+}
+
+const char *dg_last_error(const dg_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t dg_kernel_launches(const dg_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+dg_status dg_set_mesh(dg_ctx *c, int64_t Nv, const double *vx, const double *vy, int64_t K,
+                      const int32_t *EToV, const int32_t *EToE, const int32_t *EToF, const int32_t *bc)
+{
+    if (!c) return DG_EINVAL;
+    c->err.clear();
+    if (!vx || !vy || !EToV || !EToE || !EToF || !bc) return fail(c, DG_EINVAL, "null mesh array");
+    if (K < 1 || Nv < 3) return fail(c, DG_EINVAL, "need K >= 1 and Nv >= 3");
+    const int Np = c->ops.Np, Nfp = c->ops.Nfp;
+    if (K * 4LL * Np > (1LL << 40)) return fail(c, DG_EINVAL, "mesh too large");
+    // --- index checks and geometry
+    std::vector<double> geo(static_cast<size_t>(K) * 16, 0.0);
+    double scale = 0.0;
+    for (int64_t i = 0; i < Nv; ++i) scale = std::max(scale, std::max(std::fabs(vx[i]), std::fabs(vy[i])));
+    if (!(scale > 0.0) || !std::isfinite(scale)) return fail(c, DG_EMESH, "vertex coordinates not finite");
+    for (int64_t k = 0; k < K; ++k) {
+        int32_t v[3] = {EToV[k * 3], EToV[k * 3 + 1], EToV[k * 3 + 2]};
+        for (int f = 0; f < 3; ++f) {
+            if (v[f] < 0 || v[f] >= Nv) return fail(c, DG_EMESH, "EToV index out of range at element " + std::to_string(k));
+            int32_t e2 = EToE[k * 3 + f], f2 = EToF[k * 3 + f], b = bc[k * 3 + f];
+            if (e2 < 0 || e2 >= K || f2 < 0 || f2 > 2 || b < 0 || b > 2)
+                return fail(c, DG_EMESH, "EToE/EToF/bc out of range at element " + std::to_string(k));
+        }
+        double x1 = vx[v[0]], y1 = vy[v[0]], x2 = vx[v[1]], y2 = vy[v[1]], x3 = vx[v[2]], y3 = vy[v[2]];
+        double xr = 0.5 * (x2 - x1), xs = 0.5 * (x3 - x1), yr = 0.5 * (y2 - y1), ys = 0.5 * (y3 - y1);
+        double J = xr * ys - xs * yr;
+        if (!(J > 1e-14 * scale * scale))
+            return fail(c, DG_EMESH, "element " + std::to_string(k) + " is clockwise or degenerate");
+        double rx = ys / J, ry = -xs / J, sx = -yr / J, sy = xr / J;
+        double *g = &geo[k * 16];
+        g[dg::G_RX] = rx; g[dg::G_RY] = ry; g[dg::G_SX] = sx; g[dg::G_SY] = sy; g[dg::G_J] = J;
+        // outward normals from the metric: face 0 (s = -1): -grad s; face 1 (r+s = 0): grad(r+s);
+        // face 2 (r = -1): -grad r; sJ = |grad| J
+        double nn[3][2] = {{-sx, -sy}, {rx + sx, ry + sy}, {-rx, -ry}};
+        for (int f = 0; f < 3; ++f) {
+            double len = std::hypot(nn[f][0], nn[f][1]);
+            g[dg::G_NX + f] = nn[f][0] / len;
+            g[dg::G_NY + f] = nn[f][1] / len;
+            g[dg::G_FS + f] = len;          // Fscale = sJ / J = |grad| (since sJ = |grad| J)
+        }
+    }
+    // --- reciprocity and face matching
+    std::vector<int4> conn(K);
+    for (int64_t k = 0; k < K; ++k) {
+        int packed = 0;
+        int nb[3];
+        for (int f = 0; f < 3; ++f) {
+            int32_t e2 = EToE[k * 3 + f], f2 = EToF[k * 3 + f], b = bc[k * 3 + f];
+            nb[f] = e2;
+            packed |= (f2 & 3) << (2 * f);
+            packed |= (b & 3) << (8 + 2 * f);
+            if (b != DG_BC_INTERIOR) {
+                if (e2 != k || f2 != f) return fail(c, DG_EMESH, "boundary face must name itself at element " + std::to_string(k));
+                continue;
+            }
+            if (e2 == k) return fail(c, DG_EMESH, "interior face names its own element " + std::to_string(k));
+            if (EToE[e2 * 3 + f2] != k || EToF[e2 * 3 + f2] != f || bc[e2 * 3 + f2] != DG_BC_INTERIOR)
+                return fail(c, DG_EMESH, "faces not reciprocal at element " + std::to_string(k));
+            // conforming, counter-clockwise: own (a, b) meets neighbour (b', a') up to one translation
+            int32_t a = EToV[k * 3 + f], bb = EToV[k * 3 + (f + 1) % 3];
+            int32_t a2 = EToV[e2 * 3 + f2], b2 = EToV[e2 * 3 + (f2 + 1) % 3];
+            double tx1 = vx[a] - vx[b2], ty1 = vy[a] - vy[b2];
+            double tx2 = vx[bb] - vx[a2], ty2 = vy[bb] - vy[a2];
+            double tol = 1e-9 * scale;
+            if (std::fabs(tx1 - tx2) > tol || std::fabs(ty1 - ty2) > tol)
+                return fail(c, DG_EMESH, "face nodes do not match at element " + std::to_string(k));
+        }
+        conn[k] = make_int4(nb[0], nb[1], nb[2], packed);
+    }
+    // --- wall faces and their node coordinates
+    std::vector<int2> walls;
+    std::vector<double> wxy;
+    for (int64_t k = 0; k < K; ++k)
+        for (int f = 0; f < 3; ++f)
+            if (bc[k * 3 + f] == DG_BC_WALL) {
+                walls.push_back(make_int2(static_cast<int>(k), f));
+                int32_t v0 = EToV[k * 3], v1 = EToV[k * 3 + 1], v2 = EToV[k * 3 + 2];
+                for (int i = 0; i < Nfp; ++i) {
+                    int vm = c->ops.Fmask[f * Nfp + i];
+                    double r = c->ops.r[vm], s = c->ops.s[vm];
+                    wxy.push_back(0.5 * (-(r + s) * vx[v0] + (1 + r) * vx[v1] + (1 + s) * vx[v2]));
+                    wxy.push_back(0.5 * (-(r + s) * vy[v0] + (1 + r) * vy[v1] + (1 + s) * vy[v2]));
+                }
+            }
+    // --- device buffers
+    c->K = K;
+    const size_t nd = static_cast<size_t>(K) * 4 * Np;
+    DG_CUDA(c, c->K0a.alloc(nd));
+    DG_CUDA(c, c->K0b.alloc(nd));
+    DG_CUDA(c, c->K1.alloc(nd));
+    DG_CUDA(c, c->geo64.alloc(geo.size()));
+    DG_CUDA(c, c->conn.alloc(K));
+    DG_CUDA(c, c->lam.alloc(K));
+    DG_CUDA(c, cudaMemcpy(c->geo64.ptr, geo.data(), geo.size() * sizeof(double), cudaMemcpyHostToDevice));
+    DG_CUDA(c, cudaMemcpy(c->conn.ptr, conn.data(), K * sizeof(int4), cudaMemcpyHostToDevice));
+    if (c->prm.precision == DG_PRECISION_MIXED) {
+        std::vector<float> g32(geo.begin(), geo.end());
+        DG_CUDA(c, c->geo32.alloc(g32.size()));
+        DG_CUDA(c, cudaMemcpy(c->geo32.ptr, g32.data(), g32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    c->nwall = static_cast<int>(walls.size());
+    if (c->nwall > 0) {
+        DG_CUDA(c, c->wall.alloc(walls.size()));
+        DG_CUDA(c, c->fxy.alloc(wxy.size()));
+        DG_CUDA(c, c->fpart.alloc(walls.size() * 3));
+        DG_CUDA(c, cudaMemcpy(c->wall.ptr, walls.data(), walls.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        DG_CUDA(c, cudaMemcpy(c->fxy.ptr, wxy.data(), wxy.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    DG_CUDA(c, cudaMemsetAsync(c->K0a.ptr, 0, nd * sizeof(double), c->stream));
+    DG_CUDA(c, cudaMemsetAsync(c->K1.ptr, 0, nd * sizeof(double), c->stream));
+    c->cur_is_a = true;
+    c->vx.assign(vx, vx + Nv);
+    c->vy.assign(vy, vy + Nv);
+    c->EToV.assign(EToV, EToV + K * 3);
+    c->geo64h.swap(geo);
+    c->source_kind = DG_SOURCE_NONE;
+    cudaError_t e = (c->prm.precision == DG_PRECISION_FP64) ? dg::stage_shape_fp64(c->prm.p, K, c->shape)
+                                                             : dg::stage_shape_mixed(c->prm.p, K, c->shape);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel configuration");
+    return DG_OK;
+}
+
+dg_status dg_node_coords(const dg_ctx *c, double *x, double *y)
+{
+    if (!c || !x || !y || c->K < 1) return DG_EINVAL;
+    const int Np = c->ops.Np;
+    for (long long k = 0; k < c->K; ++k) {
+        int32_t v0 = c->EToV[k * 3], v1 = c->EToV[k * 3 + 1], v2 = c->EToV[k * 3 + 2];
+        for (int i = 0; i < Np; ++i) {
+            double r = c->ops.r[i], s = c->ops.s[i];
+            x[k * Np + i] = 0.5 * (-(r + s) * c->vx[v0] + (1 + r) * c->vx[v1] + (1 + s) * c->vx[v2]);
+            y[k * Np + i] = 0.5 * (-(r + s) * c->vy[v0] + (1 + r) * c->vy[v1] + (1 + s) * c->vy[v2]);
+        }
+    }
+    return DG_OK;
+}
+
+dg_status dg_set_state(dg_ctx *c, const double *U, int on_device)
+{
+    if (!c) return DG_EINVAL;
+    c->err.clear();
+    if (!U || c->K < 1) return fail(c, DG_EINVAL, "null state or no mesh");
+    const size_t nd = ndof(c);
+    c->cur_is_a = true;
+    DG_CUDA(c, cudaMemcpyAsync(c->K0a.ptr, U, nd * sizeof(double),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    DG_CUDA(c, cudaMemsetAsync(c->K1.ptr, 0, nd * sizeof(double), c->stream));
+    if (!on_device) DG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return DG_OK;
+}
+
+dg_status dg_get_state(dg_ctx *c, double *U, int on_device)
+{
+    if (!c) return DG_EINVAL;
+    c->err.clear();
+    if (!U || c->K < 1) return fail(c, DG_EINVAL, "null state or no mesh");
+    DG_CUDA(c, cudaMemcpyAsync(U, c->cur(), ndof(c) * sizeof(double),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) DG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return DG_OK;
+}
+
+dg_status dg_set_source(dg_ctx *c, int kind, const double *params)
+{
+    if (!c) return DG_EINVAL;
+    c->err.clear();
+    if (c->K < 1) return fail(c, DG_EINVAL, "no mesh");
+    if (kind == DG_SOURCE_NONE) {
+        c->source_kind = kind;
+        return DG_OK;
+    }
+    if (kind != DG_SOURCE_MANUFACTURED || !params) return fail(c, DG_EINVAL, "unknown source kind");
+    const int Np = c->ops.Np;
+    std::vector<double> x(static_cast<size_t>(c->K) * Np), y(x.size());
+    dg_node_coords(c, x.data(), y.data());
+    std::vector<double> S(ndof(c));
+    for (long long k = 0; k < c->K; ++k)
+        for (int i = 0; i < Np; ++i) {
+            double s4[4];
+            manufactured_source(x[k * Np + i], y[k * Np + i], params[0], params[1], c->prm, s4);
+            for (int q = 0; q < 4; ++q) S[(k * 4 + q) * Np + i] = s4[q];
+        }
+    DG_CUDA(c, c->src.alloc(S.size()));
+    DG_CUDA(c, cudaMemcpy(c->src.ptr, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice));
+    c->source_kind = kind;
+    return DG_OK;
+}
+
+dg_status dg_rhs(dg_ctx *c, double t, const double vw[2], double *dUdt, int on_device)
+{
+    if (!c) return DG_EINVAL;
+    c->err.clear();
+    if (!dUdt || c->K < 1) return fail(c, DG_EINVAL, "null output or no mesh");
+    double *out = dUdt;
+    if (!on_device) {
+        if (c->rtmp.n != ndof(c)) DG_CUDA(c, c->rtmp.alloc(ndof(c)));
+        out = c->rtmp.ptr;
+    }
+    dg_status st = run_stage(c, -1, t, 0.0, vw, dg::STAGE_RHS_ONLY, c->cur(), nullptr, out);
+    if (st != DG_OK) return st;
+    if (!on_device) {
+        DG_CUDA(c, cudaMemcpyAsync(dUdt, out, ndof(c) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        DG_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return DG_OK;
+}
+
+dg_status dg_lsrk_step(dg_ctx *c, double t, double dt, const double vw[2])
+{
+    if (!c) return DG_EINVAL;
+    c->err.clear();
+    if (c->K < 1) return fail(c, DG_EINVAL, "no mesh");
+    if (!std::isfinite(dt) || !std::isfinite(t)) return fail(c, DG_EINVAL, "t and dt must be finite");
+    for (int s = 0; s < 5; ++s) {
+        dg_status st = run_stage(c, s, t + kRkC[s] * dt, dt, vw, dg::STAGE_UPDATE, c->cur(), c->other(), nullptr);
+        if (st != DG_OK) return st;
+        c->cur_is_a = !c->cur_is_a;
+    }
+    return DG_OK;
+}
+
+dg_status dg_lsrk_steps(dg_ctx *c, double t, double dt, const double vw[2], int nsteps)
+{
+    for (int n = 0; n < nsteps; ++n) {
+        dg_status st = dg_lsrk_step(c, t + n * dt, dt, vw);
+        if (st != DG_OK) return st;
+    }
+    return DG_OK;
+}
+
+dg_status dg_compute_dt(dg_ctx *c, double cfl, const double vw[2], double *dt)
+{
+    if (!c) return DG_EINVAL;
+    c->err.clear();
+    if (!dt || c->K < 1 || !(cfl > 0.0)) return fail(c, DG_EINVAL, "need dt pointer, mesh and cfl > 0");
+    dg::Phys<double> ph = make_phys<double>(c->prm, vw);
+    DG_CUDA(c, dg::launch_dt_lambda(aux_mesh(c), ph, c->prm.C1, c->lam.ptr, c->stream));
+    DG_CUDA(c, dg::launch_max_reduce(c->lam.ptr, c->K, c->scal.ptr, c->stream));
+    c->launches += 2;
+    double lam = 0.0;
+    DG_CUDA(c, cudaMemcpyAsync(&lam, c->scal.ptr, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    DG_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (!std::isfinite(lam) || !(lam > 0.0)) return fail(c, DG_ENONFINITE, "time-step bound is not finite");
+    *dt = cfl / lam;
+    return DG_OK;
+}
+
+dg_status dg_wall_forces(dg_ctx *c, const double xc[2], double out[3])
+{
+    if (!c) return DG_EINVAL;
+    c->err.clear();
+    if (!out || c->K < 1) return fail(c, DG_EINVAL, "null output or no mesh");
+    if (c->nwall == 0) {
+        out[0] = out[1] = out[2] = 0.0;
+        return DG_OK;
+    }
+    double x0 = xc ? xc[0] : 0.0, y0 = xc ? xc[1] : 0.0;
+    dg::Phys<double> ph = make_phys<double>(c->prm, nullptr);
+    DG_CUDA(c, dg::launch_wall_force_faces(aux_mesh(c), ph, c->wall.ptr, c->fxy.ptr, c->wface.ptr, c->nwall,
+                                           x0, y0, c->fpart.ptr, c->stream));
+    DG_CUDA(c, dg::launch_sum3(c->fpart.ptr, c->nwall, c->scal.ptr, c->stream));
+    c->launches += 2;
+    DG_CUDA(c, cudaMemcpyAsync(out, c->scal.ptr, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    DG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return DG_OK;
+}
+
+dg_status dg_check_finite(dg_ctx *c, int *ok)
+{
+    if (!c) return DG_EINVAL;
+    c->err.clear();
+    if (!ok || c->K < 1) return fail(c, DG_EINVAL, "null output or no mesh");
+    DG_CUDA(c, cudaMemsetAsync(c->flag.ptr, 0, sizeof(int), c->stream));
+    DG_CUDA(c, dg::launch_nonfinite(c->cur(), static_cast<long long>(ndof(c)), c->flag.ptr, c->stream));
+    c->launches += 1;
+    int f = 0;
+    DG_CUDA(c, cudaMemcpyAsync(&f, c->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    DG_CUDA(c, cudaStreamSynchronize(c->stream));
+    *ok = f ? 0 : 1;
+    return DG_OK;
+}
+
+dg_status dg_rigid_step(const double coeff[3], double F, double dt, double state[3], double *v_b)
+{
+    // Newmark average acceleration (beta = 1/4, gamma = 1/2) for
+    // M y'' + C y' + K y = F: solve for the new acceleration from the
+    // effective equation, then update displacement and velocity.
+    if (!coeff || !state || !v_b || !(dt > 0.0)) return DG_EINVAL;
+    const double M = coeff[0], C = coeff[1], Kr = coeff[2];
+    const double y = state[0], yd = state[1], ydd = state[2];
+    const double meff = M + 0.5 * dt * C + 0.25 * dt * dt * Kr;
+    if (!(std::fabs(meff) > 0.0)) return DG_EINVAL;
+    const double rhs = F - C * (yd + 0.5 * dt * ydd) - Kr * (y + dt * yd + 0.25 * dt * dt * ydd);
+    const double a = rhs / meff;
+    const double yn = y + dt * yd + 0.25 * dt * dt * (ydd + a);
+    const double vn = yd + 0.5 * dt * (ydd + a);
+    *v_b = (yn - y) / dt;
+    state[0] = yn;
+    state[1] = vn;
+    state[2] = a;
+    return DG_OK;
+}
+
+}  // extern "C"
