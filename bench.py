@@ -1,0 +1,433 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused nodal IP-DG residual + LSRK stage on GB300.
+
+Metric: DOF-stage updates per second (one DOF = one conserved scalar at one
+node; one DOF-stage = that DOF carried through one RK stage: residual
+evaluation and register update).  Workload: isentropic vortex, p = 4
+(Np = 15), periodic square of 128 x 128 split quads (K = 32,768), mu = 1e-3,
+advanced by the five-stage 2N-storage scheme; the mixed path (FP32
+arithmetic, FP64 state, pressure and registers) is the headline, the plain
+FP64 path is reported beside it.  A 512 x 512 variant (K = 524,288, working
+set well above L2) is reported for the roofline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank runs an independent
+replica (the path needs no exchange between problems); the value is the
+total over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF-stage updates/s at p=4, mixed vs FP64 GPU path, and % of GB300 HBM roofline"
+UNIT = "DOF-stage/s"
+P = 4
+NP = (P + 1) * (P + 2) // 2
+L2_FLUSH_BYTES = 512 << 20
+# HBM traffic of one stage launch that the algorithm needs: read K0, K1 and
+# write K0, K1 (FP64, 32 B per DOF; the first stage does not read K1), plus
+# the FP32 geometry record (64 B) and the connectivity record (16 B) of each
+# element.
+GEO_BYTES_MIXED = 64 + 16
+GEO_BYTES_FP64 = 128 + 16
+
+
+def algorithmic_bytes_per_step(K, geo_bytes):
+    dof = 4 * K * NP
+    state = dof * (24 + 4 * 32)          # stage 1 skips the K1 read
+    return state + 5 * K * geo_bytes
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("dg_stage.cuh", "dg_device.cuh", "stage_mixed.cu"):
+        with open(os.path.join(ROOT, "paper_2508_17917_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per DOF-stage of the mixed stage kernel from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "stage_kernel_mixed_p4.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"dram_bytes_per_dof_stage:\s*([0-9.eE+-]+)\s*\(kernel_hash\s+([0-9a-f]+)\)", text)
+    if not m or m.group(2) != kernel_hash():
+        return None
+    return float(m.group(1))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[4], parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        pmax = max(r[2] for r in rows)
+        loaded = [r for r in rows if r[2] > 0.5 * pmax] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in loaded for i, v in enumerate(r[4]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": rows[0][1],
+                "reasons": reasons, "samples": len(rows), "samples_under_load": len(loaded),
+                "power_w_max": pmax}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def vortex_problem(n):
+    import dg_inputs
+    return dg_inputs.periodic_square(n)
+
+
+def timed_steps(dg, torch, solver, dt, steps, warmup, flush, stream):
+    """Per-step CUDA-event times (ms) with an L2 flush before every step."""
+    for _ in range(warmup):
+        solver.step(0.0, dt)
+    torch.cuda.synchronize()
+    evs = []
+    n0 = solver.launches
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        solver.step(0.0, dt)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    launches = solver.launches - n0
+    return [a.elapsed_time(b) for a, b in evs], launches
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import dg_inputs
+    import paper_2508_17917_gb300 as dg
+    from dg_inputs.states import to_kcn
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    mesh = vortex_problem(128)
+    K = mesh.K
+    dof = 4 * K * NP
+    results = {}
+    solvers = {}
+    for prec in ("mixed", "fp64"):
+        s = dg.Solver(mesh, P, prec, stream=sh, mu=1e-3)
+        x, y = s.node_coords()
+        U0 = dg_inputs.perturb(to_kcn(dg_inputs.isentropic_vortex(x, y)), seed=0)
+        s.set_state(U0)
+        dt = s.dt(0.3)
+        solvers[prec] = (s, U0, dt)
+
+    # --- headline: mixed path, clocks sampled during the timed region
+    s, U0, dt = solvers["mixed"]
+    s.set_state(U0)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        times, launches = timed_steps(dg, torch, s, dt, args.steps, args.warmup, flush, stream)
+    torch.cuda.synchronize()
+    total_ms = sum(times)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    ok = s.check_finite()
+    value = ws * dof * 5 * args.steps / (total_ms * 1e-3)
+    ms_step = total_ms / args.steps
+    stage_ms = ms_step / 5.0
+    peak, peak_kind = measured_peaks()
+    bytes_step = algorithmic_bytes_per_step(K, GEO_BYTES_MIXED)
+    achieved = bytes_step / 5.0 / (stage_ms * 1e-3) / 1e9
+    traffic = recorded_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind,
+                "traffic": (traffic * dof * 5 / 5.0) if traffic is not None else None,
+                "algorithmic_bytes_per_launch": bytes_step / 5.0,
+                "kernel": "dg::stage_kernel<4, float>"}
+
+    # --- FP64 path, same workload
+    s64, U64, dt64 = solvers["fp64"]
+    s64.set_state(U64)
+    t64, _ = timed_steps(dg, torch, s64, dt64, max(3, args.steps // 20), 2, flush, stream)
+    v64 = dof * 5 * len(t64) / (sum(t64) * 1e-3)
+
+    # --- large variant (working set well above L2), mixed path
+    large = None
+    if not args.no_large:
+        ml = vortex_problem(512)
+        sl = dg.Solver(ml, P, "mixed", stream=sh, mu=1e-3)
+        xl, yl = sl.node_coords()
+        sl.set_state(dg_inputs.perturb(to_kcn(dg_inputs.isentropic_vortex(xl, yl)), seed=0))
+        dtl = sl.dt(0.3)
+        tl, _ = timed_steps(dg, torch, sl, dtl, max(5, args.steps // 10), 2, flush, stream)
+        dofl = 4 * ml.K * NP
+        vl = dofl * 5 * len(tl) / (sum(tl) * 1e-3)
+        ach = algorithmic_bytes_per_step(ml.K, GEO_BYTES_MIXED) / (sum(tl) / len(tl) * 1e-3) / 1e9
+        large = {"workload": "vortex p=4, 512x512 split quads", "K": ml.K, "value": vl,
+                 "ms_per_step": sum(tl) / len(tl), "roofline_achieved_gbs": ach,
+                 "roofline_frac": ach / peak}
+        del sl
+
+    # --- end to end through the C ABI with host buffers (pinned)
+    host_in = torch.empty((K, 4, NP), dtype=torch.float64, pin_memory=True)
+    host_in.copy_(torch.from_numpy(U0))
+    host_out = torch.empty_like(host_in, pin_memory=True)
+    e2e_steps = max(3, args.steps // 10)
+    for _ in range(2):
+        dg.dg_set_state(s.ctx, host_in)
+        s.step(0.0, dt)
+        dg.dg_get_state(s.ctx, host_out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dg.dg_set_state(s.ctx, host_in)
+        s.step(0.0, dt)
+        dg.dg_get_state(s.ctx, host_out)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": ws * dof * 5 * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(host_in.numel() * 8), "d2h_bytes_per_step": int(host_out.numel() * 8)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(budget_s=args.cpu_seconds)
+
+    if ws > 1:
+        torch.distributed.barrier()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic: seeded isentropic vortex on a periodic square",
+            "config": {"workload": "isentropic vortex, p=4 (Np=15), periodic [0,10]^2, 128x128 quads "
+                                   "split SW-NE (K=32768), mu=1e-3, CFL 0.3, 5-stage 2N-storage RK",
+                       "K": K, "p": P, "dofs": dof, "precision": "mixed (FP32 arithmetic; FP64 state, "
+                                                                "pressure, RK registers)",
+                       "l2": "flushed (512 MB write) before every timed step; the 31 MB working set "
+                             "stays in L2 across the 5 stages of a step",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": roofline,
+            "fp64_path": {"value": v64, "unit": UNIT, "ms_per_step": sum(t64) / len(t64),
+                          "mixed_over_fp64": value / ws / v64},
+            "large_mesh": large,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk.summary(),
+            "gpu_launches": int(launches),
+            "finite": bool(ok),
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(budget_s=20.0, steps=1):
+    """The oracle (plain FP64 C, OpenMP over elements) on the host cores: one
+    LSRK step of a periodic vortex mesh at p = 4, mesh sized to the budget."""
+    import numpy as np
+    import dg_inputs
+    import oracle
+    from dg_inputs.states import to_kcn
+    oracle.build_oracle()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    # calibrate on a small mesh, then size the sample
+    m = dg_inputs.periodic_square(16)
+    Pq = oracle.Problem(m, P, mu=1e-3)
+    U = to_kcn(dg_inputs.isentropic_vortex(Pq.x, Pq.y))
+    t0 = time.perf_counter()
+    Pq.lsrk_step(U, 0.0, 1e-5)
+    per_elem = (time.perf_counter() - t0) / m.K
+    n = int(max(16, min(128, (budget_s / max(per_elem, 1e-9) / 2 / steps) ** 0.5)))
+    m = dg_inputs.periodic_square(n)
+    Pq = oracle.Problem(m, P, mu=1e-3)
+    U = to_kcn(dg_inputs.isentropic_vortex(Pq.x, Pq.y))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        U = Pq.lsrk_step(U, 0.0, 1e-5)
+    el = time.perf_counter() - t0
+    dof = 4 * m.K * NP
+    return {"value": dof * 5 * steps / el, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"{steps} LSRK step(s) (5 residual evaluations each) of the p=4 vortex on "
+                      f"{n}x{n} split quads (K={m.K}), same method as the GPU path",
+            "seconds": el}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import dg_inputs
+    import oracle
+    from dg_inputs.states import to_kcn
+    oracle.build_oracle()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    # one step of the reference arm: one LSRK step of a bounded sample mesh,
+    # sized so that warmup + steps take about a minute and a half in total
+    m = dg_inputs.periodic_square(16)
+    Pq = oracle.Problem(m, P, mu=1e-3)
+    U = to_kcn(dg_inputs.isentropic_vortex(Pq.x, Pq.y))
+    t0 = time.perf_counter()
+    Pq.lsrk_step(U, 0.0, 1e-5)
+    per_elem = (time.perf_counter() - t0) / m.K
+    total = args.steps + args.warmup
+    n = int(max(4, min(128, (90.0 / total / max(per_elem, 1e-9) / 2) ** 0.5)))
+    m = dg_inputs.periodic_square(n)
+    Pq = oracle.Problem(m, P, mu=1e-3)
+    U = to_kcn(dg_inputs.isentropic_vortex(Pq.x, Pq.y))
+    dt, _ = Pq.dt(U, 0.3)
+    for _ in range(args.warmup):
+        U = Pq.lsrk_step(U, 0.0, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U = Pq.lsrk_step(U, 0.0, dt)
+    el = time.perf_counter() - t0
+    dof = 4 * m.K * NP
+    value = dof * 5 * args.steps / el
+    sample = (f"oracle: one LSRK step per benchmark step of the p=4 vortex on {n}x{n} split quads "
+              f"(K={m.K}) on {oracle.get_threads()} host threads")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic: seeded isentropic vortex on a periodic square",
+            "config": {"workload": "isentropic vortex, p=4 (Np=15), periodic square, CPU sample",
+                       "K": m.K, "p": P},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_profile(args):
+    """A few steps of one workload, for ncu captures (no timing, no extras)."""
+    import torch
+    import dg_inputs
+    import paper_2508_17917_gb300 as dg
+    from dg_inputs.states import to_kcn
+    prec, n = {"mixed512": ("mixed", 512), "mixed128": ("mixed", 128),
+               "fp64_128": ("fp64", 128)}[args.profile]
+    torch.cuda.set_device(0)
+    mesh = vortex_problem(n)
+    s = dg.Solver(mesh, P, prec, stream=torch.cuda.current_stream().cuda_stream, mu=1e-3)
+    x, y = s.node_coords()
+    s.set_state(dg_inputs.perturb(to_kcn(dg_inputs.isentropic_vortex(x, y)), seed=0))
+    dt = s.dt(0.3)
+    s.steps(0.0, dt, args.steps)
+    torch.cuda.synchronize()
+    assert s.check_finite()
+    print(json.dumps({"profile": args.profile, "K": mesh.K, "steps": args.steps,
+                      "launches": s.launches}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--profile", choices=["mixed512", "mixed128", "fp64_128"], default=None)
+    args = ap.parse_args()
+    if args.profile:
+        run_profile(args)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

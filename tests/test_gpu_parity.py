@@ -92,12 +92,39 @@ def test_rhs_manufactured_source(dg, precision):
     P = oracle.Problem(mesh, 3, mu=0.01, source=("manufactured", kappa, C2))
     U = dg_inputs.perturb(to_kcn(oracle.manufactured_state(P.x, P.y, kappa, C2)), seed=2, amp=1e-4)
     ref = P.rhs(U)
+    # near the steady solution the flux terms cancel the source: measure the
+    # error against the size of the terms that cancel
+    P0 = oracle.Problem(mesh, 3, mu=0.01)
+    scale = max(np.abs(ref).max(), np.abs(P0.rhs(U)).max())
     s = dg.Solver(mesh, 3, precision, stream=stream(), mu=0.01)
     s.set_source(dg.DG_SOURCE_MANUFACTURED, (kappa, C2))
     s.set_state(U)
     got = s.rhs(0.0)
-    err = np.abs(got - ref).max() / np.abs(ref).max()
-    assert err <= (1e-12 if precision == "fp64" else 2e-5), err
+    err = np.abs(got - ref).max() / scale
+    # Mixed path: the state enters FP32 with relative rounding 2^-24 = 6e-8 of
+    # |U|; for this state |E| / |variation of E| = C2 / 2 = 100, and the
+    # derivative operators amplify by max_i sum_j |Dr_ij| h / 2 ~ 10 at p = 3,
+    # so the residual is good to about 6e-8 * 100 * 10 = 6e-5 of its terms.
+    assert err <= (1e-12 if precision == "fp64" else 2e-4), err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_manufactured_100_steps(dg, precision):
+    """The manufactured steady state of Sec. 3.1 advanced 100 steps: state
+    error within the path's tolerance (the residual-level FP32 error above is
+    multiplied by dt, so the state keeps its digits)."""
+    kappa, C2 = 25.0, 200.0
+    mesh = dg_inputs.periodic_square(4, L=4 * np.pi / kappa)
+    P = oracle.Problem(mesh, 3, mu=0.01, source=("manufactured", kappa, C2))
+    U0 = dg_inputs.perturb(to_kcn(oracle.manufactured_state(P.x, P.y, kappa, C2)), seed=3, amp=1e-4)
+    dt, _ = P.dt(U0, 0.3)
+    ref = P.run(U0, 0.0, dt, 100)
+    s = dg.Solver(mesh, 3, precision, stream=stream(), mu=0.01)
+    s.set_source(dg.DG_SOURCE_MANUFACTURED, (kappa, C2))
+    s.set_state(U0)
+    s.steps(0.0, dt, 100)
+    err = rel_l2(P, s.get_state(), ref)
+    assert np.all(err <= PREC_TOL[precision]), err
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
@@ -172,9 +199,12 @@ def test_free_stream_preserved_mixed(dg):
     U = to_kcn(dg_inputs.free_stream(x.shape, rho=1.0, u=0.35, v=0.1, p=1.0))
     s.set_state(U)
     R = s.rhs(0.0, (0.02, 0.0))
+    # FP32 arithmetic: the discrete divergence of a constant flux vanishes only
+    # to rounding (sum_j Dr_ij = 0 up to 2^-24 |Dr|), so the residual is at
+    # the 1e-6 level and 10 steps of dt = 1e-3 move the state by <= 1e-7
     assert np.abs(R).max() < 1e-5
     s.steps(0.0, 1e-3, 10)
-    assert np.abs(s.get_state() - U).max() < 1e-12 * np.abs(U).max() * 1e3
+    assert np.abs(s.get_state() - U).max() < 1e-7
 
 
 def test_check_finite_and_bad_mesh(dg):
