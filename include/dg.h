@@ -164,6 +164,35 @@ dg_status dg_node_coords(const dg_ctx *ctx, double *x, double *y);
 dg_status dg_reference_operators(int p, double *r, double *s, double *Dr, double *Ds,
                                  double *LIFT, int32_t *Fmask);
 
+/* Largest number of wall faces dg_wall_forces_noalloc accepts. */
+#define DG_NOALLOC_MAX_WALL_FACES 16384
+
+/* The wall force and moment of dg_wall_forces, computed without any device
+ * allocation.  There is no counterpart of this call in the paper.
+ *
+ * Who needs it: code that may not call cudaMalloc/cudaFree at the point
+ * where it asks for the forces -- for instance a structural solver embedded
+ * in a larger application whose device memory is owned by that application's
+ * own pool allocator, or a tight coupling loop that must not risk the device
+ * synchronisation a cudaFree can cause.  dg_wall_forces keeps its per-face
+ * partial sums in a buffer that belongs to the mesh; this call keeps them in
+ * a fixed array of DG_NOALLOC_MAX_WALL_FACES * 3 + 4 doubles (about 384 KB)
+ * that is part of the library image, so every GPU that loads the library
+ * holds that array until the process exits.
+ *
+ * Behaviour: same inputs, result and synchronisation as dg_wall_forces
+ * (out = (Fx, Fy, Mz), the context's stream is synchronised).  The first
+ * call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  All calls in the
+ * process share the one array, which keeps the last call's contents (every
+ * call overwrites all the entries it reads, so nothing has to be cleared):
+ * two calls whose work overlaps on the GPU -- different streams, or
+ * different host threads -- race on it and must be serialised by the caller.
+ * Errors: DG_EINVAL (null, no mesh, more than DG_NOALLOC_MAX_WALL_FACES wall
+ * faces: the message says so and names dg_wall_forces as the alternative),
+ * DG_EUNSUPPORTED (device index above 63), DG_ECUDA. */
+dg_status dg_wall_forces_noalloc(dg_ctx *ctx, const double xc[2], double out[3]);
+
 /* Number of the library's kernels launched by this context so far. */
 int64_t dg_kernel_launches(const dg_ctx *ctx);
 

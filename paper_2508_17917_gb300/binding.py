@@ -14,13 +14,15 @@ import numpy as np
 __all__ = ["DG_OK", "DG_PRECISION_FP64", "DG_PRECISION_MIXED", "DG_SOURCE_NONE",
            "DG_SOURCE_MANUFACTURED", "DgParams", "DGError", "lib", "library_path",
            "dg_create", "dg_destroy", "dg_set_mesh", "dg_set_state", "dg_get_state", "dg_rhs",
-           "dg_lsrk_step", "dg_lsrk_steps", "dg_compute_dt", "dg_wall_forces", "dg_rigid_step",
+           "dg_lsrk_step", "dg_lsrk_steps", "dg_compute_dt", "dg_wall_forces",
+           "dg_wall_forces_noalloc", "DG_NOALLOC_MAX_WALL_FACES", "dg_rigid_step",
            "dg_check_finite", "dg_set_source", "dg_node_coords", "dg_reference_operators",
            "dg_kernel_launches", "dg_last_error", "Solver", "EXPORTED"]
 
 DG_OK = 0
 DG_PRECISION_FP64, DG_PRECISION_MIXED = 0, 1
 DG_SOURCE_NONE, DG_SOURCE_MANUFACTURED = 0, 1
+DG_NOALLOC_MAX_WALL_FACES = 16384
 STATUS = {0: "DG_OK", -1: "DG_EINVAL", -2: "DG_EMESH", -3: "DG_ECUDA", -4: "DG_ENONFINITE",
           -5: "DG_ETIMEOUT", -6: "DG_EUNSUPPORTED"}
 
@@ -56,6 +58,7 @@ EXPORTED = {
     "dg_lsrk_steps": (C.c_int, [C.c_void_p, C.c_double, C.c_double, _dp, C.c_int]),
     "dg_compute_dt": (C.c_int, [C.c_void_p, C.c_double, _dp, _dp]),
     "dg_wall_forces": (C.c_int, [C.c_void_p, _dp, _dp]),
+    "dg_wall_forces_noalloc": (C.c_int, [C.c_void_p, _dp, _dp]),
     "dg_rigid_step": (C.c_int, [_dp, C.c_double, C.c_double, _dp, _dp]),
     "dg_check_finite": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "dg_set_source": (C.c_int, [C.c_void_p, C.c_int, _dp]),
@@ -172,6 +175,15 @@ def dg_compute_dt(ctx, cfl, vw=None):
 def dg_wall_forces(ctx, xc=(0.0, 0.0)):
     out = np.zeros(3)
     _check(lib().dg_wall_forces(ctx, _dptr(_f64(xc)), _dptr(out)), ctx)
+    return out
+
+
+def dg_wall_forces_noalloc(ctx, xc=(0.0, 0.0)):
+    """dg_wall_forces without device allocation: the partial sums live in a
+    fixed array inside the library (at most DG_NOALLOC_MAX_WALL_FACES wall
+    faces; concurrent calls on the GPU race on that array)."""
+    out = np.zeros(3)
+    _check(lib().dg_wall_forces_noalloc(ctx, _dptr(_f64(xc)), _dptr(out)), ctx)
     return out
 
 

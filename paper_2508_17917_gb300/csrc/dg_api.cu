@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -585,3 +586,74 @@ dg_status dg_rigid_step(const double coeff[3], double F, double dt, double state
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Wall forces with library-resident scratch (no device allocation).
+//
+// dg_wall_forces sums per-face partials in a buffer that belongs to the mesh.
+// This variant writes the partials and the summed triple into a fixed array
+// compiled into the library instead, so the call itself never asks the CUDA
+// allocator for memory.  The array is a host-side symbol: host code must not
+// hand its name to a kernel; its device address is looked up once per device
+// with cudaGetSymbolAddress and cached.
+namespace {
+
+constexpr int kNoallocMaxWallFaces = DG_NOALLOC_MAX_WALL_FACES;
+constexpr int kNoallocMaxDevices = 64;
+
+// nwall*3 partials followed by the 3-entry result; every call overwrites the
+// entries it reads, so nothing has to start at zero.
+static __device__ __align__(256) double g_noalloc_force_scratch[kNoallocMaxWallFaces * 3 + 4];
+
+std::mutex g_noalloc_mutex;
+double *g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up on the
+// first call per device, with that device current).
+dg_status noalloc_scratch(dg_ctx *c, double **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetDevice");
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(c, DG_EUNSUPPORTED, "device index beyond 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_force_scratch);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetSymbolAddress(g_noalloc_force_scratch)");
+        g_noalloc_addr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return DG_OK;
+}
+
+}  // namespace
+
+extern "C" dg_status dg_wall_forces_noalloc(dg_ctx *c, const double xc[2], double out[3])
+{
+    if (!c) return DG_EINVAL;
+    c->err.clear();
+    if (!out || c->K < 1) return fail(c, DG_EINVAL, "null output or no mesh");
+    if (c->nwall > kNoallocMaxWallFaces)
+        return fail(c, DG_EINVAL, "dg_wall_forces_noalloc: mesh has " + std::to_string(c->nwall) +
+                                      " wall faces, more than the fixed scratch holds (" +
+                                      std::to_string(kNoallocMaxWallFaces) + "); use dg_wall_forces");
+    if (c->nwall == 0) {
+        out[0] = out[1] = out[2] = 0.0;
+        return DG_OK;
+    }
+    double *scratch = nullptr;
+    dg_status st = noalloc_scratch(c, &scratch);
+    if (st != DG_OK) return st;
+    double *partial = scratch;
+    double *result = scratch + static_cast<size_t>(kNoallocMaxWallFaces) * 3;
+    double x0 = xc ? xc[0] : 0.0, y0 = xc ? xc[1] : 0.0;
+    dg::Phys<double> ph = make_phys<double>(c->prm, nullptr);
+    DG_CUDA(c, dg::launch_wall_force_faces(aux_mesh(c), ph, c->wall.ptr, c->fxy.ptr, c->wface.ptr, c->nwall,
+                                           x0, y0, partial, c->stream));
+    DG_CUDA(c, dg::launch_sum3(partial, c->nwall, result, c->stream));
+    c->launches += 2;
+    DG_CUDA(c, cudaMemcpyAsync(out, result, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    DG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return DG_OK;
+}
