@@ -1,0 +1,140 @@
+"""Cylinder cases through the C ABI against the oracle (Sec. 3.2-3.3).
+
+* Fixed cylinder, Re = 100, M = 0.2, p = 4 on the seeded O-grid (wall at
+  r = 0.5, far field): lift and drag coefficient histories over a window of
+  steps from a common seeded state, compared with the oracle's histories
+  (C_L relative to max |C_L| over the window, C_D relative to mean C_D).
+* The weakly coupled loop of Algorithm 3 (time step, Newmark step with the
+  previous step's lift, mesh velocity v_b = dy/dt, LSRK step with v_w,
+  forces) run by the library and by the oracle side by side.
+"""
+import numpy as np
+import pytest
+
+import dg_inputs
+import oracle
+from dg_inputs.states import to_kcn
+
+pytestmark = pytest.mark.gpu
+
+RE, MACH, GAMMA = 100.0, 0.2, 1.4
+P_INF = 1.0 / (GAMMA * MACH * MACH)
+KW = dict(mu=1.0 / RE, rho_inf=1.0, u_inf=1.0, v_inf=0.0, p_inf=P_INF)
+QINF = 0.5          # 1/2 rho |v|^2 D with rho = |v| = D = 1
+TOL = {"fp64": 1e-10, "mixed": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def dg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_17917_gb300 import build
+    build.build()
+    import paper_2508_17917_gb300 as dg
+    return dg
+
+
+def stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def start_state(P, seed=0):
+    r = np.hypot(P.x, P.y)
+    U = to_kcn(dg_inputs.free_stream(P.x.shape, rho=1.0, u=1.0, v=0.0, p=P_INF))
+    # smooth near-wall deficit so the start is not impulsive, plus a seeded perturbation
+    damp = np.tanh(4.0 * (r - 0.5))
+    U[:, 1] *= damp
+    U[:, 3] = P_INF / (GAMMA - 1) + 0.5 * U[:, 1] ** 2 / U[:, 0]
+    return dg_inputs.perturb(U, seed=seed, amp=1e-3)
+
+
+def history_errors(ref, got):
+    ref, got = np.asarray(ref), np.asarray(got)
+    cl_scale = np.abs(ref[:, 1]).max()
+    cd_scale = np.abs(ref[:, 0]).mean()
+    return (np.abs(got[:, 1] - ref[:, 1]).max() / cl_scale,
+            np.abs(got[:, 0] - ref[:, 0]).max() / cd_scale)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cylinder_cl_cd_window(dg, precision):
+    mesh = dg_inputs.ogrid_cylinder(60, 30, 0.5, 15.0, seed=0)
+    p = 4
+    P = oracle.Problem(mesh, p, **KW)
+    U0 = start_state(P)
+    dt, _ = P.dt(U0, 0.3)
+    nsteps, every = 60, 5
+    s = dg.Solver(mesh, p, precision, stream=stream(), **KW)
+    s.set_state(U0)
+    ref, got = [], []
+    U = U0.copy()
+    for n in range(nsteps // every):
+        U = P.run(U, n * every * dt, dt, every)
+        F = P.wall_forces(U)
+        ref.append((F[0] / QINF, F[1] / QINF))
+        s.steps(n * every * dt, dt, every)
+        G = s.wall_forces()
+        got.append((G[0] / QINF, G[1] / QINF))
+    e_cl, e_cd = history_errors(ref, got)
+    assert e_cl <= TOL[precision] and e_cd <= TOL[precision], (e_cl, e_cd)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cylinder_full_mesh_short(dg, precision):
+    """The 120 x 170 seeded O-grid (K = 40,800) at p = 4, ten steps."""
+    mesh = dg_inputs.ogrid_cylinder(120, 170, 0.5, 30.0, seed=0)
+    assert mesh.K == 40800
+    P = oracle.Problem(mesh, 4, **KW)
+    U0 = start_state(P, seed=1)
+    dt, _ = P.dt(U0, 0.3)
+    ref = P.run(U0, 0.0, dt, 10)
+    s = dg.Solver(mesh, 4, precision, stream=stream(), **KW)
+    s.set_state(U0)
+    assert abs(s.dt(0.3) - dt) <= 1e-12 * dt
+    s.steps(0.0, dt, 10)
+    F_ref = P.wall_forces(ref)
+    F_got = s.wall_forces()
+    assert np.all(np.abs(F_got - F_ref) <= TOL[precision] * np.abs(F_ref).max()), (F_got, F_ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_viv_coupled_loop(dg, precision):
+    """Algorithm 3 with m* = 10, zeta = 0.001, U* = 5 (Sec. 3.3 definitions:
+    M_r = 1, C_r = 4 pi f_n zeta, K_r = (1 + 1/m*)(2 pi f_n)^2, F_r = Lift/m,
+    m = m* rho pi D^2 / 4, f_n = U / (U* D))."""
+    mstar, zeta, ustar = 10.0, 1e-3, 5.0
+    fn = 1.0 / ustar
+    m = mstar * np.pi / 4.0
+    coeff = (1.0, 4 * np.pi * fn * zeta, (1 + 1 / mstar) * (2 * np.pi * fn) ** 2)
+    mesh = dg_inputs.ogrid_cylinder(40, 16, 0.5, 8.0, seed=5)
+    p = 3
+    P = oracle.Problem(mesh, p, **KW)
+    U0 = start_state(P, seed=2)
+    s = dg.Solver(mesh, p, precision, stream=stream(), **KW)
+    s.set_state(U0)
+    # oracle loop
+    U, st_o, t = U0.copy(), np.array([0.0, 0.05, 0.0]), 0.0
+    F_o = P.wall_forces(U)[1]
+    traj_o = []
+    # library loop
+    st_g, F_g = np.array([0.0, 0.05, 0.0]), s.wall_forces()[1]
+    traj_g = []
+    vb_o = vb_g = 0.0
+    for n in range(12):
+        dt_o, _ = P.dt(U, 0.3, (0.0, vb_o))
+        st_o, vb_o = oracle.newmark_step(coeff, F_o / m, dt_o, st_o)
+        U = P.lsrk_step(U, t, dt_o, (0.0, vb_o))
+        F_o = P.wall_forces(U)[1]
+        traj_o.append((st_o[0], F_o / QINF))
+        dt_g = s.dt(0.3, (0.0, vb_g))
+        st_g, vb_g = dg.dg_rigid_step(coeff, F_g / m, dt_g, st_g)
+        s.step(t, dt_g, (0.0, vb_g))
+        F_g = s.wall_forces()[1]
+        traj_g.append((st_g[0], F_g / QINF))
+        t += dt_o
+    traj_o, traj_g = np.array(traj_o), np.array(traj_g)
+    y_err = np.abs(traj_g[:, 0] - traj_o[:, 0]).max() / np.abs(traj_o[:, 0]).max()
+    cl_err = np.abs(traj_g[:, 1] - traj_o[:, 1]).max() / np.abs(traj_o[:, 1]).max()
+    assert y_err <= TOL[precision] and cl_err <= TOL[precision], (y_err, cl_err)
