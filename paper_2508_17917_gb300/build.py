@@ -19,6 +19,9 @@ LIB = os.path.join(HERE, "libdg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+# per-file extra flags: the mixed-precision kernels use fast FP32 division,
+# square root and flush-to-zero (FP64 instructions are not affected)
+FILE_FLAGS = {"stage_mixed.cu": ["--use_fast_math"]}
 
 
 def _nvcc() -> str:
@@ -37,7 +40,7 @@ def _stale() -> bool:
         return True
     t = os.path.getmtime(LIB)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
-    deps.append(os.path.join(INCLUDE, "dg.h"))
+    deps += [os.path.join(INCLUDE, "dg.h"), os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
@@ -51,7 +54,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     def compile_one(src):
         obj = os.path.join(OBJ, os.path.basename(src) + ".o")
         lang = ["-x", "cu"] if src.endswith(".cu") else []
-        cmd = [nvcc] + ARCH + flags + lang + ["-c", src, "-o", obj]
+        cmd = [nvcc] + ARCH + flags + FILE_FLAGS.get(os.path.basename(src), []) + lang + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")

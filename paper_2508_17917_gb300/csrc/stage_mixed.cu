@@ -1,17 +1,20 @@
-// stage_mixed.cu -- Mixed-precision (FP32 arithmetic, FP64 state, pressure and registers) instantiations of the fused stage kernel (p = 1..6).
-#include "dg_stage.cuh"
+// stage_mixed.cu -- mixed-precision stage kernel instantiations (p = 1..6):
+// FP32 arithmetic, FP64 state in HBM, FP64 pressure recovery and registers.
+#include "dg_stage_mixed.cuh"
 #include "launch.h"
 
 namespace dg {
 namespace {
 
-template <int P, typename real>
+template <int P>
 cudaError_t shape_p(long long K, LaunchShape &ls)
 {
-    using L = Smem<P, real>;
-    auto kern = stage_kernel<P, real>;
+    using L = MixedLayout<P>;
+    auto kern = stage_mixed_kernel<P>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(L::bytes));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     int per_sm = 0, dev = 0, sms = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Shape<P>::NT, L::bytes);
@@ -28,10 +31,10 @@ cudaError_t shape_p(long long K, LaunchShape &ls)
     return cudaSuccess;
 }
 
-template <int P, typename real>
-cudaError_t launch_p(const LaunchShape &ls, const StageParams &sp, const Phys<real> &ph, cudaStream_t st)
+template <int P>
+cudaError_t launch_p(const LaunchShape &ls, const StageParams &sp, const Phys<float> &ph, cudaStream_t st)
 {
-    stage_kernel<P, real><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
+    stage_mixed_kernel<P><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
     return cudaGetLastError();
 }
 
@@ -50,15 +53,15 @@ cudaError_t launch_p(const LaunchShape &ls, const StageParams &sp, const Phys<re
 
 cudaError_t stage_shape_mixed(int p, long long K, LaunchShape &out)
 {
-#define C_(P) shape_p<P, float>(K, out)
+#define C_(P) shape_p<P>(K, out)
     DG_SWITCH_P(p, C_)
 #undef C_
 }
 
 cudaError_t launch_stage_mixed(int p, const LaunchShape &ls, const StageParams &sp,
-                              const Phys<float> &ph, cudaStream_t st)
+                               const Phys<float> &ph, cudaStream_t st)
 {
-#define C_(P) launch_p<P, float>(ls, sp, ph, st)
+#define C_(P) launch_p<P>(ls, sp, ph, st)
     DG_SWITCH_P(p, C_)
 #undef C_
 }
