@@ -72,7 +72,8 @@ struct dg_ctx {
     std::vector<double> geo64h;
     // device
     DevBuf<double> K0a, K0b, K1, rtmp, geo64, ops64, Dr64, Ds64, src, lam, scal, fpart, fxy, wface;
-    DevBuf<float> geo32, ops32;
+    DevBuf<float> geo32, ops32, P0a, P0b;     // mixed path: pressures of the two K0 buffers
+    DevBuf<float4> S0a, S0b;                  // mixed path: FP32 copies of the two K0 buffers
     DevBuf<int4> conn;
     DevBuf<int> fmask, flag;
     DevBuf<int2> wall;
@@ -83,12 +84,20 @@ struct dg_ctx {
 
     double *cur() { return cur_is_a ? K0a.ptr : K0b.ptr; }
     double *other() { return cur_is_a ? K0b.ptr : K0a.ptr; }
+    float4 *scur() { return cur_is_a ? S0a.ptr : S0b.ptr; }
+    float4 *sother() { return cur_is_a ? S0b.ptr : S0a.ptr; }
+    float *pcur() { return cur_is_a ? P0a.ptr : P0b.ptr; }
+    float *pother() { return cur_is_a ? P0b.ptr : P0a.ptr; }
     ~dg_ctx()
     {
         for (auto *b : {&K0a, &K0b, &K1, &rtmp, &geo64, &ops64, &Dr64, &Ds64, &src, &lam, &scal, &fpart, &fxy, &wface})
             b->release();
         geo32.release();
         ops32.release();
+        P0a.release();
+        P0b.release();
+        S0a.release();
+        S0b.release();
         conn.release();
         fmask.release();
         flag.release();
@@ -164,6 +173,10 @@ dg_status run_stage(dg_ctx *c, int s, double t, double dt, const double vw[2], i
     sp.conn = c->conn.ptr;
     sp.fmask = c->fmask.ptr;
     sp.src = (c->source_kind != DG_SOURCE_NONE) ? c->src.ptr : nullptr;
+    sp.Sin = c->scur();
+    sp.Pin = c->pcur();
+    sp.Sout = c->sother();
+    sp.Pout = c->pother();
     sp.K = c->K;
     sp.A = (s >= 0) ? kRkA[s] : 0.0;
     sp.B = (s >= 0) ? kRkB[s] : 0.0;
@@ -381,6 +394,15 @@ dg_status dg_set_mesh(dg_ctx *c, int64_t Nv, const double *vx, const double *vy,
         std::vector<float> g32(geo.begin(), geo.end());
         DG_CUDA(c, c->geo32.alloc(g32.size()));
         DG_CUDA(c, cudaMemcpy(c->geo32.ptr, g32.data(), g32.size() * sizeof(float), cudaMemcpyHostToDevice));
+        const size_t np = static_cast<size_t>(K) * Np, npp = static_cast<size_t>(K) * dg::pressure_row(c->prm.p);
+        DG_CUDA(c, c->S0a.alloc(np));
+        DG_CUDA(c, c->S0b.alloc(np));
+        DG_CUDA(c, c->P0a.alloc(npp));
+        DG_CUDA(c, c->P0b.alloc(npp));
+        DG_CUDA(c, cudaMemsetAsync(c->S0a.ptr, 0, np * sizeof(float4), c->stream));
+        DG_CUDA(c, cudaMemsetAsync(c->S0b.ptr, 0, np * sizeof(float4), c->stream));
+        DG_CUDA(c, cudaMemsetAsync(c->P0a.ptr, 0, npp * sizeof(float), c->stream));
+        DG_CUDA(c, cudaMemsetAsync(c->P0b.ptr, 0, npp * sizeof(float), c->stream));
     }
     c->nwall = static_cast<int>(walls.size());
     if (c->nwall > 0) {
@@ -429,6 +451,11 @@ dg_status dg_set_state(dg_ctx *c, const double *U, int on_device)
     DG_CUDA(c, cudaMemcpyAsync(c->K0a.ptr, U, nd * sizeof(double),
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     DG_CUDA(c, cudaMemsetAsync(c->K1.ptr, 0, nd * sizeof(double), c->stream));
+    if (c->prm.precision == DG_PRECISION_MIXED) {
+        DG_CUDA(c, dg::launch_make_shadow(c->prm.p, c->K0a.ptr, c->K, c->prm.gamma - 1.0, c->S0a.ptr, c->P0a.ptr,
+                                          c->stream));
+        c->launches += 1;
+    }
     if (!on_device) DG_CUDA(c, cudaStreamSynchronize(c->stream));
     return DG_OK;
 }

@@ -36,6 +36,10 @@ struct StageParams {
     const void *ops;           // real Dr[Np*Np], Ds[Np*Np], LIFT[Np*3Nfp]
     const int *fmask;          // 3*Nfp, counter-clockwise along each face
     const double *src;         // optional nodal source [K][4][Np] or null
+    const float4 *Sin;         // mixed path: FP32 copy of K0in, [K][Np] (rho, m1, m2, E)
+    const float *Pin;          // mixed path: pressure of K0in, [K][NpP]
+    float4 *Sout;              // mixed path: FP32 copy of K0out
+    float *Pout;               // mixed path: pressure of K0out
     long long K;
     double A, B, dt;
     double gm1;                // gamma - 1 in FP64 for the pressure

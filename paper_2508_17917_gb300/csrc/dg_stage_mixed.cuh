@@ -1,21 +1,22 @@
 // dg_stage_mixed.cuh -- fused residual + LSRK stage, mixed precision.
 //
 // Same method and phase structure as dg_stage.cuh (strong-form residual of
-// Eq. dg_on_K and one stage of Algorithm 1), organised for GB300's FP32 and
-// integer pipes:
-//   * the state stays FP64 in HBM; a warp copies one 4*Np-double segment
-//     (own element or one neighbour) with 16-byte loads and converts it to
-//     FP32 by integer operations (cvt_d2f_trunc);
-//   * shared memory holds node-major float4 records (rho, m1, m2, E), so one
-//     LDS.128 feeds all four fields of a node; Dr and Ds are interleaved as
-//     float2 so one LDS.64 feeds both derivative directions;
-//   * the raw FP64 energies of the own element and of the neighbours stay in
-//     shared memory for the FP64 pressure recovery, the raw own state for the
-//     FP64 register update, and the tile's K1 block arrives by cp.async while
-//     the other phases run;
+// Eq. dg_on_K and one stage of Algorithm 1), organised for GB300:
+//   * the state and the Runge-Kutta register stay FP64 in HBM; every stage
+//     also writes an FP32 copy of its output state (node-major float4 records
+//     rho, m1, m2, E) and the node pressure, recovered in FP64 from the FP64
+//     energy (p = (gamma-1)(E - rho|v|^2/2), Sec. 2.1) once per node;
+//   * the next stage stages everything it reads -- own and neighbour FP32
+//     records and pressures, the own FP64 state and K1 block, geometry --
+//     with asynchronous 16-byte copies (cp.async), so no thread converts or
+//     waits on a global load in the staging phase;
+//   * node-major float4 records feed all four fields of a node with one
+//     LDS.128; Dr and Ds are interleaved as 8-byte float2 records;
 //   * the volume phase keeps the total flux F = F_c - v_w U - G grad U of
-//     every node, so a face node takes F+.n from it instead of re-evaluating
-//     the own side's advective and viscous fluxes.
+//     every node, so a face node reads F+.n instead of re-evaluating it;
+//   * FP64 arithmetic is left to the pressure recovery and the register
+//     update; FP64<->FP32 conversions are done with integer operations,
+//     because GB300 executes conversion instructions on its FP64 pipe.
 #pragma once
 #include "dg_stage.cuh"
 
@@ -42,29 +43,34 @@ __device__ __forceinline__ void acc_rs(float r[4], float s[4], const float2 d, c
     s[0] = fmaf(d.y, u.x, s[0]); s[1] = fmaf(d.y, u.y, s[1]); s[2] = fmaf(d.y, u.z, s[2]); s[3] = fmaf(d.y, u.w, s[3]);
 }
 
+__device__ __forceinline__ void cp_async16(unsigned dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+}
+
 template <int P>
 struct MixedLayout {
     using S = Shape<P>;
     static constexpr int Np = S::Np, NF = S::NF, E = S::E;
+    static constexpr int NpP = (Np + 3) & ~3;                                 // padded pressure row
     static constexpr size_t al(size_t b) { return (b + 15) & ~size_t(15); }
-    static constexpr size_t oD = 0;                                      // float2 Np*Np (Dr, Ds)
-    static constexpr size_t oL = oD + al(sizeof(float2) * Np * Np);      // float Np*NF
-    static constexpr size_t oFm = oL + al(sizeof(float) * Np * NF);      // int NF
-    static constexpr size_t oConn = oFm + al(sizeof(int) * NF);          // int4 E
-    static constexpr size_t oGeo = oConn + al(sizeof(int4) * E);         // float E*16
-    static constexpr size_t oNGeo = oGeo + al(sizeof(float) * E * 16);   // float4 E*3*2
-    static constexpr size_t oU = oNGeo + al(sizeof(float4) * E * 3 * 2); // float4 E*Np
-    static constexpr size_t oN = oU + al(sizeof(float4) * E * Np);       // float4 E*3*Np
-    static constexpr size_t oRaw = oN + al(sizeof(float4) * E * 3 * Np); // double E*4*Np
-    static constexpr size_t oNEd = oRaw + al(sizeof(double) * E * 4 * Np);  // double E*3*Np
-    static constexpr size_t oF = oNEd + al(sizeof(double) * E * 3 * Np);    // float4 E*Np*2
-    static constexpr size_t oP = oF + al(sizeof(float4) * E * Np * 2);      // float E*Np
-    static constexpr size_t oNorm = oP + al(sizeof(float) * E * Np);        // float E*NF
-    static constexpr size_t oDH = oNorm + al(sizeof(float) * E * NF);       // float4 E*NF
-    static constexpr size_t oK1 = oDH + al(sizeof(float4) * E * NF);        // double E*4*Np
-    static constexpr size_t oFxy = oK1 + al(sizeof(double) * E * 4 * Np);   // float4 E*Np*2
-    static constexpr size_t oNed = oFxy + al(sizeof(float4) * E * Np * 2);  // double scratch slot
-    static constexpr size_t bytes = oNed + 16;
+    static constexpr size_t oD = 0;                                           // float2 Np*Np (Dr, Ds)
+    static constexpr size_t oL = oD + al(sizeof(float2) * Np * Np);           // float Np*NF
+    static constexpr size_t oFm = oL + al(sizeof(float) * Np * NF);           // int NF
+    static constexpr size_t oConn = oFm + al(sizeof(int) * NF);               // int4 E
+    static constexpr size_t oGeo = oConn + al(sizeof(int4) * E);              // float E*16
+    static constexpr size_t oNGeo = oGeo + al(sizeof(float) * E * 16);        // float E*3*16
+    static constexpr size_t oU = oNGeo + al(sizeof(float) * E * 3 * 16);      // float4 E*Np
+    static constexpr size_t oN = oU + al(sizeof(float4) * E * Np);            // float4 E*3*Np
+    static constexpr size_t oPo = oN + al(sizeof(float4) * E * 3 * Np);       // float E*NpP
+    static constexpr size_t oPn = oPo + al(sizeof(float) * E * NpP);          // float E*3*NpP
+    static constexpr size_t oRaw = oPn + al(sizeof(float) * E * 3 * NpP);     // double E*4*Np
+    static constexpr size_t oK1 = oRaw + al(sizeof(double) * E * 4 * Np);     // double E*4*Np
+    static constexpr size_t oF = oK1 + al(sizeof(double) * E * 4 * Np);       // float4 E*Np*2 (Fr, Fs)
+    static constexpr size_t oFxy = oF + al(sizeof(float4) * E * Np * 2);      // float4 E*Np*2 (Fx, Fy)
+    static constexpr size_t oNorm = oFxy + al(sizeof(float4) * E * Np * 2);   // float E*NF
+    static constexpr size_t oDH = oNorm + al(sizeof(float) * E * NF);         // float4 E*NF
+    static constexpr size_t bytes = oDH + al(sizeof(float4) * E * NF);
 };
 
 __device__ __forceinline__ void f4_to(const float4 &a, float o[4]) { o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; }
@@ -77,27 +83,27 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
     using S = Shape<P>;
     using L = MixedLayout<P>;
     constexpr int Np = S::Np, Nfp = S::Nfp, NF = S::NF, E = S::E, NT = S::NT;
-    constexpr int NW = NT / 32;
+    constexpr int NpP = L::NpP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *sD = reinterpret_cast<float2 *>(smem_raw + L::oD);
     float *sL = reinterpret_cast<float *>(smem_raw + L::oL);
     int *sFm = reinterpret_cast<int *>(smem_raw + L::oFm);
     int4 *sConn = reinterpret_cast<int4 *>(smem_raw + L::oConn);
     float *sGeo = reinterpret_cast<float *>(smem_raw + L::oGeo);
-    float4 *sNGeo = reinterpret_cast<float4 *>(smem_raw + L::oNGeo);
+    float *sNGeo = reinterpret_cast<float *>(smem_raw + L::oNGeo);
     float4 *sU = reinterpret_cast<float4 *>(smem_raw + L::oU);
     float4 *sN = reinterpret_cast<float4 *>(smem_raw + L::oN);
+    float *sPo = reinterpret_cast<float *>(smem_raw + L::oPo);
+    float *sPn = reinterpret_cast<float *>(smem_raw + L::oPn);
     double *sRaw = reinterpret_cast<double *>(smem_raw + L::oRaw);
-    double *sNEd = reinterpret_cast<double *>(smem_raw + L::oNEd);
+    double *sK1 = reinterpret_cast<double *>(smem_raw + L::oK1);
     float4 *sF = reinterpret_cast<float4 *>(smem_raw + L::oF);
-    float *sP = reinterpret_cast<float *>(smem_raw + L::oP);
+    float4 *sFxy = reinterpret_cast<float4 *>(smem_raw + L::oFxy);
     float *sNorm = reinterpret_cast<float *>(smem_raw + L::oNorm);
     float4 *sDH = reinterpret_cast<float4 *>(smem_raw + L::oDH);
-    double *sK1 = reinterpret_cast<double *>(smem_raw + L::oK1);
-    float4 *sFxy = reinterpret_cast<float4 *>(smem_raw + L::oFxy);
-    double *sDummy = reinterpret_cast<double *>(smem_raw + L::oNed);
+    const unsigned sbase = static_cast<unsigned>(__cvta_generic_to_shared(smem_raw));
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     {
         const float *ops = static_cast<const float *>(sp.ops);   // Dr | Ds | LIFT
         for (int i = tid; i < Np * Np; i += NT) sD[i] = make_float2(ops[i], ops[Np * Np + i]);
@@ -105,26 +111,14 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
         for (int i = tid; i < NF; i += NT) sFm[i] = sp.fmask[i];
     }
     const float *geo = static_cast<const float *>(sp.geo);
-    const double *K0 = sp.K0in;
     const long long K = sp.K;
     const long long ntiles = (K + E - 1) / E;
     const double gm1d = sp.gm1;
     const float cinv_fac = 0.5f * float(P + 1) * float(P + 2);
     const float C1x3 = 3.0f * static_cast<float>(sp.C1);
     const float dtr = static_cast<float>(sp.dt);
-
-    // per-lane chunk decomposition of a 4*Np segment: chunk ch holds doubles
-    // 2ch, 2ch+1 of the [c][node] segment
-    constexpr int NCH = 2 * Np;
-    constexpr int NIT = (NCH + 31) / 32;
-    int ch_c0[NIT], ch_j0[NIT], ch_c1[NIT], ch_j1[NIT];
-#pragma unroll
-    for (int it = 0; it < NIT; ++it) {
-        int ch = lane + 32 * it;
-        int q = 2 * ch;
-        ch_c0[it] = q / Np; ch_j0[it] = q - (q / Np) * Np;
-        ch_c1[it] = (q + 1) / Np; ch_j1[it] = (q + 1) - ((q + 1) / Np) * Np;
-    }
+    const bool update = sp.mode == STAGE_UPDATE;
+    const bool need_k1 = update && !sp.first_stage;
     __syncthreads();
 
     const int ve = tid / Np, vi = tid - (tid / Np) * Np;
@@ -134,63 +128,48 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const long long k0 = tile * E;
         const int ne = static_cast<int>((K - k0) < E ? (K - k0) : E);
-        // ---- P1a: connectivity and own geometry of the tile
+        // ---- P1a: connectivity of the tile (needed to address the neighbours)
         if (tid < ne) sConn[tid] = sp.conn[k0 + tid];
-        for (int idx = tid; idx < ne * 16; idx += NT) sGeo[idx] = geo[k0 * 16 + idx];
         __syncthreads();
-        // ---- P1b: K1 block by asynchronous copies; own and neighbour state segments
-        const bool need_k1 = (sp.mode == STAGE_UPDATE) && !sp.first_stage;
-        if (need_k1) {
-            const char *g = reinterpret_cast<const char *>(sp.K1 + k0 * 4 * Np);
-            const unsigned s0 = static_cast<unsigned>(__cvta_generic_to_shared(sK1));
-            for (int ch = tid; ch < ne * 2 * Np; ch += NT)
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s0 + 16u * ch),
-                             "l"(g + 16 * ch));
+        // ---- P1b: asynchronous 16-byte copies of everything the tile reads
+        {
+            // own FP32 records, own pressures, own FP64 state, K1, own geometry
+            const char *gU = reinterpret_cast<const char *>(sp.Sin + k0 * Np);
+            for (int c = tid; c < ne * Np; c += NT) cp_async16(sbase + L::oU + 16u * c, gU + 16 * c);
+            const char *gP = reinterpret_cast<const char *>(sp.Pin + k0 * NpP);
+            for (int c = tid; c < ne * (NpP / 4); c += NT) cp_async16(sbase + L::oPo + 16u * c, gP + 16 * c);
+            const char *gR = reinterpret_cast<const char *>(sp.K0in + k0 * 4 * Np);
+            for (int c = tid; c < ne * 2 * Np; c += NT) cp_async16(sbase + L::oRaw + 16u * c, gR + 16 * c);
+            if (need_k1) {
+                const char *gK = reinterpret_cast<const char *>(sp.K1 + k0 * 4 * Np);
+                for (int c = tid; c < ne * 2 * Np; c += NT) cp_async16(sbase + L::oK1 + 16u * c, gK + 16 * c);
+            }
+            const char *gG = reinterpret_cast<const char *>(geo + k0 * 16);
+            for (int c = tid; c < ne * 4; c += NT) cp_async16(sbase + L::oGeo + 16u * c, gG + 16 * c);
+            // neighbour FP32 records, pressures and geometry records
+            for (int c = tid; c < ne * 3 * Np; c += NT) {
+                const int seg = c / Np, j = c - (c / Np) * Np;
+                const int4 cn = sConn[seg / 3];
+                const int f = seg - 3 * (seg / 3);
+                const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
+                cp_async16(sbase + L::oN + 16u * c, sp.Sin + nb * Np + j);
+            }
+            for (int c = tid; c < ne * 3 * (NpP / 4); c += NT) {
+                const int seg = c / (NpP / 4), q = c - (c / (NpP / 4)) * (NpP / 4);
+                const int4 cn = sConn[seg / 3];
+                const int f = seg - 3 * (seg / 3);
+                const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
+                cp_async16(sbase + L::oPn + 16u * c, sp.Pin + nb * NpP + 4 * q);
+            }
+            for (int c = tid; c < ne * 3 * 4; c += NT) {
+                const int seg = c >> 2, q = c & 3;
+                const int4 cn = sConn[seg / 3];
+                const int f = seg - 3 * (seg / 3);
+                const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
+                cp_async16(sbase + L::oNGeo + 16u * c, geo + nb * 16 + 4 * q);
+            }
             asm volatile("cp.async.commit_group;\n" ::);
-        }
-        for (int e = warp; e < ne; e += NW) {
-            const double2 *g2 = reinterpret_cast<const double2 *>(K0 + (k0 + e) * (4 * Np));
-            float *dstf = reinterpret_cast<float *>(sU + e * Np);
-            double2 *raw = reinterpret_cast<double2 *>(sRaw + e * 4 * Np);
-#pragma unroll
-            for (int it = 0; it < NIT; ++it) {
-                const int ch = lane + 32 * it;
-                if (ch < NCH) {
-                    const double2 v = __ldg(g2 + ch);
-                    dstf[ch_j0[it] * 4 + ch_c0[it]] = cvt_d2f_trunc(v.x);
-                    dstf[ch_j1[it] * 4 + ch_c1[it]] = cvt_d2f_trunc(v.y);
-                    raw[ch] = v;
-                }
-            }
-        }
-        for (int seg = warp; seg < ne * 3; seg += NW) {
-            const int e = seg / 3, f = seg - 3 * (seg / 3);
-            const int4 cn = sConn[e];
-            const long long src = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
-            const double2 *g2 = reinterpret_cast<const double2 *>(K0 + src * (4 * Np));
-            float *dstf = reinterpret_cast<float *>(sN + seg * Np);
-            double *ned = sNEd + seg * Np;
-#pragma unroll
-            for (int it = 0; it < NIT; ++it) {
-                const int ch = lane + 32 * it;
-                if (ch < NCH) {
-                    const double2 v = __ldg(g2 + ch);
-                    dstf[ch_j0[it] * 4 + ch_c0[it]] = cvt_d2f_trunc(v.x);
-                    dstf[ch_j1[it] * 4 + ch_c1[it]] = cvt_d2f_trunc(v.y);
-                    // raw energies for the FP64 pressure; other fields go to a dummy slot
-                    *((ch_c0[it] == 3) ? ned + ch_j0[it] : sDummy) = v.x;
-                    *((ch_c1[it] == 3) ? ned + ch_j1[it] : sDummy) = v.y;
-                }
-            }
-        }
-        if (tid < ne * 3) {
-            const int e = tid / 3, f = tid - 3 * (tid / 3);
-            const int4 cn = sConn[e];
-            const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
-            const int f2 = (cn.w >> (2 * f)) & 3;
-            const float4 m = *reinterpret_cast<const float4 *>(geo + nb * 16);
-            sNGeo[tid * 2] = m;                                   // rx, ry, sx, sy
-            sNGeo[tid * 2 + 1] = make_float4(geo[nb * 16 + G_FS + f2], 0.f, 0.f, 0.f);
+            asm volatile("cp.async.wait_group 0;\n" ::);
         }
         __syncthreads();
 
@@ -210,8 +189,7 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
                 gx[c] = rx * ur[c] + sx * us[c];
                 gy[c] = ry * ur[c] + sy * us[c];
             }
-            const float p = pressure<float>(u, sRaw[(ve * 4 + 3) * Np + vi], gm1d);
-            sP[ve * Np + vi] = p;
+            const float p = sPo[ve * NpP + vi];
             float cx[4], cy[4], vx[4], vy[4], fr[4], fs[4], Fx[4], Fy[4];
             adv_flux(u, p, ph, cx, cy);
             visc_flux(u, gx, gy, ph, vx, vy);
@@ -251,7 +229,7 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
                 const float iw = 1.0f / ph.Uinf[0];
                 b = penalty_norm(ph.Uinf[0], ph.Uinf[1] * iw, ph.Uinf[2] * iw, ph.Uinf[3] * iw, n1, n2, ph);
             } else {
-                const float pw = pressure<float>(u, sRaw[(fe * 4 + 3) * Np + vm], gm1d);
+                const float pw = sPo[fe * NpP + vm];
                 const float eb = (pw / ph.gm1 + 0.5f * u[0] * (ph.vw1 * ph.vw1 + ph.vw2 * ph.vw2)) * ir;
                 b = penalty_norm(u[0], ph.vw1, ph.vw2, eb, n1, n2, ph);
             }
@@ -260,7 +238,7 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
         __syncthreads();
 
         // ---- P3: divergence (volume) and face fluxes (face nodes)
-        float Dv[4] = {0, 0, 0, 0};       // divergence sum_j Dr_ij Fr_j + Ds_ij Fs_j
+        float Dv[4] = {0, 0, 0, 0};       // sum_j Dr_ij Fr_j + Ds_ij Fs_j
         if (vol) {
             const float4 *fe4 = sF + ve * Np * 2;
 #pragma unroll
@@ -280,11 +258,15 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
 #pragma unroll
             for (int l = 0; l < Nfp; ++l) gbar = fmaxf(gbar, sNorm[fe * NF + ff * Nfp + l]);
             float cinv = cinv_fac * fsc;
-            if (btype == BCT_INTERIOR) cinv = fmaxf(cinv, cinv_fac * sNGeo[(fe * 3 + ff) * 2 + 1].x);
+            const float *ng = sNGeo + (fe * 3 + ff) * 16;     // neighbour's geometry record
+            if (btype == BCT_INTERIOR) {
+                const int f2 = (sConn[fe].w >> (2 * ff)) & 3;
+                cinv = fmaxf(cinv, cinv_fac * ng[G_FS + f2]);
+            }
             const float sigma = C1x3 * gbar * cinv;
             float up[4], dH[4], Ftp[4];
             f4_to(sU[fe * Np + vm], up);
-            const float pp = sP[fe * Np + vm];
+            const float pp = sPo[fe * NpP + vm];
             {   // F+.n of the total flux F = F_c - v_w U - G grad U, from the volume phase
                 const float4 a = sFxy[(fe * Np + vm) * 2], b = sFxy[(fe * Np + vm) * 2 + 1];
                 Ftp[0] = a.x * n1 + b.x * n2; Ftp[1] = a.y * n1 + b.y * n2;
@@ -295,15 +277,14 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
                 float wr[4] = {0, 0, 0, 0}, ws[4] = {0, 0, 0, 0};
 #pragma unroll
                 for (int j = 0; j < Np; ++j) acc_rs(wr, ws, sD[vp * Np + j], w[j]);
-                const float4 nm0 = sNGeo[(fe * 3 + ff) * 2];
                 float um[4], gxm[4], gym[4];
                 f4_to(w[vp], um);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    gxm[c] = nm0.x * wr[c] + nm0.z * ws[c];
-                    gym[c] = nm0.y * wr[c] + nm0.w * ws[c];
+                    gxm[c] = ng[G_RX] * wr[c] + ng[G_SX] * ws[c];
+                    gym[c] = ng[G_RY] * wr[c] + ng[G_SY] * ws[c];
                 }
-                const float pm = pressure<float>(um, sNEd[(fe * 3 + ff) * Np + vp], gm1d);
+                const float pm = sPn[(fe * 3 + ff) * NpP + vp];
                 float Fnm[4], vxm[4], vym[4], D[4];
                 flux_n(um, pm, n1, n2, ph, Fnm);
                 visc_flux(um, gxm, gym, ph, vxm, vym);
@@ -351,10 +332,9 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
             }
             sDH[fe * NF + fm] = make_float4(fsc * dH[0], fsc * dH[1], fsc * dH[2], fsc * dH[3]);
         }
-        if (need_k1) asm volatile("cp.async.wait_group 0;\n" ::);
         __syncthreads();
 
-        // ---- P4: lift and the stage update
+        // ---- P4: lift, the stage update and the FP32 copy of the new state
         if (vol) {
             const float4 *dh = sDH + ve * NF;
             float R[4] = {-Dv[0], -Dv[1], -Dv[2], -Dv[3]};
@@ -369,20 +349,45 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) R[c] += cvt_d2f(sp.src[base + c * Np]);
             }
-            if (sp.mode == STAGE_RHS_ONLY) {
+            if (!update) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) sp.Rout[base + c * Np] = cvt_f2d(R[c]);
             } else {
+                double knew[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const double inc = cvt_f2d(dtr * R[c]);
                     const double k1 = sp.first_stage ? inc : fma(sp.A, sK1[(ve * 4 + c) * Np + vi], inc);
                     sp.K1[base + c * Np] = k1;
-                    sp.K0out[base + c * Np] = fma(sp.B, k1, sRaw[(ve * 4 + c) * Np + vi]);
+                    knew[c] = fma(sp.B, k1, sRaw[(ve * 4 + c) * Np + vi]);
+                    sp.K0out[base + c * Np] = knew[c];
                 }
+                // FP32 copy of the new state and its pressure, recovered in FP64
+                const float un[4] = {cvt_d2f_trunc(knew[0]), cvt_d2f_trunc(knew[1]),
+                                     cvt_d2f_trunc(knew[2]), cvt_d2f_trunc(knew[3])};
+                sp.Sout[(k0 + ve) * Np + vi] = to_f4(un);
+                sp.Pout[(k0 + ve) * NpP + vi] = pressure<float>(un, knew[3], gm1d);
             }
         }
     }
+}
+
+// FP32 copy and FP64-recovered pressure of a state (used when the state is
+// set from outside the stage kernel).
+template <int P>
+__global__ void make_shadow_kernel(const double *K0, long long K, double gm1, float4 *S, float *Pr)
+{
+    constexpr int Np = (P + 1) * (P + 2) / 2, NpP = (Np + 3) & ~3;
+    const long long n = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (n >= K * Np) return;
+    const long long k = n / Np;
+    const int i = static_cast<int>(n - k * Np);
+    double d[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) d[c] = K0[(k * 4 + c) * Np + i];
+    const float u[4] = {cvt_d2f_trunc(d[0]), cvt_d2f_trunc(d[1]), cvt_d2f_trunc(d[2]), cvt_d2f_trunc(d[3])};
+    S[k * Np + i] = to_f4(u);
+    Pr[k * NpP + i] = pressure<float>(u, d[3], gm1);
 }
 
 }  // namespace dg

@@ -24,6 +24,11 @@ cudaError_t launch_stage_fp64(int p, const LaunchShape &ls, const StageParams &s
                               const Phys<double> &ph, cudaStream_t st);
 cudaError_t launch_stage_mixed(int p, const LaunchShape &ls, const StageParams &sp,
                                const Phys<float> &ph, cudaStream_t st);
+// FP32 copy [K][Np] float4 and FP64-recovered pressure [K][NpP] of a state
+cudaError_t launch_make_shadow(int p, const double *K0, long long K, double gm1, float4 *S,
+                               float *Pr, cudaStream_t st);
+// padded pressure row length: Np rounded up to a multiple of 4
+inline int pressure_row(int p) { return (((p + 1) * (p + 2) / 2) + 3) & ~3; }
 
 struct AuxMesh {
     const double *U;          // [K][4][Np]

@@ -38,6 +38,16 @@ cudaError_t launch_p(const LaunchShape &ls, const StageParams &sp, const Phys<fl
     return cudaGetLastError();
 }
 
+template <int P>
+cudaError_t shadow_p(const double *K0, long long K, double gm1, float4 *S, float *Pr, cudaStream_t st)
+{
+    constexpr int Np = (P + 1) * (P + 2) / 2;
+    const long long n = K * Np;
+    const int threads = 256;
+    make_shadow_kernel<P><<<static_cast<unsigned>((n + threads - 1) / threads), threads, 0, st>>>(K0, K, gm1, S, Pr);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 #define DG_SWITCH_P(p, CALL)                      \
@@ -62,6 +72,14 @@ cudaError_t launch_stage_mixed(int p, const LaunchShape &ls, const StageParams &
                                const Phys<float> &ph, cudaStream_t st)
 {
 #define C_(P) launch_p<P>(ls, sp, ph, st)
+    DG_SWITCH_P(p, C_)
+#undef C_
+}
+
+cudaError_t launch_make_shadow(int p, const double *K0, long long K, double gm1, float4 *S, float *Pr,
+                               cudaStream_t st)
+{
+#define C_(P) shadow_p<P>(K0, K, gm1, S, Pr, st)
     DG_SWITCH_P(p, C_)
 #undef C_
 }
