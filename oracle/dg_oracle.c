@@ -16,7 +16,11 @@
  *   - broken gradient grad_h U = (rx Dr + sx Ds, ry Dr + sy Ds) U;
  *   - Roe flux with moving-wall eigenvalues, built as R |Lambda| R^-1 with an
  *     explicit eigenvector matrix and a Gauss-Jordan inverse (Eq. roe_flux);
- *   - interior-penalty diffusion flux, theta = 0 (Eq. ip_flux);
+ *   - interior-penalty diffusion flux for theta in [-1, 1] (Eq. ip_flux): the
+ *     consistency and penalty terms through the face flux H_m, and the theta
+ *     term H_theta of Eq. dg_on_K tested against grad l_i on the face, with
+ *     weight 1/2 (the average) on interior faces and 1 on boundary faces,
+ *     G taken at U+ (interior, far field) or at the wall state U^b;
  *   - penalty sigma_e = C1 (1+theta)^2 (d+1) Gbar_e max C_inv (Eq.
  *     penalty_final) with Gbar_e the largest spectral norm of
  *     N G N^T = n1^2 G11 + n1 n2 (G12+G21) + n2^2 G22 over the face nodes of
@@ -31,8 +35,9 @@
  *
  * Readings where the paper is garbled or silent (pressure law, Roe factor
  * 1/2 and eigenvalue signs, boundary-face penalty, adiabatic heat flux, CFL
- * constants) are listed in the project's design notes and repeated next to
- * the code that takes them.
+ * constants, which side's G the theta term uses on far-field faces) are
+ * listed in the project's design notes and repeated next to the code that
+ * takes them.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -511,16 +516,36 @@ void oracle_manufactured_source(double x, double y, double kappa, double C2, dou
          + 2.0 * gamma * mu * kappa * kappa * sp / Pr;
 }
 
+/* theta term of the IP flux (Eq. ip_flux, H_theta of Eq. dg_on_K) at one face
+ * node: the 8-vector (U+ - U-)^T N G(U*) with N = n^T (x) I4, i.e.
+ * t_x[k] = sum_c dU_c (n1 G11 + n2 G21)_{c,k},  t_y[k] = sum_c dU_c (n1 G12 + n2 G22)_{c,k},
+ * G evaluated at Ustar (U+ on interior and far-field faces, U^b on walls). */
+static void theta_vector(const double dU[4], const double Ustar[4], const double n[2], double gamma,
+                         double Pr, double mu, double tx[4], double ty[4])
+{
+    double G[2][2][16];
+    oracle_G_blocks(Ustar, gamma, Pr, mu, G);
+    for (int k = 0; k < 4; ++k) {
+        double ax = 0, ay = 0;
+        for (int c = 0; c < 4; ++c) {
+            ax += dU[c] * (n[0] * G[0][0][4 * c + k] + n[1] * G[1][0][4 * c + k]);
+            ay += dU[c] * (n[0] * G[0][1][4 * c + k] + n[1] * G[1][1][4 * c + k]);
+        }
+        tx[k] = ax;
+        ty[k] = ay;
+    }
+}
+
 /* ---------------------------------------------------------------- residual */
 
-/* R = M^-1 [ (S_x F_x + S_y F_y) - sum_e E^e M_e H ]  (Eq. dg_on_K), theta = 0.
+/* R = M^-1 [ (S_x F_x + S_y F_y) - S_x H_theta,x - S_y H_theta,y - sum_e E^e M_e H_m ]
+ * (Eq. dg_on_K); H_theta = -theta (U+ - U-)^T N G grad l_i, so its terms enter with +theta.
  * U, R: [K][4][Np]. */
 int oracle_rhs(const oracle_problem *P, const double *U, double t, const double vw[2], double *R)
 {
     (void)t;
     int Np = P->Np, Nfp = P->Nfp;
     long long K = P->K;
-    if (P->theta != 0.0) return -6;
     size_t nd = (size_t)K * 4 * Np;
     double *Ux = malloc(nd * sizeof(double)), *Uy = malloc(nd * sizeof(double));
     if (!Ux || !Uy) { free(Ux); free(Uy); return -1; }
@@ -544,6 +569,9 @@ int oracle_rhs(const oracle_problem *P, const double *U, double t, const double 
         /* face terms q_i = sum_e E^e (M_e H)_i, with M_e = sJ * M1D */
         double q[4][32];
         memset(q, 0, sizeof q);
+        /* theta terms: th[c][i] = theta w int_e (dx l_i t_x[c] + dy l_i t_y[c]) ds */
+        double th[4][32];
+        memset(th, 0, sizeof th);
         for (int f = 0; f < 3; ++f) {
             double Up[8][4], Upx[8][4], Upy[8][4], Uo[8][4], Uox[8][4], Uoy[8][4], H[8][4];
             face_traces(P, U, Ux, Uy, vw, k, f, Up, Upx, Upy, Uo, Uox, Uoy);
@@ -562,6 +590,35 @@ int oracle_rhs(const oracle_problem *P, const double *U, double t, const double 
                     for (int l = 0; l < Nfp; ++l) acc += M1[i * Nfp + l] * H[l][c];
                     q[c][vm] += sJ * acc;
                 }
+            }
+            if (P->theta != 0.0) {
+                /* w = 1/2 from the average {{G grad Phi}} on interior faces, 1 on boundary
+                 * faces; G at U+ (interior, far field) or at the wall state U^b */
+                double w = (btype == BC_INTERIOR) ? 0.5 : 1.0;
+                double tx[8][4], ty[8][4];
+                for (int l = 0; l < Nfp; ++l) {
+                    double dU[4];
+                    for (int c = 0; c < 4; ++c) dU[c] = Up[l][c] - Uo[l][c];
+                    const double *Ustar = (btype == BC_WALL) ? Uo[l] : Up[l];
+                    theta_vector(dU, Ustar, n, P->gamma, P->Pr, P->mu, tx[l], ty[l]);
+                }
+                /* int_e f g ds = sJ f^T M1D g for face polynomials f, g; g = d l_i / dx at
+                 * the face nodes, from the rows of Dr, Ds at those nodes */
+                double rx = P->rx[k], ry = P->ry[k], sx = P->sx[k], sy = P->sy[k];
+                for (int ii = 0; ii < Np; ++ii)
+                    for (int m = 0; m < Nfp; ++m) {
+                        long long vm = P->Fmask[f * Nfp + m];
+                        double dxl = rx * P->Dr[vm * Np + ii] + sx * P->Ds[vm * Np + ii];
+                        double dyl = ry * P->Dr[vm * Np + ii] + sy * P->Ds[vm * Np + ii];
+                        for (int c = 0; c < 4; ++c) {
+                            double fx = 0, fy = 0;
+                            for (int l = 0; l < Nfp; ++l) {
+                                fx += M1[m * Nfp + l] * tx[l][c];
+                                fy += M1[m * Nfp + l] * ty[l][c];
+                            }
+                            th[c][ii] += P->theta * w * sJ * (dxl * fx + dyl * fy);
+                        }
+                    }
             }
         }
         /* weak volume term (Dr^T M F) scaled by the metric, then M^-1 */
@@ -582,8 +639,8 @@ int oracle_rhs(const oracle_problem *P, const double *U, double t, const double 
                 for (int j = 0; j < Np; ++j)
                     acc += (rx * P->Dr[j * Np + m] + sx * P->Ds[j * Np + m]) * a[j]
                          + (ry * P->Dr[j * Np + m] + sy * P->Ds[j * Np + m]) * b[j];
-                /* (1/J) M^-1 of [ J * vol - face ] */
-                vol[m] = acc - q[c][m] / J;
+                /* (1/J) M^-1 of [ J * vol - face + theta terms ] */
+                vol[m] = acc - q[c][m] / J + th[c][m] / J;
             }
             for (int i = 0; i < Np; ++i) {
                 double acc = 0;
