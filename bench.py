@@ -45,6 +45,15 @@ GEO_BYTES_MIXED = 64 + 16
 GEO_BYTES_FP64 = 128 + 16
 
 
+K_BENCH = 2 * 128 * 128
+CONFIG = {"workload": "isentropic vortex, p=4 (Np=15), periodic [0,10]^2, 128x128 quads "
+                      "split SW-NE (K=32768), mu=1e-3, CFL 0.3, 5-stage 2N-storage RK",
+          "K": K_BENCH, "p": 4, "dofs": 4 * K_BENCH * 15,
+          "precision": "mixed (FP32 arithmetic; FP64 state, pressure, RK registers)",
+          "l2": "flushed (512 MB write) before every timed step; the 31 MB working set "
+                "stays in L2 across the 5 stages of a step"}
+
+
 def algorithmic_bytes_per_step(K, geo_bytes):
     dof = 4 * K * NP
     state = dof * (24 + 4 * 32)          # stage 1 skips the K1 read
@@ -53,7 +62,7 @@ def algorithmic_bytes_per_step(K, geo_bytes):
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("dg_stage.cuh", "dg_device.cuh", "stage_mixed.cu"):
+    for f in ("dg_stage.cuh", "dg_stage_mixed.cuh", "dg_device.cuh", "stage_mixed.cu"):
         with open(os.path.join(ROOT, "paper_2508_17917_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -229,13 +238,24 @@ def run_ours(args):
                 "frac": achieved / peak, "peak_kind": peak_kind,
                 "traffic": (traffic * dof * 5 / 5.0) if traffic is not None else None,
                 "algorithmic_bytes_per_launch": bytes_step / 5.0,
-                "kernel": "dg::stage_kernel<4, float>"}
+                "kernel": "dg::stage_mixed_kernel<4, false>"}
 
     # --- FP64 path, same workload
     s64, U64, dt64 = solvers["fp64"]
     s64.set_state(U64)
     t64, _ = timed_steps(dg, torch, s64, dt64, max(3, args.steps // 20), 2, flush, stream)
     v64 = dof * 5 * len(t64) / (sum(t64) * 1e-3)
+
+    # --- SIP variant (theta = 1, Eq. ip_flux), mixed path, same workload
+    ssip = dg.Solver(mesh, P, "mixed", stream=sh, mu=1e-3, theta=1.0, C1=0.05)
+    ssip.set_state(U0)
+    dts = ssip.dt(0.3)
+    ts, _ = timed_steps(dg, torch, ssip, dts, max(5, args.steps // 10), 2, flush, stream)
+    vs = dof * 5 * len(ts) / (sum(ts) * 1e-3)
+    sip = {"workload": "same mesh and state, SIP (theta = 1, C1 = 0.05)", "value": vs, "unit": UNIT,
+           "ms_per_step": sum(ts) / len(ts), "sip_over_iip": vs / (value / ws),
+           "kernel": "dg::stage_mixed_kernel<4, true>"}
+    del ssip
 
     # --- large variant (working set well above L2), mixed path
     large = None
@@ -286,17 +306,12 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic: seeded isentropic vortex on a periodic square",
-            "config": {"workload": "isentropic vortex, p=4 (Np=15), periodic [0,10]^2, 128x128 quads "
-                                   "split SW-NE (K=32768), mu=1e-3, CFL 0.3, 5-stage 2N-storage RK",
-                       "K": K, "p": P, "dofs": dof, "precision": "mixed (FP32 arithmetic; FP64 state, "
-                                                                "pressure, RK registers)",
-                       "l2": "flushed (512 MB write) before every timed step; the 31 MB working set "
-                             "stays in L2 across the 5 stages of a step",
-                       "parallelism": f"replicas x{ws}"},
+            "config": dict(CONFIG, parallelism=f"replicas x{ws}"),
             "roofline": roofline,
             "fp64_path": {"value": v64, "unit": UNIT, "ms_per_step": sum(t64) / len(t64),
                           "mixed_over_fp64": value / ws / v64},
             "large_mesh": large,
+            "sip_path": sip,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk.summary(),
@@ -308,9 +323,10 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def cpu_baseline(budget_s=20.0, steps=1):
-    """The oracle (plain FP64 C, OpenMP over elements) on the host cores: one
-    LSRK step of a periodic vortex mesh at p = 4, mesh sized to the budget."""
+def cpu_baseline(budget_s=20.0):
+    """The oracle (plain FP64 C, OpenMP over elements) on the host cores:
+    LSRK steps of the benchmark's own p = 4 vortex mesh (128 x 128 split
+    quads), as many as fit the time budget (at least one)."""
     import numpy as np
     import dg_inputs
     import oracle
@@ -318,17 +334,14 @@ def cpu_baseline(budget_s=20.0, steps=1):
     oracle.build_oracle()
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
-    # calibrate on a small mesh, then size the sample
-    m = dg_inputs.periodic_square(16)
-    Pq = oracle.Problem(m, P, mu=1e-3)
-    U = to_kcn(dg_inputs.isentropic_vortex(Pq.x, Pq.y))
-    t0 = time.perf_counter()
-    Pq.lsrk_step(U, 0.0, 1e-5)
-    per_elem = (time.perf_counter() - t0) / m.K
-    n = int(max(16, min(128, (budget_s / max(per_elem, 1e-9) / 2 / steps) ** 0.5)))
+    n = 128
     m = dg_inputs.periodic_square(n)
     Pq = oracle.Problem(m, P, mu=1e-3)
     U = to_kcn(dg_inputs.isentropic_vortex(Pq.x, Pq.y))
+    t0 = time.perf_counter()
+    U = Pq.lsrk_step(U, 0.0, 1e-5)                  # calibration step, untimed
+    per_step = time.perf_counter() - t0
+    steps = int(max(1, min(200, budget_s / max(per_step, 1e-6))))
     t0 = time.perf_counter()
     for _ in range(steps):
         U = Pq.lsrk_step(U, 0.0, 1e-5)
@@ -378,8 +391,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic: seeded isentropic vortex on a periodic square",
-            "config": {"workload": "isentropic vortex, p=4 (Np=15), periodic square, CPU sample",
-                       "K": m.K, "p": P},
+            "config": dict(CONFIG, parallelism="host cores, rank 0"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -392,11 +404,12 @@ def run_profile(args):
     import dg_inputs
     import paper_2508_17917_gb300 as dg
     from dg_inputs.states import to_kcn
-    prec, n = {"mixed512": ("mixed", 512), "mixed128": ("mixed", 128),
-               "fp64_128": ("fp64", 128)}[args.profile]
+    prec, n, theta = {"mixed512": ("mixed", 512, 0.0), "mixed128": ("mixed", 128, 0.0),
+                      "fp64_128": ("fp64", 128, 0.0), "sip128": ("mixed", 128, 1.0)}[args.profile]
     torch.cuda.set_device(0)
     mesh = vortex_problem(n)
-    s = dg.Solver(mesh, P, prec, stream=torch.cuda.current_stream().cuda_stream, mu=1e-3)
+    s = dg.Solver(mesh, P, prec, stream=torch.cuda.current_stream().cuda_stream, mu=1e-3,
+                  theta=theta, C1=0.05 if theta else 0.01)
     x, y = s.node_coords()
     s.set_state(dg_inputs.perturb(to_kcn(dg_inputs.isentropic_vortex(x, y)), seed=0))
     dt = s.dt(0.3)
@@ -416,7 +429,7 @@ def main():
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--profile", choices=["mixed512", "mixed128", "fp64_128"], default=None)
+    ap.add_argument("--profile", choices=["mixed512", "mixed128", "fp64_128", "sip128"], default=None)
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

@@ -66,7 +66,7 @@ typedef struct {
     int p;                       /* polynomial degree, 1..6 (Sec. 2.2)                   */
     int precision;               /* DG_PRECISION_FP64 or DG_PRECISION_MIXED              */
     double gamma, Pr, mu;        /* adiabatic index, Prandtl number, viscosity (Sec. 2.1) */
-    double theta;                /* IP variant (Eq. ip_flux); only 0 (IIP) is supported  */
+    double theta;                /* IP variant (Eq. ip_flux), -1..1: 1 SIP, 0 IIP, -1 NIPG */
     double C1;                   /* penalty constant of Eq. penalty_final                */
     double rho_inf, u_inf, v_inf, p_inf;   /* far-field state (Sec. 2.2, boundary term) */
     int adiabatic_zero_heatflux; /* 1: wall energy flux keeps only v_w.(tau n)           */
@@ -75,8 +75,13 @@ typedef struct {
 /* Create a context on the current CUDA device.  `cuda_stream` is a
  * cudaStream_t (NULL = legacy default stream).  Builds the reference
  * operators of degree params->p (Sec. 2.2, weak matrices) and uploads them.
- * Errors: DG_EINVAL (null, p out of range, gamma <= 1, mu < 0, ...),
- * DG_EUNSUPPORTED (theta != 0), DG_ECUDA.  *out is NULL on failure. */
+ * theta != 0 selects the kernel variant with the theta terms of Eq. dg_on_K
+ * (weight 1/2 on interior faces, 1 on boundary faces; G at U+ on interior
+ * and far-field faces, at the wall state on walls); the penalty is
+ * C1 (1+theta)^2 (d+1) Gbar_e max C_inv (Eq. penalty_final), so theta = -1
+ * has no penalty.
+ * Errors: DG_EINVAL (null, p out of range, gamma <= 1, mu < 0, theta outside
+ * [-1, 1], ...), DG_ECUDA.  *out is NULL on failure. */
 dg_status dg_create(const dg_params *params, void *cuda_stream, dg_ctx **out);
 
 /* Free the context and all its device memory.  NULL is accepted. */

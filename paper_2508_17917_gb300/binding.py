@@ -237,9 +237,9 @@ class Solver:
 
     def __init__(self, mesh, p, precision="fp64", stream=0, gamma=1.4, Pr=0.72, mu=1e-3,
                  C1=0.01, rho_inf=1.0, u_inf=1.0, v_inf=0.0, p_inf=1.0,
-                 adiabatic_zero_heatflux=1):
+                 adiabatic_zero_heatflux=1, theta=0.0):
         prec = {"fp64": DG_PRECISION_FP64, "mixed": DG_PRECISION_MIXED}[precision]
-        self.params = DgParams(p, prec, gamma, Pr, mu, 0.0, C1, rho_inf, u_inf, v_inf, p_inf,
+        self.params = DgParams(p, prec, gamma, Pr, mu, theta, C1, rho_inf, u_inf, v_inf, p_inf,
                                int(adiabatic_zero_heatflux))
         self.p, self.K = p, mesh.K
         self.Np = (p + 1) * (p + 2) // 2

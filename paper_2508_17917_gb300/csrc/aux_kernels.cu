@@ -19,7 +19,7 @@ __device__ __forceinline__ void load_node(const double *U, int Np, long long k, 
 // largest Gbar_e over the faces of K, sigma_K, C_inv,K the largest over its
 // faces, beta_K = max over nodes of |b_ns|_2, (b_ns)_j = |v_j - v_w,j| + c
 // (Eq. cfl_general), beta'_K = 0.
-__global__ void dt_lambda_kernel(AuxMesh m, Phys<double> ph, double C1, double *lam)
+__global__ void dt_lambda_kernel(AuxMesh m, Phys<double> ph, double sig_fac, double *lam)
 {
     long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     if (k >= m.K) return;
@@ -57,7 +57,7 @@ __global__ void dt_lambda_kernel(AuxMesh m, Phys<double> ph, double C1, double *
         double ci = pp * fs * 0.5;
         double cmax = ci;
         if (bt == BCT_INTERIOR) cmax = fmax(ci, pp * m.geo[nb * 16 + G_FS + f2] * 0.5);
-        double sig = 3.0 * C1 * gbar * cmax;
+        double sig = sig_fac * gbar * cmax;
         GK = fmax(GK, gbar);
         sigK = fmax(sigK, sig);
         ciK = fmax(ciK, ci);
@@ -179,12 +179,12 @@ __global__ void nonfinite_kernel(const double *x, long long n, int *flag)
 
 }  // namespace
 
-cudaError_t launch_dt_lambda(const AuxMesh &m, const Phys<double> &ph, double C1, double *lam,
+cudaError_t launch_dt_lambda(const AuxMesh &m, const Phys<double> &ph, double sig_fac, double *lam,
                              cudaStream_t st)
 {
     int threads = 128;
     long long blocks = (m.K + threads - 1) / threads;
-    dt_lambda_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(m, ph, C1, lam);
+    dt_lambda_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(m, ph, sig_fac, lam);
     return cudaGetLastError();
 }
 

@@ -162,6 +162,9 @@ void manufactured_source(double x, double y, double kappa, double C2, const dg_p
     S[3] = 2.0 * dEp + heat;                                 // minus div of heat flux -mu g/Pr kappa^2 sin
 }
 
+// C1 (1+theta)^2 (d+1) of Eq. penalty_final, d = 2
+double sigma_factor(const dg_params &p) { return p.C1 * (1.0 + p.theta) * (1.0 + p.theta) * 3.0; }
+
 dg_status run_stage(dg_ctx *c, int s, double t, double dt, const double vw[2], int mode,
                     const double *in, double *out, double *rout)
 {
@@ -182,7 +185,15 @@ dg_status run_stage(dg_ctx *c, int s, double t, double dt, const double vw[2], i
     sp.B = (s >= 0) ? kRkB[s] : 0.0;
     sp.dt = dt;
     sp.gm1 = c->prm.gamma - 1.0;
-    sp.C1 = c->prm.C1;
+    sp.sig_fac = sigma_factor(c->prm);
+    sp.theta = c->prm.theta;
+    {
+        const dg_params &q = c->prm;
+        sp.uinf[0] = q.rho_inf;
+        sp.uinf[1] = q.rho_inf * q.u_inf;
+        sp.uinf[2] = q.rho_inf * q.v_inf;
+        sp.uinf[3] = q.p_inf / (q.gamma - 1.0) + 0.5 * q.rho_inf * (q.u_inf * q.u_inf + q.v_inf * q.v_inf);
+    }
     sp.mode = mode;
     sp.first_stage = (s == 0) ? 1 : 0;
     (void)t;
@@ -244,7 +255,7 @@ dg_status dg_create(const dg_params *params, void *cuda_stream, dg_ctx **out)
         !(p.rho_inf > 0.0) || !(p.p_inf > 0.0) ||
         (p.precision != DG_PRECISION_FP64 && p.precision != DG_PRECISION_MIXED))
         return DG_EINVAL;
-    if (p.theta != 0.0) return DG_EUNSUPPORTED;
+    if (!(p.theta >= -1.0 && p.theta <= 1.0)) return DG_EINVAL;
     dg_ctx *c = new dg_ctx();
     c->prm = p;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -263,6 +274,8 @@ dg_status dg_create(const dg_params *params, void *cuda_stream, dg_ctx **out)
     o64.insert(o64.end(), c->ops.Dr.begin(), c->ops.Dr.end());
     o64.insert(o64.end(), c->ops.Ds.begin(), c->ops.Ds.end());
     o64.insert(o64.end(), c->ops.LIFT.begin(), c->ops.LIFT.end());
+    o64.insert(o64.end(), c->ops.Wr.begin(), c->ops.Wr.end());
+    o64.insert(o64.end(), c->ops.Ws.begin(), c->ops.Ws.end());
     std::vector<float> o32(o64.begin(), o64.end());
     if (c->ops64.alloc(o64.size()) != cudaSuccess || c->ops32.alloc(o32.size()) != cudaSuccess ||
         c->Dr64.alloc(Np * Np) != cudaSuccess || c->Ds64.alloc(Np * Np) != cudaSuccess ||
@@ -420,8 +433,9 @@ dg_status dg_set_mesh(dg_ctx *c, int64_t Nv, const double *vx, const double *vy,
     c->EToV.assign(EToV, EToV + K * 3);
     c->geo64h.swap(geo);
     c->source_kind = DG_SOURCE_NONE;
-    cudaError_t e = (c->prm.precision == DG_PRECISION_FP64) ? dg::stage_shape_fp64(c->prm.p, K, c->shape)
-                                                             : dg::stage_shape_mixed(c->prm.p, K, c->shape);
+    const bool th = c->prm.theta != 0.0;
+    cudaError_t e = (c->prm.precision == DG_PRECISION_FP64) ? dg::stage_shape_fp64(c->prm.p, K, th, c->shape)
+                                                             : dg::stage_shape_mixed(c->prm.p, K, th, c->shape);
     if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel configuration");
     return DG_OK;
 }
@@ -545,7 +559,7 @@ dg_status dg_compute_dt(dg_ctx *c, double cfl, const double vw[2], double *dt)
     c->err.clear();
     if (!dt || c->K < 1 || !(cfl > 0.0)) return fail(c, DG_EINVAL, "need dt pointer, mesh and cfl > 0");
     dg::Phys<double> ph = make_phys<double>(c->prm, vw);
-    DG_CUDA(c, dg::launch_dt_lambda(aux_mesh(c), ph, c->prm.C1, c->lam.ptr, c->stream));
+    DG_CUDA(c, dg::launch_dt_lambda(aux_mesh(c), ph, sigma_factor(c->prm), c->lam.ptr, c->stream));
     DG_CUDA(c, dg::launch_max_reduce(c->lam.ptr, c->K, c->scal.ptr, c->stream));
     c->launches += 2;
     double lam = 0.0;

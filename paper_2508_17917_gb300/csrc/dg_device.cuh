@@ -138,6 +138,43 @@ __device__ __forceinline__ void visc_flux(const real u[4], const real gx[4], con
     visc_flux_prim(u[0], u[1] * ir, u[2] * ir, u[3] * ir, gx, gy, ph, Fx, Fy);
 }
 
+// Theta term of the interior-penalty flux (Eq. ip_flux; H_theta of Eq.
+// dg_on_K) at one face node: t_l[k] = sum_j n_j (G_jl^T d)_k, l = x, y, for
+// the jump d = U+ - U- and G at (rho, v, e).  Because G(U) grad U is linear
+// in grad U, t_l[k] is d . (n . F_v) for the gradient that is the unit
+// vector e_k along x_l and zero along the other axis.  With a = (d1 + v1 d3,
+// d2 + v2 d3) weighting the momentum rows and d3 the energy row, a unit
+// gradient of field k gives the velocity gradient w = (dv1, dv2) and energy
+// gradient de along x_l:
+//   k = 0: w = -(v1, v2)/rho, de = -e/rho;  k = 1: w = (1/rho, 0);
+//   k = 2: w = (0, 1/rho);                  k = 3: de = 1/rho,
+// and d . (n . F_v) = w1 alpha_1 + w2 alpha_2 + de beta with the
+// coefficients below (Newtonian stress with the -2/3 div v term, heat flux
+// mu gamma/Pr grad(e - |v|^2/2)).
+template <typename real>
+__device__ __forceinline__ void theta_vec(real rho, real v1, real v2, real e, const real d[4],
+                                          real n1, real n2, const Phys<real> &ph, real tx[4], real ty[4])
+{
+    const real mu = ph.mu, kq = ph.mu * ph.gPr;
+    const real a1 = d[1] + v1 * d[3], a2 = d[2] + v2 * d[3];
+    const real sh = mu * (a1 * n2 + a2 * n1);
+    const real ax1 = mu * (real(4.0 / 3.0) * a1 * n1 - real(2.0 / 3.0) * a2 * n2) - kq * d[3] * n1 * v1;
+    const real ax2 = sh - kq * d[3] * n1 * v2;
+    const real bx = kq * d[3] * n1;
+    const real ay1 = sh - kq * d[3] * n2 * v1;
+    const real ay2 = mu * (real(4.0 / 3.0) * a2 * n2 - real(2.0 / 3.0) * a1 * n1) - kq * d[3] * n2 * v2;
+    const real by = kq * d[3] * n2;
+    const real ir = real(1) / rho;
+    tx[0] = -(v1 * ax1 + v2 * ax2 + e * bx) * ir;
+    tx[1] = ax1 * ir;
+    tx[2] = ax2 * ir;
+    tx[3] = bx * ir;
+    ty[0] = -(v1 * ay1 + v2 * ay2 + e * by) * ir;
+    ty[1] = ay1 * ir;
+    ty[2] = ay2 * ir;
+    ty[3] = by * ir;
+}
+
 // Largest eigenvalue of a symmetric 3x3 matrix by the trigonometric solution
 // of its characteristic cubic.
 template <typename real>

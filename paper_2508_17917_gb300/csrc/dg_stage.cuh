@@ -3,9 +3,15 @@
 // One launch evaluates, for every element, the nodal residual of Eq. dg_on_K
 // in strong form
 //     dU/dt = -(rx Dr + sx Ds) F_x - (ry Dr + sy Ds) F_y + LIFT (Fscale (F.n - H))
-// with F = F_c - v_w (x) U - G(U) grad_h U (Sec. 2.1), H the Roe + IIP face
-// flux with the penalty of Eq. penalty_final, and then applies one stage of
-// Algorithm 1:  K1 <- A K1 + dt R;  K0_out <- K0_in + B K1.
+// with F = F_c - v_w (x) U - G(U) grad_h U (Sec. 2.1), H the Roe + interior-
+// penalty face flux with the penalty of Eq. penalty_final, and then applies
+// one stage of Algorithm 1:  K1 <- A K1 + dt R;  K0_out <- K0_in + B K1.
+// For theta != 0 (SIP, NIPG) the terms -S_x H_theta,x - S_y H_theta,y of
+// Eq. dg_on_K add
+//     Wr (rx Lx + ry Ly) + Ws (sx Lx + sy Ly),  L_l = LIFT (Fscale theta w t_l),
+// with Wr = M^-1 Dr^T M, Ws = M^-1 Ds^T M, t_l the theta vector of each face
+// node (theta_vec) and w = 1/2 on interior faces (the average), 1 on boundary
+// faces; G is taken at U+ on interior and far-field faces, at U^b on walls.
 // (The strong form equals the paper's weak form exactly for collocated
 // fluxes on affine elements: the weak volume term integrated by parts gives
 // the strong divergence plus the lifted interior trace F.n.)
@@ -33,7 +39,7 @@ struct StageParams {
     double *Rout;              // STAGE_RHS_ONLY output
     const void *geo;           // real[16] per element
     const int4 *conn;          // (nbr0, nbr1, nbr2, packed faces/bc)
-    const void *ops;           // real Dr[Np*Np], Ds[Np*Np], LIFT[Np*3Nfp]
+    const void *ops;           // real Dr, Ds [Np*Np], LIFT [Np*3Nfp], Wr, Ws [Np*Np]
     const int *fmask;          // 3*Nfp, counter-clockwise along each face
     const double *src;         // optional nodal source [K][4][Np] or null
     const float4 *Sin;         // mixed path: FP32 copy of K0in, [K][Np] (rho, m1, m2, E)
@@ -43,7 +49,9 @@ struct StageParams {
     long long K;
     double A, B, dt;
     double gm1;                // gamma - 1 in FP64 for the pressure
-    double C1;
+    double sig_fac;            // C1 (1+theta)^2 (d+1) of Eq. penalty_final
+    double theta;              // IP variant (Eq. ip_flux): 1 SIP, 0 IIP, -1 NIPG
+    double uinf[4];            // far-field conserved state in FP64 (mixed theta variant)
     int mode;
     int first_stage;           // A == 0: K1 is not read
 };
@@ -61,12 +69,12 @@ struct Shape {
 // geometry record (real[16]) per element
 enum { G_RX = 0, G_RY = 1, G_SX = 2, G_SY = 3, G_J = 4, G_NX = 5, G_NY = 8, G_FS = 11 };
 
-template <int P, typename real>
+template <int P, typename real, bool TH = false>
 struct Smem {
     using S = Shape<P>;
     static constexpr int Np = S::Np, NF = S::NF, E = S::E;
     // sizes in elements of `real`
-    static constexpr int ops = 2 * Np * Np + Np * NF;
+    static constexpr int ops = 2 * Np * Np + Np * NF + (TH ? 2 * Np * Np : 0);
     static constexpr int u = E * 4 * Np;
     static constexpr int gx = E * 4 * Np;
     static constexpr int gy = E * 4 * Np;
@@ -78,22 +86,25 @@ struct Smem {
     static constexpr int dh = E * NF * 4;
     static constexpr int geo = E * 16;
     static constexpr int ngeo = E * 3 * 8;
-    static constexpr int total_real = ops + u + gx + gy + fr + fs + pr + nb + norm + dh + geo + ngeo;
+    static constexpr int th = TH ? E * NF * 8 : 0;
+    static constexpr int total_real = ops + u + gx + gy + fr + fs + pr + nb + norm + dh + geo + ngeo + th;
     static constexpr size_t bytes = total_real * sizeof(real) + NF * sizeof(int) + 16;
 };
 
-template <int P, typename real>
+template <int P, typename real, bool TH>
 __global__ void __launch_bounds__(Shape<P>::NT)
 stage_kernel(StageParams sp, Phys<real> ph)
 {
     using S = Shape<P>;
     constexpr int Np = S::Np, Nfp = S::Nfp, NF = S::NF, E = S::E, NT = S::NT;
-    using L = Smem<P, real>;
+    using L = Smem<P, real, TH>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *sDr = reinterpret_cast<real *>(smem_raw);
     real *sDs = sDr + Np * Np;
     real *sLIFT = sDs + Np * Np;
-    real *sU = sLIFT + Np * NF;
+    real *sWr = sLIFT + Np * NF;               // theta variant only
+    real *sWs = sWr + Np * Np;
+    real *sU = sDr + L::ops;
     real *sGx = sU + L::u;
     real *sGy = sGx + L::gx;
     real *sFr = sGy + L::gy;
@@ -104,7 +115,8 @@ stage_kernel(StageParams sp, Phys<real> ph)
     real *sDH = sNorm + L::norm;
     real *sGeo = sDH + L::dh;
     real *sNGeo = sGeo + L::geo;
-    int *sFm = reinterpret_cast<int *>(sNGeo + L::ngeo);
+    real *sTH = sNGeo + L::ngeo;               // theta variant: Fscale theta w (t_x, t_y)
+    int *sFm = reinterpret_cast<int *>(sTH + L::th);
 
     const int tid = threadIdx.x;
     {
@@ -117,7 +129,8 @@ stage_kernel(StageParams sp, Phys<real> ph)
     const long long ntiles = (K + E - 1) / E;
     const double gm1d = sp.gm1;
     const real p1 = real(P + 1), p2 = real(P + 2);
-    const real C1x3 = real(3) * static_cast<real>(sp.C1);   // C1 (1+theta)^2 (d+1), theta = 0
+    const real sig_fac = static_cast<real>(sp.sig_fac);
+    const real theta = static_cast<real>(sp.theta);
 
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const long long k0 = tile * E;
@@ -254,7 +267,7 @@ stage_kernel(StageParams sp, Phys<real> ph)
                 real c2 = p1 * p2 * sNGeo[(fe * 3 + ff) * 8 + 4] * real(0.5);
                 cinv = c2 > cinv ? c2 : cinv;
             }
-            real sigma = C1x3 * gbar * cinv;
+            real sigma = sig_fac * gbar * cinv;
             real up[4], gxp[4], gyp[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -267,6 +280,12 @@ stage_kernel(StageParams sp, Phys<real> ph)
             flux_n(up, pp, n1, n2, ph, Fnp);
             visc_flux(up, gxp, gyp, ph, vxp, vyp);
             real dH[4];
+            // theta term inputs: jump U+ - U-, the state G is taken at, weight
+            real jmp[4], gs[4], wth = real(1);
+            {
+                const real ir = real(1) / up[0];
+                gs[0] = up[0]; gs[1] = up[1] * ir; gs[2] = up[2] * ir; gs[3] = up[3] * ir;
+            }
             if (btype == BCT_INTERIOR) {
                 const real *w = sN + (fe * 3 + ff) * 4 * Np;
                 const real *ng = sNGeo + (fe * 3 + ff) * 8;
@@ -294,6 +313,9 @@ stage_kernel(StageParams sp, Phys<real> ph)
                 flux_n(um, pm, n1, n2, ph, Fnm);
                 visc_flux(um, gxm, gym, ph, vxm, vym);
                 roe_dissipation(up, pp, um, pm, n1, n2, ph, D);
+                wth = real(0.5);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) jmp[c] = up[c] - um[c];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     real vnp = vxp[c] * n1 + vyp[c] * n2, vnm = vxm[c] * n1 + vym[c] * n2;
@@ -307,8 +329,10 @@ stage_kernel(StageParams sp, Phys<real> ph)
                 roe_dissipation(up, pp, ub, ph.pinf, n1, n2, ph, D);
                 // H = Roe - G(U+) grad U+ . n + sigma (U+ - Ub); F+.n - H:
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
+                for (int c = 0; c < 4; ++c) {
                     dH[c] = real(0.5) * (Fnp[c] - Fnb[c]) - real(0.5) * D[c] - sigma * (up[c] - ub[c]);
+                    jmp[c] = up[c] - ub[c];
+                }
             } else {
                 // wall: U^b from Q^b = (rho+, v_w, p+); H = n.(F_c - v_w U)(U^b)
                 //       - G(U^b) grad U+ . n + sigma (U+ - U^b)
@@ -326,10 +350,22 @@ stage_kernel(StageParams sp, Phys<real> ph)
                 for (int c = 0; c < 4; ++c) {
                     real vnp = vxp[c] * n1 + vyp[c] * n2;
                     dH[c] = (Fnp[c] - vnp) - (Fnb[c] - vnb[c] + sigma * (up[c] - ub[c]));
+                    jmp[c] = up[c] - ub[c];
                 }
+                gs[0] = rb; gs[1] = ph.vw1; gs[2] = ph.vw2; gs[3] = ub[3] / rb;
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c) sDH[(fe * NF + fm) * 4 + c] = fsc * dH[c];
+            if constexpr (TH) {
+                real tx[4], ty[4];
+                theta_vec(gs[0], gs[1], gs[2], gs[3], jmp, n1, n2, ph, tx, ty);
+                const real sc = theta * wth * fsc;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    sTH[(fe * NF + fm) * 8 + c] = sc * tx[c];
+                    sTH[(fe * NF + fm) * 8 + 4 + c] = sc * ty[c];
+                }
+            }
         }
         __syncthreads();
 
@@ -342,6 +378,41 @@ stage_kernel(StageParams sp, Phys<real> ph)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) R[c] += l * dh[m * 4 + c];
             }
+        }
+        if constexpr (TH) {
+            // lift the theta vectors, map to (r, s) and park them in the flux slots
+            if (vol) {
+                const real *th = sTH + ve * NF * 8;
+                real Lx[4] = {0, 0, 0, 0}, Ly[4] = {0, 0, 0, 0};
+#pragma unroll
+                for (int m = 0; m < NF; ++m) {
+                    const real l = sLIFT[vi * NF + m];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        Lx[c] += l * th[m * 8 + c];
+                        Ly[c] += l * th[m * 8 + 4 + c];
+                    }
+                }
+                const real *g = sGeo + ve * 16;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    sFr[(ve * 4 + c) * Np + vi] = g[G_RX] * Lx[c] + g[G_RY] * Ly[c];
+                    sFs[(ve * 4 + c) * Np + vi] = g[G_SX] * Lx[c] + g[G_SY] * Ly[c];
+                }
+            }
+            __syncthreads();
+            if (vol) {
+                const real *ar = sFr + ve * 4 * Np;
+                const real *as = sFs + ve * 4 * Np;
+#pragma unroll
+                for (int j = 0; j < Np; ++j) {
+                    const real wr = sWr[vi * Np + j], ws = sWs[vi * Np + j];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) R[c] += wr * ar[c * Np + j] + ws * as[c * Np + j];
+                }
+            }
+        }
+        if (vol) {
             const long long base = (k0 + ve) * 4 * Np + vi;
             if (sp.src) {
 #pragma unroll

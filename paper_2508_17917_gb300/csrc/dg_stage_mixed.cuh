@@ -16,7 +16,13 @@
 //     every node, so a face node reads F+.n instead of re-evaluating it;
 //   * FP64 arithmetic is left to the pressure recovery and the register
 //     update; FP64<->FP32 conversions are done with integer operations,
-//     because GB300 executes conversion instructions on its FP64 pipe.
+//     because GB300 executes conversion instructions on its FP64 pipe;
+//   * the theta variant (SIP, NIPG) adds the face theta vectors, lifts them
+//     and applies Wr, Ws to their (r, s) components in a second lift phase,
+//     as in dg_stage.cuh.  Both the theta and the penalty term are linear in
+//     the face jump U+ - U-, a small difference of large values, so this
+//     variant forms the jump in FP64 from the FP64 states (the neighbour's
+//     trace read from HBM/L2) instead of from the FP32 copies.
 #pragma once
 #include "dg_stage.cuh"
 
@@ -48,7 +54,7 @@ __device__ __forceinline__ void cp_async16(unsigned dst, const void *src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
 }
 
-template <int P>
+template <int P, bool TH = false>
 struct MixedLayout {
     using S = Shape<P>;
     static constexpr int Np = S::Np, NF = S::NF, E = S::E;
@@ -70,18 +76,20 @@ struct MixedLayout {
     static constexpr size_t oFxy = oF + al(sizeof(float4) * E * Np * 2);      // float4 E*Np*2 (Fx, Fy)
     static constexpr size_t oNorm = oFxy + al(sizeof(float4) * E * Np * 2);   // float E*NF
     static constexpr size_t oDH = oNorm + al(sizeof(float) * E * NF);         // float4 E*NF
-    static constexpr size_t bytes = oDH + al(sizeof(float4) * E * NF);
+    static constexpr size_t oW = oDH + al(sizeof(float4) * E * NF);           // theta: float2 Np*Np (Wr, Ws)
+    static constexpr size_t oTH = oW + (TH ? al(sizeof(float2) * Np * Np) : 0);  // theta: float4 E*NF*2
+    static constexpr size_t bytes = oTH + (TH ? al(sizeof(float4) * E * NF * 2) : 0);
 };
 
 __device__ __forceinline__ void f4_to(const float4 &a, float o[4]) { o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; }
 __device__ __forceinline__ float4 to_f4(const float o[4]) { return make_float4(o[0], o[1], o[2], o[3]); }
 
-template <int P>
-__global__ void __launch_bounds__(Shape<P>::NT, 3)
+template <int P, bool TH>
+__global__ void __launch_bounds__(Shape<P>::NT, TH ? 2 : 3)
 stage_mixed_kernel(StageParams sp, Phys<float> ph)
 {
     using S = Shape<P>;
-    using L = MixedLayout<P>;
+    using L = MixedLayout<P, TH>;
     constexpr int Np = S::Np, Nfp = S::Nfp, NF = S::NF, E = S::E, NT = S::NT;
     constexpr int NpP = L::NpP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -101,6 +109,8 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
     float4 *sFxy = reinterpret_cast<float4 *>(smem_raw + L::oFxy);
     float *sNorm = reinterpret_cast<float *>(smem_raw + L::oNorm);
     float4 *sDH = reinterpret_cast<float4 *>(smem_raw + L::oDH);
+    float2 *sW = reinterpret_cast<float2 *>(smem_raw + L::oW);
+    float4 *sTH = reinterpret_cast<float4 *>(smem_raw + L::oTH);
     const unsigned sbase = static_cast<unsigned>(__cvta_generic_to_shared(smem_raw));
 
     const int tid = threadIdx.x;
@@ -109,13 +119,18 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
         for (int i = tid; i < Np * Np; i += NT) sD[i] = make_float2(ops[i], ops[Np * Np + i]);
         for (int i = tid; i < Np * NF; i += NT) sL[i] = ops[2 * Np * Np + i];
         for (int i = tid; i < NF; i += NT) sFm[i] = sp.fmask[i];
+        if constexpr (TH) {
+            const float *w = ops + 2 * Np * Np + Np * NF;                 // Wr | Ws
+            for (int i = tid; i < Np * Np; i += NT) sW[i] = make_float2(w[i], w[Np * Np + i]);
+        }
     }
     const float *geo = static_cast<const float *>(sp.geo);
     const long long K = sp.K;
     const long long ntiles = (K + E - 1) / E;
     const double gm1d = sp.gm1;
     const float cinv_fac = 0.5f * float(P + 1) * float(P + 2);
-    const float C1x3 = 3.0f * static_cast<float>(sp.C1);
+    const float sig_fac = static_cast<float>(sp.sig_fac);
+    const float theta = static_cast<float>(sp.theta);
     const float dtr = static_cast<float>(sp.dt);
     const bool update = sp.mode == STAGE_UPDATE;
     const bool need_k1 = update && !sp.first_stage;
@@ -263,9 +278,14 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
                 const int f2 = (sConn[fe].w >> (2 * ff)) & 3;
                 cinv = fmaxf(cinv, cinv_fac * ng[G_FS + f2]);
             }
-            const float sigma = C1x3 * gbar * cinv;
+            const float sigma = sig_fac * gbar * cinv;
             float up[4], dH[4], Ftp[4];
             f4_to(sU[fe * Np + vm], up);
+            float jmp[4], gs[4], wth = 1.0f;     // theta term: jump, state of G, weight
+            {
+                const float ir = 1.0f / up[0];
+                gs[0] = up[0]; gs[1] = up[1] * ir; gs[2] = up[2] * ir; gs[3] = up[3] * ir;
+            }
             const float pp = sPo[fe * NpP + vm];
             {   // F+.n of the total flux F = F_c - v_w U - G grad U, from the volume phase
                 const float4 a = sFxy[(fe * Np + vm) * 2], b = sFxy[(fe * Np + vm) * 2 + 1];
@@ -285,6 +305,16 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
                     gym[c] = ng[G_RY] * wr[c] + ng[G_SY] * ws[c];
                 }
                 const float pm = sPn[(fe * 3 + ff) * NpP + vp];
+                if constexpr (TH) {
+                    const int4 cn = sConn[fe];
+                    const long long nb = (ff == 0) ? cn.x : (ff == 1 ? cn.y : cn.z);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        jmp[c] = cvt_d2f(sRaw[(fe * 4 + c) * Np + vm] - sp.K0in[(nb * 4 + c) * Np + vp]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) jmp[c] = up[c] - um[c];
+                }
                 float Fnm[4], vxm[4], vym[4], D[4];
                 flux_n(um, pm, n1, n2, ph, Fnm);
                 visc_flux(um, gxm, gym, ph, vxm, vym);
@@ -292,8 +322,9 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const float Ftm = Fnm[c] - (vxm[c] * n1 + vym[c] * n2);
-                    dH[c] = 0.5f * (Ftp[c] - Ftm) - 0.5f * D[c] - sigma * (up[c] - um[c]);
+                    dH[c] = 0.5f * (Ftp[c] - Ftm) - 0.5f * D[c] - sigma * jmp[c];
                 }
+                wth = 0.5f;
             } else if (btype == BCT_FARFIELD) {
                 const float ub[4] = {ph.Uinf[0], ph.Uinf[1], ph.Uinf[2], ph.Uinf[3]};
                 float Fnp[4], Fnb[4], D[4];
@@ -302,7 +333,10 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
                 roe_dissipation(up, pp, ub, ph.pinf, n1, n2, ph, D);
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
-                    dH[c] = 0.5f * (Fnp[c] - Fnb[c]) - 0.5f * D[c] - sigma * (up[c] - ub[c]);
+                    jmp[c] = TH ? cvt_d2f(sRaw[(fe * 4 + c) * Np + vm] - sp.uinf[c]) : up[c] - ub[c];
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    dH[c] = 0.5f * (Fnp[c] - Fnb[c]) - 0.5f * D[c] - sigma * jmp[c];
             } else {
                 // own broken gradient at the wall node (wall faces only)
                 float gxp[4], gyp[4];
@@ -328,22 +362,72 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
                 for (int c = 0; c < 4; ++c) vnb[c] = vxb[c] * n1 + vyb[c] * n2;
                 if (ph.adiabatic) vnb[3] -= qx * n1 + qy * n2;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) dH[c] = Ftp[c] - (Fnb[c] - vnb[c] + sigma * (up[c] - ub[c]));
+                for (int c = 0; c < 4; ++c) jmp[c] = up[c] - ub[c];
+                // E+ - E^b = (|m+|^2 / rho - rho |v_w|^2) / 2 without the cancellation
+                if constexpr (TH) jmp[3] = 0.5f * (up[1] * up[1] + up[2] * up[2]) / rb - kw;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) dH[c] = Ftp[c] - (Fnb[c] - vnb[c] + sigma * jmp[c]);
+                gs[0] = rb; gs[1] = ph.vw1; gs[2] = ph.vw2; gs[3] = ub[3] / rb;
             }
             sDH[fe * NF + fm] = make_float4(fsc * dH[0], fsc * dH[1], fsc * dH[2], fsc * dH[3]);
+            if constexpr (TH) {
+                float tx[4], ty[4];
+                theta_vec(gs[0], gs[1], gs[2], gs[3], jmp, n1, n2, ph, tx, ty);
+                const float sc = theta * wth * fsc;
+                sTH[(fe * NF + fm) * 2] = make_float4(sc * tx[0], sc * tx[1], sc * tx[2], sc * tx[3]);
+                sTH[(fe * NF + fm) * 2 + 1] = make_float4(sc * ty[0], sc * ty[1], sc * ty[2], sc * ty[3]);
+            }
         }
         __syncthreads();
 
         // ---- P4: lift, the stage update and the FP32 copy of the new state
+        float R[4] = {-Dv[0], -Dv[1], -Dv[2], -Dv[3]};
         if (vol) {
             const float4 *dh = sDH + ve * NF;
-            float R[4] = {-Dv[0], -Dv[1], -Dv[2], -Dv[3]};
 #pragma unroll
             for (int m = 0; m < NF; ++m) {
                 const float4 h = dh[m];
                 const float l = sL[vi * NF + m];
                 R[0] = fmaf(l, h.x, R[0]); R[1] = fmaf(l, h.y, R[1]); R[2] = fmaf(l, h.z, R[2]); R[3] = fmaf(l, h.w, R[3]);
             }
+        }
+        if constexpr (TH) {
+            // lift the theta vectors, map them to (r, s), park them in the flux slots
+            if (vol) {
+                const float4 *th = sTH + ve * NF * 2;
+                float Lx[4] = {0, 0, 0, 0}, Ly[4] = {0, 0, 0, 0};
+#pragma unroll
+                for (int m = 0; m < NF; ++m) {
+                    const float l = sL[vi * NF + m];
+                    const float4 a = th[2 * m], b = th[2 * m + 1];
+                    Lx[0] = fmaf(l, a.x, Lx[0]); Lx[1] = fmaf(l, a.y, Lx[1]); Lx[2] = fmaf(l, a.z, Lx[2]); Lx[3] = fmaf(l, a.w, Lx[3]);
+                    Ly[0] = fmaf(l, b.x, Ly[0]); Ly[1] = fmaf(l, b.y, Ly[1]); Ly[2] = fmaf(l, b.z, Ly[2]); Ly[3] = fmaf(l, b.w, Ly[3]);
+                }
+                const float *g = sGeo + ve * 16;
+                float ar[4], as[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    ar[c] = g[G_RX] * Lx[c] + g[G_RY] * Ly[c];
+                    as[c] = g[G_SX] * Lx[c] + g[G_SY] * Ly[c];
+                }
+                sF[(ve * Np + vi) * 2] = to_f4(ar);
+                sF[(ve * Np + vi) * 2 + 1] = to_f4(as);
+            }
+            __syncthreads();
+            if (vol) {
+                const float4 *fe4 = sF + ve * Np * 2;
+#pragma unroll
+                for (int j = 0; j < Np; ++j) {
+                    const float4 a = fe4[2 * j], b = fe4[2 * j + 1];
+                    const float2 w = sW[vi * Np + j];
+                    R[0] = fmaf(w.x, a.x, fmaf(w.y, b.x, R[0]));
+                    R[1] = fmaf(w.x, a.y, fmaf(w.y, b.y, R[1]));
+                    R[2] = fmaf(w.x, a.z, fmaf(w.y, b.z, R[2]));
+                    R[3] = fmaf(w.x, a.w, fmaf(w.y, b.w, R[3]));
+                }
+            }
+        }
+        if (vol) {
             const long long base = (k0 + ve) * 4 * Np + vi;
             if (sp.src) {
 #pragma unroll

@@ -10,6 +10,7 @@ namespace dg {
 struct StageParams;
 
 struct LaunchShape {
+    bool theta = false;      // kernel variant with the theta terms of the IP flux
     int grid = 0;
     int threads = 0;
     size_t smem = 0;
@@ -18,8 +19,8 @@ struct LaunchShape {
 
 // Launch configuration of the fused stage kernel for degree p and K elements
 // on the current device (persistent grid: SMs x resident CTAs, capped by tiles).
-cudaError_t stage_shape_fp64(int p, long long K, LaunchShape &out);
-cudaError_t stage_shape_mixed(int p, long long K, LaunchShape &out);
+cudaError_t stage_shape_fp64(int p, long long K, bool theta, LaunchShape &out);
+cudaError_t stage_shape_mixed(int p, long long K, bool theta, LaunchShape &out);
 cudaError_t launch_stage_fp64(int p, const LaunchShape &ls, const StageParams &sp,
                               const Phys<double> &ph, cudaStream_t st);
 cudaError_t launch_stage_mixed(int p, const LaunchShape &ls, const StageParams &sp,
@@ -40,8 +41,9 @@ struct AuxMesh {
     int p;
 };
 
-// Lambda_K of Eq. rayleigh_bound per element into lam[K] (FP64).
-cudaError_t launch_dt_lambda(const AuxMesh &m, const Phys<double> &ph, double C1,
+// Lambda_K of Eq. rayleigh_bound per element into lam[K] (FP64);
+// sig_fac = C1 (1+theta)^2 (d+1) of Eq. penalty_final.
+cudaError_t launch_dt_lambda(const AuxMesh &m, const Phys<double> &ph, double sig_fac,
                              double *lam, cudaStream_t st);
 // max over lam[0..K) into *out (one block).
 cudaError_t launch_max_reduce(const double *lam, long long K, double *out, cudaStream_t st);

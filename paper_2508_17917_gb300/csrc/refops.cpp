@@ -8,7 +8,9 @@
 // with P^(alpha,beta) the Jacobi polynomials normalised to unit weighted
 // L2 norm.  From the Vandermonde matrix V_{n,m} = psi_m(r_n, s_n):
 //     Dr = Vr V^-1, Ds = Vs V^-1, M^-1 = V V^T,
-// and LIFT = M^-1 E M_e with M_e the 1D face mass matrix on the LGL points.
+// and LIFT = M^-1 E M_e with M_e the 1D face mass matrix on the LGL points;
+// Wr = M^-1 Dr^T M and Ws = M^-1 Ds^T M carry the theta terms of Eq. dg_on_K,
+// which test a face quantity against the gradient of the basis.
 //
 // This builder is the library's own: Jacobi values by the three-term
 // recurrence, LGL points by Newton iteration on P_p', matrix inverses by
@@ -266,6 +268,16 @@ bool build_reference_operators(int p, RefOps &o)
             for (int l = 0; l < Nfp; ++l)
                 Emat[o.Fmask[f * Nfp + i] * (3 * Nfp) + f * Nfp + l] += o.M1D[f * Nfp * Nfp + i * Nfp + l];
     o.LIFT = matmul(Minv, Emat, Np, Np, 3 * Nfp);
+    // Wr = M^-1 Dr^T M, Ws = M^-1 Ds^T M: nodal values of the function whose
+    // L2 product with any l_i equals the product of the input with d l_i/dr
+    std::vector<double> Drt(Np * Np), Dst(Np * Np);
+    for (int i = 0; i < Np; ++i)
+        for (int j = 0; j < Np; ++j) {
+            Drt[j * Np + i] = o.Dr[i * Np + j];
+            Dst[j * Np + i] = o.Ds[i * Np + j];
+        }
+    o.Wr = matmul(matmul(Minv, Drt, Np, Np, Np), o.Mhat, Np, Np, Np);
+    o.Ws = matmul(matmul(Minv, Dst, Np, Np, Np), o.Mhat, Np, Np, Np);
     return true;
 }
 

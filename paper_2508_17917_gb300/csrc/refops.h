@@ -13,6 +13,7 @@ struct RefOps {
     std::vector<double> M1D;         // 3*Nfp*Nfp face mass in CCW order
     std::vector<double> Mhat;        // Np*Np
     std::vector<double> wface;       // Nfp LGL weights (column sums of M1D)
+    std::vector<double> Wr, Ws;      // Np*Np: M^-1 Dr^T M, M^-1 Ds^T M
 };
 
 // Builds every operator for degree p (1..6). Returns false on bad p.

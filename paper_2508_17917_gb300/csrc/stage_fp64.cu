@@ -5,11 +5,11 @@
 namespace dg {
 namespace {
 
-template <int P, typename real>
+template <int P, typename real, bool TH>
 cudaError_t shape_p(long long K, LaunchShape &ls)
 {
-    using L = Smem<P, real>;
-    auto kern = stage_kernel<P, real>;
+    using L = Smem<P, real, TH>;
+    auto kern = stage_kernel<P, real, TH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(L::bytes));
     if (e != cudaSuccess) return e;
@@ -25,13 +25,17 @@ cudaError_t shape_p(long long K, LaunchShape &ls)
     ls.threads = Shape<P>::NT;
     ls.smem = L::bytes;
     ls.elems_per_tile = Shape<P>::E;
+    ls.theta = TH;
     return cudaSuccess;
 }
 
 template <int P, typename real>
 cudaError_t launch_p(const LaunchShape &ls, const StageParams &sp, const Phys<real> &ph, cudaStream_t st)
 {
-    stage_kernel<P, real><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
+    if (ls.theta)
+        stage_kernel<P, real, true><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
+    else
+        stage_kernel<P, real, false><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
     return cudaGetLastError();
 }
 
@@ -48,9 +52,9 @@ cudaError_t launch_p(const LaunchShape &ls, const StageParams &sp, const Phys<re
     default: return cudaErrorInvalidValue;        \
     }
 
-cudaError_t stage_shape_fp64(int p, long long K, LaunchShape &out)
+cudaError_t stage_shape_fp64(int p, long long K, bool theta, LaunchShape &out)
 {
-#define C_(P) shape_p<P, double>(K, out)
+#define C_(P) (theta ? shape_p<P, double, true>(K, out) : shape_p<P, double, false>(K, out))
     DG_SWITCH_P(p, C_)
 #undef C_
 }

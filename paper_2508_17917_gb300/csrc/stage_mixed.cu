@@ -6,11 +6,11 @@
 namespace dg {
 namespace {
 
-template <int P>
+template <int P, bool TH>
 cudaError_t shape_p(long long K, LaunchShape &ls)
 {
-    using L = MixedLayout<P>;
-    auto kern = stage_mixed_kernel<P>;
+    using L = MixedLayout<P, TH>;
+    auto kern = stage_mixed_kernel<P, TH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(L::bytes));
     if (e != cudaSuccess) return e;
@@ -28,13 +28,17 @@ cudaError_t shape_p(long long K, LaunchShape &ls)
     ls.threads = Shape<P>::NT;
     ls.smem = L::bytes;
     ls.elems_per_tile = Shape<P>::E;
+    ls.theta = TH;
     return cudaSuccess;
 }
 
 template <int P>
 cudaError_t launch_p(const LaunchShape &ls, const StageParams &sp, const Phys<float> &ph, cudaStream_t st)
 {
-    stage_mixed_kernel<P><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
+    if (ls.theta)
+        stage_mixed_kernel<P, true><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
+    else
+        stage_mixed_kernel<P, false><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
     return cudaGetLastError();
 }
 
@@ -61,9 +65,9 @@ cudaError_t shadow_p(const double *K0, long long K, double gm1, float4 *S, float
     default: return cudaErrorInvalidValue;        \
     }
 
-cudaError_t stage_shape_mixed(int p, long long K, LaunchShape &out)
+cudaError_t stage_shape_mixed(int p, long long K, bool theta, LaunchShape &out)
 {
-#define C_(P) shape_p<P>(K, out)
+#define C_(P) (theta ? shape_p<P, true>(K, out) : shape_p<P, false>(K, out))
     DG_SWITCH_P(p, C_)
 #undef C_
 }

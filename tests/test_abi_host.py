@@ -81,10 +81,11 @@ def test_create_rejects_bad_params(dg):
     with pytest.raises(dg.DGError) as e:
         dg.dg_create(bad)
     assert e.value.status == -1
-    sip = dg.DgParams(2, 0, 1.4, 0.72, 1e-3, 1.0, 0.01, 1, 1, 0, 1, 1)
-    with pytest.raises(dg.DGError) as e:
-        dg.dg_create(sip)
-    assert e.value.status == -6
+    for theta in (1.5, -1.01, float("nan")):
+        bad_theta = dg.DgParams(2, 0, 1.4, 0.72, 1e-3, theta, 0.01, 1, 1, 0, 1, 1)
+        with pytest.raises(dg.DGError) as e:
+            dg.dg_create(bad_theta)
+        assert e.value.status == -1
 
 
 def test_no_cpu_fallback_without_gpu(dg):
