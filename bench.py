@@ -274,6 +274,27 @@ def run_ours(args):
                  "roofline_frac": ach / peak}
         del sl
 
+    # --- p = 6 on an 80,000-triangle O-grid (wall, far field), mixed path
+    p6 = None
+    if not args.no_large:
+        m6 = dg_inputs.ogrid_cylinder(200, 200, 0.5, 30.0, seed=6)
+        p_inf = 1.0 / (1.4 * 0.2 * 0.2)
+        s6 = dg.Solver(m6, 6, "mixed", stream=sh, mu=1.0 / 150.0, rho_inf=1.0, u_inf=1.0, v_inf=0.0,
+                       p_inf=p_inf)
+        x6, y6 = s6.node_coords()
+        U6 = to_kcn(dg_inputs.free_stream(x6.shape, rho=1.0, u=1.0, v=0.0, p=p_inf))
+        U6[:, 1] *= np.tanh(4.0 * (np.hypot(x6, y6) - 0.5))
+        U6[:, 3] = p_inf / 0.4 + 0.5 * U6[:, 1] ** 2 / U6[:, 0]
+        s6.set_state(dg_inputs.perturb(U6, seed=3, amp=1e-3))
+        dt6 = s6.dt(0.3)
+        t6, _ = timed_steps(dg, torch, s6, dt6, max(5, args.steps // 10), 2, flush, stream)
+        dof6 = 4 * m6.K * 28
+        ach6 = (4 * m6.K * 28 * (24 + 4 * 32) + 5 * m6.K * GEO_BYTES_MIXED) / (sum(t6) / len(t6) * 1e-3) / 1e9
+        p6 = {"workload": "p=6 (Np=28), seeded O-grid 200x200 (K=80,000), Re=150, M=0.2, wall + far field",
+              "K": m6.K, "value": dof6 * 5 * len(t6) / (sum(t6) * 1e-3), "unit": UNIT,
+              "ms_per_step": sum(t6) / len(t6), "roofline_achieved_gbs": ach6, "roofline_frac": ach6 / peak}
+        del s6
+
     # --- end to end through the C ABI with host buffers (pinned)
     host_in = torch.empty((K, 4, NP), dtype=torch.float64, pin_memory=True)
     host_in.copy_(torch.from_numpy(U0))
@@ -312,6 +333,7 @@ def run_ours(args):
                           "mixed_over_fp64": value / ws / v64},
             "large_mesh": large,
             "sip_path": sip,
+            "p6_large": p6,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk.summary(),
