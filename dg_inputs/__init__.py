@@ -9,6 +9,8 @@ parity test take their inputs from here and nothing else.
 from .meshes import periodic_square, ogrid_cylinder, Mesh
 from .states import (isentropic_vortex, free_stream, splitmix64_uniform,
                      perturb, shu_vortex_params)
+from .sweeps import viv_sweep, sweep_mesh
 
 __all__ = ["periodic_square", "ogrid_cylinder", "Mesh", "isentropic_vortex",
-           "free_stream", "splitmix64_uniform", "perturb", "shu_vortex_params"]
+           "free_stream", "splitmix64_uniform", "perturb", "shu_vortex_params",
+           "viv_sweep", "sweep_mesh"]

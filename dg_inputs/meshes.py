@@ -56,23 +56,31 @@ def _connect(EToV, canon):
     """Pair faces that join the same two canonical vertices.
 
     ``canon[v]`` identifies vertices that coincide (directly or through a
-    period).  Every canonical edge must be shared by exactly one or two faces.
+    period).  Every canonical edge must be shared by exactly one or two faces;
+    returns EToE, EToF and a dict {(a, b): (k, f)} of the unpaired faces.
     """
     K = EToV.shape[0]
     EToE = np.tile(np.arange(K, dtype=np.int32)[:, None], (1, 3))
     EToF = np.tile(np.arange(3, dtype=np.int32)[None, :], (K, 1))
+    a = canon[EToV].astype(np.int64)                     # (K, 3)
+    b = canon[np.roll(EToV, -1, axis=1)].astype(np.int64)
+    lo, hi = np.minimum(a, b).ravel(), np.maximum(a, b).ravel()
+    order = np.lexsort((hi, lo))
+    lo_s, hi_s = lo[order], hi[order]
+    same = (lo_s[1:] == lo_s[:-1]) & (hi_s[1:] == hi_s[:-1])
+    if np.any(same[1:] & same[:-1]):
+        raise RuntimeError("an edge is shared by more than two faces")
+    first = np.nonzero(same)[0]
+    f1, f2 = order[first], order[first + 1]
+    k1, j1, k2, j2 = f1 // 3, f1 % 3, f2 // 3, f2 % 3
+    EToE[k1, j1], EToF[k1, j1] = k2, j2
+    EToE[k2, j2], EToF[k2, j2] = k1, j1
+    paired = np.zeros(3 * K, dtype=bool)
+    paired[f1] = True
+    paired[f2] = True
     owner = {}
-    for k in range(K):
-        for f in range(3):
-            a = int(canon[EToV[k, f]])
-            b = int(canon[EToV[k, (f + 1) % 3]])
-            key = (a, b) if a < b else (b, a)
-            if key in owner:
-                k2, f2 = owner.pop(key)
-                EToE[k, f], EToF[k, f] = k2, f2
-                EToE[k2, f2], EToF[k2, f2] = k, f
-            else:
-                owner[key] = (k, f)
+    for g in np.nonzero(~paired)[0]:
+        owner[(int(lo[g]), int(hi[g]))] = (int(g // 3), int(g % 3))
     return EToE, EToF, owner
 
 
@@ -146,15 +154,14 @@ def ogrid_cylinder(n_theta: int = 120, n_r: int = 170, r0: float = 0.5,
     vy = (R * np.sin(T)).ravel().astype(np.float64)
     rng = np.random.default_rng(seed)
     flips = rng.integers(0, 2, size=(n_r, n_theta))
-    tris = []
-    for k in range(n_r):
-        for i in range(n_theta):
-            a, b, c, d = vid(i, k), vid(i + 1, k), vid(i + 1, k + 1), vid(i, k + 1)
-            if flips[k, i]:
-                tris += [(a, b, c), (a, c, d)]
-            else:
-                tris += [(a, b, d), (b, c, d)]
-    EToV = _orient_ccw(vx, vy, np.array(tris, dtype=np.int32))
+    kk, ii = np.meshgrid(np.arange(n_r), np.arange(n_theta), indexing="ij")
+    a, b = vid(ii, kk), vid(ii + 1, kk)
+    c, d = vid(ii + 1, kk + 1), vid(ii, kk + 1)
+    f = flips[..., None].astype(bool)
+    t1 = np.where(f, np.stack([a, b, c], -1), np.stack([a, b, d], -1))
+    t2 = np.where(f, np.stack([a, c, d], -1), np.stack([b, c, d], -1))
+    tris = np.stack([t1, t2], axis=2).reshape(-1, 3)      # (k, i, two triangles) order
+    EToV = _orient_ccw(vx, vy, tris.astype(np.int32))
     canon = np.arange(vx.size, dtype=np.int64)
     EToE, EToF, unpaired = _connect(EToV, canon)
     bc = np.zeros_like(EToE)

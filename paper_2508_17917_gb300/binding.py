@@ -17,7 +17,11 @@ __all__ = ["DG_OK", "DG_PRECISION_FP64", "DG_PRECISION_MIXED", "DG_SOURCE_NONE",
            "dg_lsrk_step", "dg_lsrk_steps", "dg_compute_dt", "dg_wall_forces",
            "dg_wall_forces_noalloc", "DG_NOALLOC_MAX_WALL_FACES", "dg_rigid_step",
            "dg_check_finite", "dg_set_source", "dg_node_coords", "dg_reference_operators",
-           "dg_kernel_launches", "dg_last_error", "Solver", "EXPORTED"]
+           "dg_kernel_launches", "dg_last_error", "Solver", "EXPORTED",
+           "DgCase", "dg_batch_create", "dg_batch_destroy", "dg_batch_last_error",
+           "dg_batch_kernel_launches", "dg_batch_stream", "dg_batch_case_size", "dg_batch_node_coords",
+           "dg_batch_set_state", "dg_batch_get_state", "dg_batch_run", "dg_batch_reset_history",
+           "dg_batch_rigid", "BatchSolver"]
 
 DG_OK = 0
 DG_PRECISION_FP64, DG_PRECISION_MIXED = 0, 1
@@ -38,6 +42,14 @@ class DgParams(C.Structure):
                 ("mu", C.c_double), ("theta", C.c_double), ("C1", C.c_double),
                 ("rho_inf", C.c_double), ("u_inf", C.c_double), ("v_inf", C.c_double),
                 ("p_inf", C.c_double), ("adiabatic_zero_heatflux", C.c_int)]
+
+
+class DgCase(C.Structure):
+    """dg_case of include/dg_batch.h."""
+    _fields_ = [("p", C.c_int), ("Nv", C.c_int64), ("vx", _dp), ("vy", _dp), ("K", C.c_int64),
+                ("EToV", _ip), ("EToE", _ip), ("EToF", _ip), ("bc", _ip), ("mu", C.c_double),
+                ("M_r", C.c_double), ("C_r", C.c_double), ("K_r", C.c_double), ("mass", C.c_double),
+                ("y0", C.c_double), ("ydot0", C.c_double)]
 
 
 class DGError(RuntimeError):
@@ -66,6 +78,19 @@ EXPORTED = {
     "dg_reference_operators": (C.c_int, [C.c_int, _dp, _dp, _dp, _dp, _dp, _ip]),
     "dg_kernel_launches": (C.c_int64, [C.c_void_p]),
     "dg_last_error": (C.c_char_p, [C.c_void_p]),
+    # include/dg_batch.h
+    "dg_batch_create": (C.c_int, [C.POINTER(DgParams), C.c_int, C.POINTER(DgCase), C.POINTER(C.c_void_p)]),
+    "dg_batch_destroy": (C.c_int, [C.c_void_p]),
+    "dg_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "dg_batch_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "dg_batch_stream": (C.c_void_p, [C.c_void_p]),
+    "dg_batch_case_size": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
+    "dg_batch_node_coords": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp]),
+    "dg_batch_set_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "dg_batch_get_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "dg_batch_run": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_void_p, C.c_int]),
+    "dg_batch_reset_history": (C.c_int, [C.c_void_p]),
+    "dg_batch_rigid": (C.c_int, [C.c_void_p, _dp]),
 }
 
 _lib = None
@@ -293,3 +318,146 @@ class Solver:
     @property
     def launches(self):
         return dg_kernel_launches(self.ctx)
+
+
+# ---- include/dg_batch.h ---------------------------------------------------
+
+def _bcheck(st, b=None):
+    if st != DG_OK:
+        raise DGError(st, lib().dg_batch_last_error(b).decode())
+
+
+def dg_batch_create(params: DgParams, cases):
+    """cases: a sequence of DgCase (their arrays must stay alive during the call)."""
+    arr = (DgCase * len(cases))(*cases)
+    out = C.c_void_p()
+    _bcheck(lib().dg_batch_create(C.byref(params), len(cases), arr, C.byref(out)), None)
+    return out
+
+
+def dg_batch_destroy(b):
+    return lib().dg_batch_destroy(b)
+
+
+def dg_batch_last_error(b):
+    return lib().dg_batch_last_error(b).decode()
+
+
+def dg_batch_kernel_launches(b):
+    return int(lib().dg_batch_kernel_launches(b))
+
+
+def dg_batch_stream(b):
+    """Integer handle of the batch's cudaStream_t."""
+    return int(lib().dg_batch_stream(b) or 0)
+
+
+def dg_batch_case_size(b, i):
+    K, p = C.c_int64(0), C.c_int(0)
+    _bcheck(lib().dg_batch_case_size(b, int(i), C.byref(K), C.byref(p)), b)
+    return int(K.value), int(p.value)
+
+
+def dg_batch_node_coords(b, i):
+    K, p = dg_batch_case_size(b, i)
+    Np = (p + 1) * (p + 2) // 2
+    x, y = np.zeros((K, Np)), np.zeros((K, Np))
+    _bcheck(lib().dg_batch_node_coords(b, int(i), _dptr(x), _dptr(y)), b)
+    return x, y
+
+
+def dg_batch_set_state(b, i, U):
+    ptr, dev = _arr_ptr(U)
+    _bcheck(lib().dg_batch_set_state(b, int(i), ptr, dev), b)
+
+
+def dg_batch_get_state(b, i, U):
+    ptr, dev = _arr_ptr(U)
+    _bcheck(lib().dg_batch_get_state(b, int(i), ptr, dev), b)
+
+
+def dg_batch_run(b, cfl, nsteps, use_graph=True, hist=None):
+    """hist: optional torch CUDA float64 tensor [rows][ncases][8]."""
+    hp, rows = None, 0
+    if hist is not None:
+        ptr, dev = _arr_ptr(hist)
+        if not dev:
+            raise ValueError("the history must be a device tensor")
+        hp, rows = ptr, int(hist.shape[0])
+    _bcheck(lib().dg_batch_run(b, float(cfl), int(nsteps), int(bool(use_graph)), hp, rows), b)
+
+
+def dg_batch_reset_history(b):
+    _bcheck(lib().dg_batch_reset_history(b), b)
+
+
+def dg_batch_rigid(b, ncases):
+    out = np.zeros((ncases, 10))
+    _bcheck(lib().dg_batch_rigid(b, _dptr(out)), b)
+    return out
+
+
+class BatchSolver:
+    """A batch of cases: the dg_batch_* calls as methods.
+
+    Each case is a dict with keys mesh, p, mu, M_r, C_r, K_r, mass and
+    optionally y0, ydot0; the other keyword arguments are the shared
+    parameters (gamma, Pr, C1, far field, wall flag)."""
+
+    def __init__(self, cases, gamma=1.4, Pr=0.72, C1=0.01, rho_inf=1.0, u_inf=1.0, v_inf=0.0,
+                 p_inf=1.0, adiabatic_zero_heatflux=1):
+        self.params = DgParams(0, DG_PRECISION_MIXED, gamma, Pr, 0.0, 0.0, C1, rho_inf, u_inf, v_inf,
+                               p_inf, int(adiabatic_zero_heatflux))
+        keep, descs = [], []
+        for c in cases:
+            m = c["mesh"]
+            arrs = (_f64(m.vx), _f64(m.vy), _i32(m.EToV), _i32(m.EToE), _i32(m.EToF), _i32(m.bc))
+            keep.append(arrs)
+            vx, vy, EToV, EToE, EToF, bc = arrs
+            descs.append(DgCase(int(c["p"]), vx.size, _dptr(vx), _dptr(vy), EToV.shape[0],
+                                EToV.ctypes.data_as(_ip), EToE.ctypes.data_as(_ip),
+                                EToF.ctypes.data_as(_ip), bc.ctypes.data_as(_ip), float(c["mu"]),
+                                float(c["M_r"]), float(c["C_r"]), float(c["K_r"]), float(c["mass"]),
+                                float(c.get("y0", 0.0)), float(c.get("ydot0", 0.0))))
+        self.ncases = len(descs)
+        self.b = dg_batch_create(self.params, descs)
+        self.sizes = [dg_batch_case_size(self.b, i) for i in range(self.ncases)]
+
+    def __del__(self):
+        b = getattr(self, "b", None)
+        if b is not None and _lib is not None:
+            dg_batch_destroy(b)
+            self.b = None
+
+    def shape(self, i):
+        K, p = self.sizes[i]
+        return (K, 4, (p + 1) * (p + 2) // 2)
+
+    def node_coords(self, i):
+        return dg_batch_node_coords(self.b, i)
+
+    def set_state(self, i, U):
+        dg_batch_set_state(self.b, i, U if not isinstance(U, np.ndarray) else _f64(U))
+
+    def get_state(self, i):
+        out = np.zeros(self.shape(i))
+        dg_batch_get_state(self.b, i, out)
+        return out
+
+    def run(self, cfl, nsteps, use_graph=True, hist=None):
+        dg_batch_run(self.b, cfl, nsteps, use_graph, hist)
+
+    def reset_history(self):
+        dg_batch_reset_history(self.b)
+
+    def rigid(self):
+        """[ncases][10]: t, dt, y, y', y'', v_b, Fx, Fy, Mz, frozen."""
+        return dg_batch_rigid(self.b, self.ncases)
+
+    @property
+    def launches(self):
+        return dg_batch_kernel_launches(self.b)
+
+    @property
+    def stream(self):
+        return dg_batch_stream(self.b)

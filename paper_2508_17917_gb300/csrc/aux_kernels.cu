@@ -3,6 +3,7 @@
 
 #include "dg_stage.cuh"
 #include "launch.h"
+#include "rigid.h"
 
 namespace dg {
 namespace {
@@ -23,6 +24,11 @@ __global__ void dt_lambda_kernel(AuxMesh m, Phys<double> ph, double sig_fac, dou
 {
     long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     if (k >= m.K) return;
+    if (m.elem_case) {            // batch: the element's case sets mu and v_b
+        const BatchCase &cs = m.cases[m.elem_case[k]];
+        ph.mu = cs.mu;
+        ph.vw2 = cs.vb;
+    }
     const int p = m.p, Np = (p + 1) * (p + 2) / 2, Nfp = p + 1;
     const double *g = m.geo + k * 16;
     const int4 cn = m.conn[k];
@@ -112,6 +118,7 @@ __global__ void wall_force_kernel(AuxMesh m, Phys<double> ph, const int2 *faces,
     const int p = m.p, Np = (p + 1) * (p + 2) / 2, Nfp = p + 1;
     const long long k = faces[w].x;
     const int f = faces[w].y;
+    if (m.elem_case) ph.mu = m.cases[m.elem_case[k]].mu;
     const double *g = m.geo + k * 16;
     const double rx = g[G_RX], ry = g[G_RY], sx = g[G_SX], sy = g[G_SY];
     const double n1 = g[G_NX + f], n2 = g[G_NY + f], sJ = g[G_FS + f] * g[G_J];
@@ -177,7 +184,137 @@ __global__ void nonfinite_kernel(const double *x, long long n, int *flag)
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) *flag = 1;
 }
 
+// ---- batch of independent cases (Algorithm 3 per case, on the device)
+
+// One block per case: max_K Lambda_K over the case's elements, then
+// dt = cfl / max (Eq. rayleigh_bound); a bound that is not finite freezes the
+// case (dt = 0, bad = 1) instead of spreading NaN.
+__global__ void batch_dt_kernel(const double *lam, const long long *seg, BatchCase *cases, double cfl)
+{
+    __shared__ double s[256];
+    const int i = blockIdx.x;
+    const long long b = seg[2 * i], e = seg[2 * i + 1];
+    double m = 0.0;
+    bool bad = false;
+    for (long long k = b + threadIdx.x; k < e; k += blockDim.x) {
+        const double v = lam[k];
+        bad |= !isfinite(v);
+        m = fmax(m, v);
+    }
+    s[threadIdx.x] = bad ? NAN : m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            const double x = s[threadIdx.x], y = s[threadIdx.x + w];
+            s[threadIdx.x] = (isnan(x) || isnan(y)) ? NAN : fmax(x, y);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        BatchCase &cs = cases[i];
+        const double l = s[0];
+        cs.lam = l;
+        if (cs.bad || !isfinite(l) || !(l > 0.0)) {
+            cs.bad = 1;
+            cs.dt = 0.0;
+        } else {
+            cs.dt = cfl / l;
+        }
+    }
+}
+
+// One thread per case: Newmark step with the lift of the previous force
+// evaluation (Algorithm 3: F_r = lift / m), v_b for the coming RK step.
+__global__ void batch_newmark_kernel(BatchCase *cases, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    BatchCase &cs = cases[i];
+    if (cs.bad) {
+        cs.vb = 0.0;
+        return;
+    }
+    double y = cs.y, yd = cs.yd, ydd = cs.ydd, vb = 0.0;
+    if (newmark_step(cs.Mr, cs.Cr, cs.Kr, cs.Fy / cs.mass, cs.dt, y, yd, ydd, vb)) {
+        cs.y = y;
+        cs.yd = yd;
+        cs.ydd = ydd;
+        cs.vb = vb;
+        cs.t += cs.dt;
+    } else {
+        cs.bad = 1;
+        cs.vb = 0.0;
+    }
+}
+
+// One block per case: deterministic tree sum of its wall-face partials.
+__global__ void batch_forces_kernel(const double *partial, const int *wseg, BatchCase *cases)
+{
+    __shared__ double s[3][256];
+    const int i = blockIdx.x;
+    const int b = wseg[2 * i], e = wseg[2 * i + 1];
+    double a[3] = {0, 0, 0};
+    for (int w = b + threadIdx.x; w < e; w += blockDim.x)
+        for (int c = 0; c < 3; ++c) a[c] += partial[static_cast<long long>(w) * 3 + c];
+    for (int c = 0; c < 3; ++c) s[c][threadIdx.x] = a[c];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < 3; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        cases[i].Fx = s[0][0];
+        cases[i].Fy = s[1][0];
+        cases[i].Mz = s[2][0];
+    }
+}
+
+// One block: row *counter of hist gets (t, dt, y, y', v_b, Fx, Fy, lam) of
+// every case; rows beyond cap are dropped; the counter always advances.
+__global__ void batch_record_kernel(const BatchCase *cases, int n, double *hist, int cap, int *counter)
+{
+    const int row = *counter;
+    __syncthreads();
+    if (row < cap)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const BatchCase &cs = cases[i];
+            double *h = hist + (static_cast<long long>(row) * n + i) * 8;
+            h[0] = cs.t; h[1] = cs.dt; h[2] = cs.y; h[3] = cs.yd;
+            h[4] = cs.vb; h[5] = cs.Fx; h[6] = cs.Fy; h[7] = cs.lam;
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) *counter = row + 1;
+}
+
 }  // namespace
+
+cudaError_t launch_batch_dt(const double *lam, const long long *seg, BatchCase *cases, int ncases, double cfl,
+                            cudaStream_t st)
+{
+    batch_dt_kernel<<<ncases, 256, 0, st>>>(lam, seg, cases, cfl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_newmark(BatchCase *cases, int ncases, cudaStream_t st)
+{
+    batch_newmark_kernel<<<(ncases + 127) / 128, 128, 0, st>>>(cases, ncases);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_forces(const double *partial, const int *wseg, BatchCase *cases, int ncases,
+                                cudaStream_t st)
+{
+    batch_forces_kernel<<<ncases, 256, 0, st>>>(partial, wseg, cases);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_record(const BatchCase *cases, int ncases, double *hist, int cap, int *counter,
+                                cudaStream_t st)
+{
+    batch_record_kernel<<<1, 256, 0, st>>>(cases, ncases, hist, cap, counter);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_dt_lambda(const AuxMesh &m, const Phys<double> &ph, double sig_fac, double *lam,
                              cudaStream_t st)

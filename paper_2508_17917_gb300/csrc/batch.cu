@@ -1,0 +1,583 @@
+// batch.cu -- host side of the batch C ABI (include/dg_batch.h): many
+// independent cylinder / VIV cases advanced together, Algorithm 3 per case
+// on the device, optionally replayed from a CUDA graph.
+//
+// Layout: cases are grouped by polynomial degree.  A group stores the
+// elements of its cases back to back ([K_g][4][Np] FP64 state, FP32 copies,
+// geometry, connectivity with neighbour indices offset by the case's first
+// element).  A tile table lists (first element, count, case) for every tile
+// of the mixed stage kernel, so no tile straddles two cases and the kernel
+// reads each case's dt, v_b and viscosity once per tile.  The time-step
+// bound Lambda_K of every element of every group goes into one array with a
+// contiguous range per case; wall-face partial forces likewise.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/dg_batch.h"
+#include "devbuf.h"
+#include "dg_stage.cuh"
+#include "launch.h"
+#include "mesh.h"
+#include "refops.h"
+#include "rk.h"
+
+namespace {
+
+using dg::DevBuf;
+
+struct Group {
+    int p = 0;
+    dg::RefOps ops;
+    long long K = 0;                 // elements of all cases of this degree
+    long long lam_base = 0;          // first entry in the batch's Lambda_K array
+    int wall_base = 0;               // first entry in the batch's wall partials
+    int nwall = 0;
+    long long ntiles = 0;
+    dg::LaunchShape shape;
+    DevBuf<double> K0a, K0b, K1, geo64, Dr64, Ds64, wface, fxy;
+    DevBuf<float> geo32, ops32, P0a, P0b;
+    DevBuf<float4> S0a, S0b;
+    DevBuf<int4> conn, tiles;
+    DevBuf<int> fmask, elem_case;
+    DevBuf<int2> walls;
+};
+
+struct CaseHost {
+    int group = 0;
+    long long off = 0;               // first element within the group
+    long long K = 0;
+    int p = 0;
+    std::vector<double> vx, vy;
+    std::vector<int32_t> EToV;
+};
+
+}  // namespace
+
+struct dg_batch {
+    dg_params prm{};
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int64_t launches = 0;
+    std::vector<Group> groups;
+    std::vector<CaseHost> cases;
+    std::vector<dg::BatchCase> init;
+    DevBuf<dg::BatchCase> dcases;
+    DevBuf<double> lam, fpart;
+    DevBuf<long long> seg;
+    DevBuf<int> wseg, counter;
+    bool cur_is_a = true;
+    bool forces_stale = true;
+    // graphs: [0] starts from buffers a, [1] from buffers b
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t graph_launches = 0;
+    double graph_cfl = 0.0;
+    double *graph_hist = nullptr;
+    int graph_rows = 0;
+
+    ~dg_batch()
+    {
+        drop_graphs();
+        if (stream) cudaStreamDestroy(stream);
+    }
+    void drop_graphs()
+    {
+        for (auto &g : graph)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+    }
+};
+
+namespace {
+
+thread_local std::string g_create_err;     // message of the last failed dg_batch_create
+
+dg_status bfail(dg_batch *b, dg_status st, const std::string &msg)
+{
+    if (b) b->err = msg;
+    return st;
+}
+
+dg_status bcuda(dg_batch *b, cudaError_t e, const char *where)
+{
+    return bfail(b, DG_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define B_CUDA(b, expr)                                          \
+    do {                                                         \
+        cudaError_t e_ = (expr);                                 \
+        if (e_ != cudaSuccess) return bcuda(b, e_, #expr);       \
+    } while (0)
+
+template <typename real>
+dg::Phys<real> phys_of(const dg_params &p)
+{
+    dg::Phys<real> ph;
+    ph.gamma = real(p.gamma);
+    ph.gm1 = real(p.gamma - 1.0);
+    ph.mu = real(0);                 // per case, set in the kernels
+    ph.gPr = real(p.gamma / p.Pr);
+    ph.vw1 = real(0);
+    ph.vw2 = real(0);                // per case
+    const double E = p.p_inf / (p.gamma - 1.0) + 0.5 * p.rho_inf * (p.u_inf * p.u_inf + p.v_inf * p.v_inf);
+    ph.Uinf[0] = real(p.rho_inf);
+    ph.Uinf[1] = real(p.rho_inf * p.u_inf);
+    ph.Uinf[2] = real(p.rho_inf * p.v_inf);
+    ph.Uinf[3] = real(E);
+    ph.pinf = real(p.p_inf);
+    ph.adiabatic = p.adiabatic_zero_heatflux;
+    return ph;
+}
+
+double sigma_factor(const dg_params &p) { return p.C1 * (1.0 + p.theta) * (1.0 + p.theta) * 3.0; }
+
+dg::AuxMesh aux_of(const dg_batch *b, const Group &g)
+{
+    dg::AuxMesh m;
+    m.U = b->cur_is_a ? g.K0a.ptr : g.K0b.ptr;
+    m.elem_case = g.elem_case.ptr;
+    m.cases = b->dcases.ptr;
+    m.geo = g.geo64.ptr;
+    m.conn = g.conn.ptr;
+    m.Dr = g.Dr64.ptr;
+    m.Ds = g.Ds64.ptr;
+    m.fmask = g.fmask.ptr;
+    m.K = g.K;
+    m.p = g.p;
+    return m;
+}
+
+// wall forces of every case into cases[].Fx, Fy, Mz
+dg_status enqueue_forces(dg_batch *b)
+{
+    const dg::Phys<double> ph = phys_of<double>(b->prm);
+    for (auto &g : b->groups) {
+        if (g.nwall == 0) continue;
+        B_CUDA(b, dg::launch_wall_force_faces(aux_of(b, g), ph, g.walls.ptr, g.fxy.ptr, g.wface.ptr, g.nwall, 0.0,
+                                              0.0, b->fpart.ptr + static_cast<size_t>(g.wall_base) * 3, b->stream));
+        b->launches += 1;
+    }
+    B_CUDA(b, dg::launch_batch_forces(b->fpart.ptr, b->wseg.ptr, b->dcases.ptr, static_cast<int>(b->cases.size()),
+                                      b->stream));
+    b->launches += 1;
+    return DG_OK;
+}
+
+// one time step of every case (Algorithm 3), queued on the batch stream
+dg_status enqueue_step(dg_batch *b, double cfl, double *hist, int rows)
+{
+    const int n = static_cast<int>(b->cases.size());
+    const double sf = sigma_factor(b->prm);
+    const dg::Phys<float> ph32 = phys_of<float>(b->prm);
+    for (auto &g : b->groups) {
+        // FP32 bound from the FP32 state copy: a stability estimate recomputed every step
+        const bool a = b->cur_is_a;
+        B_CUDA(b, dg::launch_dt_lambda_mixed(g.p, a ? g.S0a.ptr : g.S0b.ptr, a ? g.P0a.ptr : g.P0b.ptr, g.geo32.ptr,
+                                             g.conn.ptr, g.fmask.ptr, g.tiles.ptr, g.ntiles, b->dcases.ptr, g.K,
+                                             ph32, static_cast<float>(sf), b->lam.ptr + g.lam_base, b->stream));
+        b->launches += 1;
+    }
+    B_CUDA(b, dg::launch_batch_dt(b->lam.ptr, b->seg.ptr, b->dcases.ptr, n, cfl, b->stream));
+    B_CUDA(b, dg::launch_batch_newmark(b->dcases.ptr, n, b->stream));
+    b->launches += 2;
+    for (int s = 0; s < 5; ++s) {
+        for (auto &g : b->groups) {
+            dg::StageParams sp{};
+            const bool a = b->cur_is_a;
+            sp.K0in = a ? g.K0a.ptr : g.K0b.ptr;
+            sp.K0out = a ? g.K0b.ptr : g.K0a.ptr;
+            sp.K1 = g.K1.ptr;
+            sp.geo = g.geo32.ptr;
+            sp.conn = g.conn.ptr;
+            sp.ops = g.ops32.ptr;
+            sp.fmask = g.fmask.ptr;
+            sp.Sin = a ? g.S0a.ptr : g.S0b.ptr;
+            sp.Pin = a ? g.P0a.ptr : g.P0b.ptr;
+            sp.Sout = a ? g.S0b.ptr : g.S0a.ptr;
+            sp.Pout = a ? g.P0b.ptr : g.P0a.ptr;
+            sp.K = g.K;
+            sp.A = dg::kRkA[s];
+            sp.B = dg::kRkB[s];
+            sp.gm1 = b->prm.gamma - 1.0;
+            sp.sig_fac = sf;
+            sp.mode = dg::STAGE_UPDATE;
+            sp.first_stage = (s == 0) ? 1 : 0;
+            sp.tiles = g.tiles.ptr;
+            sp.cases = b->dcases.ptr;
+            sp.ntiles = g.ntiles;
+            B_CUDA(b, dg::launch_stage_mixed_batch(g.p, g.shape, sp, ph32, b->stream));
+            b->launches += 1;
+        }
+        b->cur_is_a = !b->cur_is_a;
+    }
+    dg_status st = enqueue_forces(b);
+    if (st != DG_OK) return st;
+    if (hist) {
+        B_CUDA(b, dg::launch_batch_record(b->dcases.ptr, n, hist, rows, b->counter.ptr, b->stream));
+        b->launches += 1;
+    }
+    return DG_OK;
+}
+
+bool valid_case(const dg_case &c)
+{
+    return c.p >= 1 && c.p <= 6 && c.vx && c.vy && c.EToV && c.EToE && c.EToF && c.bc && c.K >= 1 && c.Nv >= 3 &&
+           c.mu >= 0.0 && std::isfinite(c.mu) && c.mass > 0.0 && std::isfinite(c.M_r) && std::isfinite(c.C_r) &&
+           std::isfinite(c.K_r) && std::isfinite(c.y0) && std::isfinite(c.ydot0);
+}
+
+}  // namespace
+
+extern "C" {
+
+dg_status dg_batch_create(const dg_params *common, int ncases, const dg_case *cases, dg_batch **out)
+{
+    g_create_err.clear();
+    auto cfail = [](dg_status st, const std::string &msg) {
+        g_create_err = msg;
+        return st;
+    };
+    if (!out) return cfail(DG_EINVAL, "null output");
+    *out = nullptr;
+    if (!common || !cases || ncases < 1) return cfail(DG_EINVAL, "need parameters and ncases >= 1");
+    const dg_params &p = *common;
+    if (!(p.gamma > 1.0) || !(p.Pr > 0.0) || !(p.C1 >= 0.0) || !(p.rho_inf > 0.0) || !(p.p_inf > 0.0))
+        return cfail(DG_EINVAL, "bad common parameters");
+    if (p.theta != 0.0 || p.precision != DG_PRECISION_MIXED)
+        return cfail(DG_EUNSUPPORTED, "the batch runs the mixed-precision IIP kernel only");
+    for (int i = 0; i < ncases; ++i)
+        if (!valid_case(cases[i])) return cfail(DG_EINVAL, "case " + std::to_string(i) + ": bad description");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return cfail(DG_ECUDA, "no CUDA device");
+    }
+    dg_batch *b = new dg_batch();
+    b->prm = p;
+    auto bail = [&](dg_status st, const std::string &msg = "CUDA error while creating the batch") {
+        *out = nullptr;
+        cudaGetLastError();
+        delete b;
+        return cfail(st, msg);
+    };
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(DG_ECUDA);
+    // degree groups in increasing p
+    std::vector<int> degrees;
+    for (int i = 0; i < ncases; ++i) degrees.push_back(cases[i].p);
+    std::sort(degrees.begin(), degrees.end());
+    degrees.erase(std::unique(degrees.begin(), degrees.end()), degrees.end());
+    b->groups.resize(degrees.size());
+    b->cases.resize(ncases);
+    b->init.resize(ncases);
+    std::vector<long long> seg(2 * static_cast<size_t>(ncases));
+    std::vector<int> wseg(2 * static_cast<size_t>(ncases));
+    long long lam_total = 0;
+    int wall_total = 0;
+    for (size_t gi = 0; gi < degrees.size(); ++gi) {
+        Group &g = b->groups[gi];
+        g.p = degrees[gi];
+        if (!dg::build_reference_operators(g.p, g.ops)) return bail(DG_EINVAL);
+        const int Np = g.ops.Np, Nfp = g.ops.Nfp, NF = 3 * Nfp;
+        const int E = dg::stage_tile_elems(g.p);
+        std::vector<double> geo;
+        std::vector<int4> conn;
+        std::vector<int2> walls;
+        std::vector<double> wxy;
+        std::vector<int4> tiles;
+        std::vector<int> ecase;
+        g.lam_base = lam_total;
+        g.wall_base = wall_total;
+        for (int i = 0; i < ncases; ++i) {
+            const dg_case &c = cases[i];
+            if (c.p != g.p) continue;
+            dg::MeshArrays ma;
+            std::string msg;
+            const int mst = dg::build_mesh(g.ops, c.Nv, c.vx, c.vy, c.K, c.EToV, c.EToE, c.EToF, c.bc, ma, msg);
+            if (mst != dg::MESH_OK)
+                return bail((mst == dg::MESH_EINVAL) ? DG_EINVAL : DG_EMESH, "case " + std::to_string(i) + ": " + msg);
+            const long long off = g.K;
+            if (off + c.K > (1LL << 30)) return bail(DG_EINVAL, "too many elements of one degree");
+            CaseHost &ch = b->cases[i];
+            ch.group = static_cast<int>(gi);
+            ch.off = off;
+            ch.K = c.K;
+            ch.p = c.p;
+            ch.vx.assign(c.vx, c.vx + c.Nv);
+            ch.vy.assign(c.vy, c.vy + c.Nv);
+            ch.EToV.assign(c.EToV, c.EToV + c.K * 3);
+            for (auto &cn : ma.conn) {
+                cn.x += static_cast<int>(off);
+                cn.y += static_cast<int>(off);
+                cn.z += static_cast<int>(off);
+            }
+            geo.insert(geo.end(), ma.geo.begin(), ma.geo.end());
+            conn.insert(conn.end(), ma.conn.begin(), ma.conn.end());
+            seg[2 * i] = lam_total + off;
+            seg[2 * i + 1] = lam_total + off + c.K;
+            wseg[2 * i] = wall_total + static_cast<int>(walls.size());
+            for (auto w : ma.walls) walls.push_back(make_int2(w.x + static_cast<int>(off), w.y));
+            wseg[2 * i + 1] = wall_total + static_cast<int>(walls.size());
+            wxy.insert(wxy.end(), ma.wxy.begin(), ma.wxy.end());
+            for (long long k0 = 0; k0 < c.K; k0 += E)
+                tiles.push_back(make_int4(static_cast<int>(off + k0), static_cast<int>(std::min<long long>(E, c.K - k0)),
+                                          i, 0));
+            ecase.insert(ecase.end(), static_cast<size_t>(c.K), i);
+            g.K += c.K;
+            dg::BatchCase &bc = b->init[i];
+            bc = dg::BatchCase{};
+            bc.y = c.y0;
+            bc.yd = c.ydot0;
+            bc.Mr = c.M_r;
+            bc.Cr = c.C_r;
+            bc.Kr = c.K_r;
+            bc.mass = c.mass;
+            bc.mu = c.mu;
+        }
+        g.nwall = static_cast<int>(walls.size());
+        g.ntiles = static_cast<long long>(tiles.size());
+        lam_total += g.K;
+        wall_total += g.nwall;
+        const size_t nd = static_cast<size_t>(g.K) * 4 * Np;
+        const size_t npp = static_cast<size_t>(g.K) * dg::pressure_row(g.p);
+        std::vector<double> o64;
+        o64.insert(o64.end(), g.ops.Dr.begin(), g.ops.Dr.end());
+        o64.insert(o64.end(), g.ops.Ds.begin(), g.ops.Ds.end());
+        o64.insert(o64.end(), g.ops.LIFT.begin(), g.ops.LIFT.end());
+        std::vector<float> o32(o64.begin(), o64.end());
+        std::vector<float> g32(geo.begin(), geo.end());
+        cudaError_t e = cudaSuccess;
+        auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+        chk(g.K0a.alloc(nd));
+        chk(g.K0b.alloc(nd));
+        chk(g.K1.alloc(nd));
+        chk(g.S0a.alloc(static_cast<size_t>(g.K) * Np));
+        chk(g.S0b.alloc(static_cast<size_t>(g.K) * Np));
+        chk(g.P0a.alloc(npp));
+        chk(g.P0b.alloc(npp));
+        chk(g.geo64.alloc(geo.size()));
+        chk(g.geo32.alloc(g32.size()));
+        chk(g.conn.alloc(conn.size()));
+        chk(g.tiles.alloc(tiles.size()));
+        chk(g.elem_case.alloc(ecase.size()));
+        chk(g.ops32.alloc(o32.size()));
+        chk(g.Dr64.alloc(static_cast<size_t>(Np) * Np));
+        chk(g.Ds64.alloc(static_cast<size_t>(Np) * Np));
+        chk(g.fmask.alloc(NF));
+        chk(g.wface.alloc(Nfp));
+        if (g.nwall > 0) {
+            chk(g.walls.alloc(walls.size()));
+            chk(g.fxy.alloc(wxy.size()));
+        }
+        if (e != cudaSuccess) return bail(DG_ECUDA);
+        chk(cudaMemcpy(g.geo64.ptr, geo.data(), geo.size() * sizeof(double), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(g.geo32.ptr, g32.data(), g32.size() * sizeof(float), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(g.conn.ptr, conn.data(), conn.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(g.tiles.ptr, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(g.elem_case.ptr, ecase.data(), ecase.size() * sizeof(int), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(g.ops32.ptr, o32.data(), o32.size() * sizeof(float), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(g.Dr64.ptr, g.ops.Dr.data(), g.ops.Dr.size() * sizeof(double), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(g.Ds64.ptr, g.ops.Ds.data(), g.ops.Ds.size() * sizeof(double), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(g.fmask.ptr, g.ops.Fmask.data(), NF * sizeof(int), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(g.wface.ptr, g.ops.wface.data(), Nfp * sizeof(double), cudaMemcpyHostToDevice));
+        if (g.nwall > 0) {
+            chk(cudaMemcpy(g.walls.ptr, walls.data(), walls.size() * sizeof(int2), cudaMemcpyHostToDevice));
+            chk(cudaMemcpy(g.fxy.ptr, wxy.data(), wxy.size() * sizeof(double), cudaMemcpyHostToDevice));
+        }
+        chk(cudaMemset(g.K0a.ptr, 0, nd * sizeof(double)));
+        chk(cudaMemset(g.K0b.ptr, 0, nd * sizeof(double)));
+        chk(cudaMemset(g.K1.ptr, 0, nd * sizeof(double)));
+        chk(cudaMemset(g.S0a.ptr, 0, static_cast<size_t>(g.K) * Np * sizeof(float4)));
+        chk(cudaMemset(g.S0b.ptr, 0, static_cast<size_t>(g.K) * Np * sizeof(float4)));
+        chk(cudaMemset(g.P0a.ptr, 0, npp * sizeof(float)));
+        chk(cudaMemset(g.P0b.ptr, 0, npp * sizeof(float)));
+        chk(dg::stage_shape_mixed_batch(g.p, g.ntiles, g.shape));
+        if (e != cudaSuccess) return bail(DG_ECUDA);
+    }
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    chk(b->dcases.alloc(ncases));
+    chk(b->lam.alloc(static_cast<size_t>(lam_total)));
+    chk(b->fpart.alloc(static_cast<size_t>(std::max(wall_total, 1)) * 3));
+    chk(b->seg.alloc(seg.size()));
+    chk(b->wseg.alloc(wseg.size()));
+    chk(b->counter.alloc(1));
+    if (e != cudaSuccess) return bail(DG_ECUDA);
+    chk(cudaMemcpy(b->dcases.ptr, b->init.data(), ncases * sizeof(dg::BatchCase), cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(b->seg.ptr, seg.data(), seg.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(b->wseg.ptr, wseg.data(), wseg.size() * sizeof(int), cudaMemcpyHostToDevice));
+    chk(cudaMemset(b->counter.ptr, 0, sizeof(int)));
+    chk(cudaMemset(b->fpart.ptr, 0, b->fpart.n * sizeof(double)));
+    if (e != cudaSuccess) return bail(DG_ECUDA);
+    *out = b;
+    return DG_OK;
+}
+
+dg_status dg_batch_destroy(dg_batch *b)
+{
+    delete b;
+    return DG_OK;
+}
+
+const char *dg_batch_last_error(const dg_batch *b) { return b ? b->err.c_str() : g_create_err.c_str(); }
+
+int64_t dg_batch_kernel_launches(const dg_batch *b) { return b ? b->launches : 0; }
+
+void *dg_batch_stream(const dg_batch *b) { return b ? static_cast<void *>(b->stream) : nullptr; }
+
+dg_status dg_batch_case_size(const dg_batch *b, int i, int64_t *K, int *p)
+{
+    if (!b || i < 0 || i >= static_cast<int>(b->cases.size())) return DG_EINVAL;
+    if (K) *K = b->cases[i].K;
+    if (p) *p = b->cases[i].p;
+    return DG_OK;
+}
+
+dg_status dg_batch_node_coords(const dg_batch *b, int i, double *x, double *y)
+{
+    if (!b || !x || !y || i < 0 || i >= static_cast<int>(b->cases.size())) return DG_EINVAL;
+    const CaseHost &c = b->cases[i];
+    const dg::RefOps &o = b->groups[c.group].ops;
+    for (long long k = 0; k < c.K; ++k) {
+        const int32_t v0 = c.EToV[k * 3], v1 = c.EToV[k * 3 + 1], v2 = c.EToV[k * 3 + 2];
+        for (int n = 0; n < o.Np; ++n) {
+            const double r = o.r[n], s = o.s[n];
+            x[k * o.Np + n] = 0.5 * (-(r + s) * c.vx[v0] + (1 + r) * c.vx[v1] + (1 + s) * c.vx[v2]);
+            y[k * o.Np + n] = 0.5 * (-(r + s) * c.vy[v0] + (1 + r) * c.vy[v1] + (1 + s) * c.vy[v2]);
+        }
+    }
+    return DG_OK;
+}
+
+dg_status dg_batch_set_state(dg_batch *b, int i, const double *U, int on_device)
+{
+    if (!b) return DG_EINVAL;
+    b->err.clear();
+    if (!U || i < 0 || i >= static_cast<int>(b->cases.size())) return bfail(b, DG_EINVAL, "bad case or null state");
+    const CaseHost &c = b->cases[i];
+    Group &g = b->groups[c.group];
+    const int Np = g.ops.Np;
+    const size_t off = static_cast<size_t>(c.off) * 4 * Np, n = static_cast<size_t>(c.K) * 4 * Np;
+    double *cur = b->cur_is_a ? g.K0a.ptr : g.K0b.ptr;
+    float4 *S = b->cur_is_a ? g.S0a.ptr : g.S0b.ptr;
+    float *P = b->cur_is_a ? g.P0a.ptr : g.P0b.ptr;
+    B_CUDA(b, cudaMemcpyAsync(cur + off, U, n * sizeof(double),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream));
+    B_CUDA(b, cudaMemsetAsync(g.K1.ptr + off, 0, n * sizeof(double), b->stream));
+    B_CUDA(b, dg::launch_make_shadow(g.p, cur + off, c.K, b->prm.gamma - 1.0, S + c.off * Np,
+                                     P + c.off * dg::pressure_row(g.p), b->stream));
+    b->launches += 1;
+    b->forces_stale = true;
+    B_CUDA(b, cudaStreamSynchronize(b->stream));
+    return DG_OK;
+}
+
+dg_status dg_batch_get_state(dg_batch *b, int i, double *U, int on_device)
+{
+    if (!b) return DG_EINVAL;
+    b->err.clear();
+    if (!U || i < 0 || i >= static_cast<int>(b->cases.size())) return bfail(b, DG_EINVAL, "bad case or null state");
+    const CaseHost &c = b->cases[i];
+    Group &g = b->groups[c.group];
+    const int Np = g.ops.Np;
+    const size_t off = static_cast<size_t>(c.off) * 4 * Np, n = static_cast<size_t>(c.K) * 4 * Np;
+    const double *cur = b->cur_is_a ? g.K0a.ptr : g.K0b.ptr;
+    B_CUDA(b, cudaMemcpyAsync(U, cur + off, n * sizeof(double),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
+    B_CUDA(b, cudaStreamSynchronize(b->stream));
+    return DG_OK;
+}
+
+dg_status dg_batch_reset_history(dg_batch *b)
+{
+    if (!b) return DG_EINVAL;
+    b->err.clear();
+    B_CUDA(b, cudaMemsetAsync(b->counter.ptr, 0, sizeof(int), b->stream));
+    B_CUDA(b, cudaStreamSynchronize(b->stream));
+    return DG_OK;
+}
+
+dg_status dg_batch_run(dg_batch *b, double cfl, int nsteps, int use_graph, double *hist, int hist_rows)
+{
+    if (!b) return DG_EINVAL;
+    b->err.clear();
+    if (!(cfl > 0.0) || !std::isfinite(cfl) || nsteps < 0 || (hist && hist_rows < 0))
+        return bfail(b, DG_EINVAL, "need cfl > 0, nsteps >= 0, hist_rows >= 0");
+    if (b->forces_stale) {
+        dg_status st = enqueue_forces(b);
+        if (st != DG_OK) return st;
+        b->forces_stale = false;
+    }
+    if (use_graph && nsteps > 0) {
+        if (b->graph_cfl != cfl || b->graph_hist != hist || b->graph_rows != hist_rows) {
+            b->drop_graphs();
+            b->graph_cfl = cfl;
+            b->graph_hist = hist;
+            b->graph_rows = hist_rows;
+        }
+        for (int n = 0; n < nsteps; ++n) {
+            const int which = b->cur_is_a ? 0 : 1;
+            if (!b->graph[which]) {
+                // capture one step starting from the current buffers; the step
+                // flips the buffer parity (five stages), as a replay will
+                const bool start_a = b->cur_is_a;
+                const int64_t l0 = b->launches;
+                B_CUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+                dg_status st = enqueue_step(b, cfl, hist, hist_rows);
+                cudaGraph_t gr = nullptr;
+                cudaError_t e = cudaStreamEndCapture(b->stream, &gr);
+                b->launches = l0;
+                b->cur_is_a = start_a;
+                if (st != DG_OK) {
+                    if (gr) cudaGraphDestroy(gr);
+                    return st;
+                }
+                if (e != cudaSuccess) return bcuda(b, e, "cudaStreamEndCapture");
+                e = cudaGraphInstantiate(&b->graph[which], gr, 0);
+                cudaGraphDestroy(gr);
+                if (e != cudaSuccess) return bcuda(b, e, "cudaGraphInstantiate");
+                // kernels per replay: dt per group, dt reduce, Newmark, 5 stages per group,
+                // forces per group with walls, force sum, record
+                int64_t per = static_cast<int64_t>(b->groups.size()) * 6 + 3 + (hist ? 1 : 0);
+                for (auto &g : b->groups) per += (g.nwall > 0) ? 1 : 0;
+                b->graph_launches = per;
+            }
+            B_CUDA(b, cudaGraphLaunch(b->graph[which], b->stream));
+            b->launches += b->graph_launches;
+            b->cur_is_a = !b->cur_is_a;
+        }
+    } else {
+        for (int n = 0; n < nsteps; ++n) {
+            dg_status st = enqueue_step(b, cfl, hist, hist_rows);
+            if (st != DG_OK) return st;
+        }
+    }
+    B_CUDA(b, cudaStreamSynchronize(b->stream));
+    std::vector<dg::BatchCase> h(b->cases.size());
+    B_CUDA(b, cudaMemcpy(h.data(), b->dcases.ptr, h.size() * sizeof(dg::BatchCase), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < h.size(); ++i)
+        if (h[i].bad) return bfail(b, DG_ENONFINITE, "case " + std::to_string(i) + " met a non-finite time-step bound");
+    return DG_OK;
+}
+
+dg_status dg_batch_rigid(dg_batch *b, double *out)
+{
+    if (!b) return DG_EINVAL;
+    b->err.clear();
+    if (!out) return bfail(b, DG_EINVAL, "null output");
+    B_CUDA(b, cudaStreamSynchronize(b->stream));
+    std::vector<dg::BatchCase> h(b->cases.size());
+    B_CUDA(b, cudaMemcpy(h.data(), b->dcases.ptr, h.size() * sizeof(dg::BatchCase), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < h.size(); ++i) {
+        double *o = out + i * 10;
+        o[0] = h[i].t; o[1] = h[i].dt; o[2] = h[i].y; o[3] = h[i].yd; o[4] = h[i].ydd;
+        o[5] = h[i].vb; o[6] = h[i].Fx; o[7] = h[i].Fy; o[8] = h[i].Mz; o[9] = h[i].bad;
+    }
+    return DG_OK;
+}
+
+}  // extern "C"

@@ -15,47 +15,18 @@
 
 #include "../../include/dg.h"
 #include "dg_stage.cuh"
+#include "devbuf.h"
 #include "launch.h"
+#include "mesh.h"
 #include "refops.h"
+#include "rigid.h"
+#include "rk.h"
 
 namespace {
 
-// Carpenter & Kennedy (1994), five-stage fourth-order 2N-storage scheme:
-// the coefficients A_i, B_i, c_i of Algorithm 1.
-const double kRkA[5] = {0.0,
-                        -567301805773.0 / 1357537059087.0,
-                        -2404267990393.0 / 2016746695238.0,
-                        -3550918686646.0 / 2091501179385.0,
-                        -1275806237668.0 / 842570457699.0};
-const double kRkB[5] = {1432997174477.0 / 9575080441755.0,
-                        5161836677717.0 / 13612068292357.0,
-                        1720146321549.0 / 2090206949498.0,
-                        3134564353537.0 / 4481467310338.0,
-                        2277821191437.0 / 14882151754819.0};
-const double kRkC[5] = {0.0,
-                        1432997174477.0 / 9575080441755.0,
-                        2526269341429.0 / 6820363962896.0,
-                        2006345519317.0 / 3224310063776.0,
-                        2802321613138.0 / 2924317926251.0};
-
-template <typename T>
-struct DevBuf {
-    T *ptr = nullptr;
-    size_t n = 0;
-    cudaError_t alloc(size_t count)
-    {
-        release();
-        n = count;
-        if (count == 0) return cudaSuccess;
-        return cudaMalloc(reinterpret_cast<void **>(&ptr), count * sizeof(T));
-    }
-    void release()
-    {
-        if (ptr) cudaFree(ptr);
-        ptr = nullptr;
-        n = 0;
-    }
-};
+using dg::kRkA;
+using dg::kRkB;
+using dg::kRkC;
 
 }  // namespace
 
@@ -71,12 +42,12 @@ struct dg_ctx {
     std::vector<int32_t> EToV;
     std::vector<double> geo64h;
     // device
-    DevBuf<double> K0a, K0b, K1, rtmp, geo64, ops64, Dr64, Ds64, src, lam, scal, fpart, fxy, wface;
-    DevBuf<float> geo32, ops32, P0a, P0b;     // mixed path: pressures of the two K0 buffers
-    DevBuf<float4> S0a, S0b;                  // mixed path: FP32 copies of the two K0 buffers
-    DevBuf<int4> conn;
-    DevBuf<int> fmask, flag;
-    DevBuf<int2> wall;
+    dg::DevBuf<double> K0a, K0b, K1, rtmp, geo64, ops64, Dr64, Ds64, src, lam, scal, fpart, fxy, wface;
+    dg::DevBuf<float> geo32, ops32, P0a, P0b;     // mixed path: pressures of the two K0 buffers
+    dg::DevBuf<float4> S0a, S0b;                  // mixed path: FP32 copies of the two K0 buffers
+    dg::DevBuf<int4> conn;
+    dg::DevBuf<int> fmask, flag;
+    dg::DevBuf<int2> wall;
     int nwall = 0;
     bool cur_is_a = true;
     dg::LaunchShape shape;
@@ -314,84 +285,16 @@ dg_status dg_set_mesh(dg_ctx *c, int64_t Nv, const double *vx, const double *vy,
 {
     if (!c) return DG_EINVAL;
     c->err.clear();
-    if (!vx || !vy || !EToV || !EToE || !EToF || !bc) return fail(c, DG_EINVAL, "null mesh array");
-    if (K < 1 || Nv < 3) return fail(c, DG_EINVAL, "need K >= 1 and Nv >= 3");
-    const int Np = c->ops.Np, Nfp = c->ops.Nfp;
-    if (K * 4LL * Np > (1LL << 40)) return fail(c, DG_EINVAL, "mesh too large");
-    // --- index checks and geometry
-    std::vector<double> geo(static_cast<size_t>(K) * 16, 0.0);
-    double scale = 0.0;
-    for (int64_t i = 0; i < Nv; ++i) scale = std::max(scale, std::max(std::fabs(vx[i]), std::fabs(vy[i])));
-    if (!(scale > 0.0) || !std::isfinite(scale)) return fail(c, DG_EMESH, "vertex coordinates not finite");
-    for (int64_t k = 0; k < K; ++k) {
-        int32_t v[3] = {EToV[k * 3], EToV[k * 3 + 1], EToV[k * 3 + 2]};
-        for (int f = 0; f < 3; ++f) {
-            if (v[f] < 0 || v[f] >= Nv) return fail(c, DG_EMESH, "EToV index out of range at element " + std::to_string(k));
-            int32_t e2 = EToE[k * 3 + f], f2 = EToF[k * 3 + f], b = bc[k * 3 + f];
-            if (e2 < 0 || e2 >= K || f2 < 0 || f2 > 2 || b < 0 || b > 2)
-                return fail(c, DG_EMESH, "EToE/EToF/bc out of range at element " + std::to_string(k));
-        }
-        double x1 = vx[v[0]], y1 = vy[v[0]], x2 = vx[v[1]], y2 = vy[v[1]], x3 = vx[v[2]], y3 = vy[v[2]];
-        double xr = 0.5 * (x2 - x1), xs = 0.5 * (x3 - x1), yr = 0.5 * (y2 - y1), ys = 0.5 * (y3 - y1);
-        double J = xr * ys - xs * yr;
-        if (!(J > 1e-14 * scale * scale))
-            return fail(c, DG_EMESH, "element " + std::to_string(k) + " is clockwise or degenerate");
-        double rx = ys / J, ry = -xs / J, sx = -yr / J, sy = xr / J;
-        double *g = &geo[k * 16];
-        g[dg::G_RX] = rx; g[dg::G_RY] = ry; g[dg::G_SX] = sx; g[dg::G_SY] = sy; g[dg::G_J] = J;
-        // outward normals from the metric: face 0 (s = -1): -grad s; face 1 (r+s = 0): grad(r+s);
-        // face 2 (r = -1): -grad r; sJ = |grad| J
-        double nn[3][2] = {{-sx, -sy}, {rx + sx, ry + sy}, {-rx, -ry}};
-        for (int f = 0; f < 3; ++f) {
-            double len = std::hypot(nn[f][0], nn[f][1]);
-            g[dg::G_NX + f] = nn[f][0] / len;
-            g[dg::G_NY + f] = nn[f][1] / len;
-            g[dg::G_FS + f] = len;          // Fscale = sJ / J = |grad| (since sJ = |grad| J)
-        }
-    }
-    // --- reciprocity and face matching
-    std::vector<int4> conn(K);
-    for (int64_t k = 0; k < K; ++k) {
-        int packed = 0;
-        int nb[3];
-        for (int f = 0; f < 3; ++f) {
-            int32_t e2 = EToE[k * 3 + f], f2 = EToF[k * 3 + f], b = bc[k * 3 + f];
-            nb[f] = e2;
-            packed |= (f2 & 3) << (2 * f);
-            packed |= (b & 3) << (8 + 2 * f);
-            if (b != DG_BC_INTERIOR) {
-                if (e2 != k || f2 != f) return fail(c, DG_EMESH, "boundary face must name itself at element " + std::to_string(k));
-                continue;
-            }
-            if (e2 == k) return fail(c, DG_EMESH, "interior face names its own element " + std::to_string(k));
-            if (EToE[e2 * 3 + f2] != k || EToF[e2 * 3 + f2] != f || bc[e2 * 3 + f2] != DG_BC_INTERIOR)
-                return fail(c, DG_EMESH, "faces not reciprocal at element " + std::to_string(k));
-            // conforming, counter-clockwise: own (a, b) meets neighbour (b', a') up to one translation
-            int32_t a = EToV[k * 3 + f], bb = EToV[k * 3 + (f + 1) % 3];
-            int32_t a2 = EToV[e2 * 3 + f2], b2 = EToV[e2 * 3 + (f2 + 1) % 3];
-            double tx1 = vx[a] - vx[b2], ty1 = vy[a] - vy[b2];
-            double tx2 = vx[bb] - vx[a2], ty2 = vy[bb] - vy[a2];
-            double tol = 1e-9 * scale;
-            if (std::fabs(tx1 - tx2) > tol || std::fabs(ty1 - ty2) > tol)
-                return fail(c, DG_EMESH, "face nodes do not match at element " + std::to_string(k));
-        }
-        conn[k] = make_int4(nb[0], nb[1], nb[2], packed);
-    }
-    // --- wall faces and their node coordinates
-    std::vector<int2> walls;
-    std::vector<double> wxy;
-    for (int64_t k = 0; k < K; ++k)
-        for (int f = 0; f < 3; ++f)
-            if (bc[k * 3 + f] == DG_BC_WALL) {
-                walls.push_back(make_int2(static_cast<int>(k), f));
-                int32_t v0 = EToV[k * 3], v1 = EToV[k * 3 + 1], v2 = EToV[k * 3 + 2];
-                for (int i = 0; i < Nfp; ++i) {
-                    int vm = c->ops.Fmask[f * Nfp + i];
-                    double r = c->ops.r[vm], s = c->ops.s[vm];
-                    wxy.push_back(0.5 * (-(r + s) * vx[v0] + (1 + r) * vx[v1] + (1 + s) * vx[v2]));
-                    wxy.push_back(0.5 * (-(r + s) * vy[v0] + (1 + r) * vy[v1] + (1 + s) * vy[v2]));
-                }
-            }
+    dg::MeshArrays ma;
+    std::string msg;
+    const int mst = dg::build_mesh(c->ops, Nv, vx, vy, K, EToV, EToE, EToF, bc, ma, msg);
+    if (mst == dg::MESH_EINVAL) return fail(c, DG_EINVAL, msg);
+    if (mst != dg::MESH_OK) return fail(c, DG_EMESH, msg);
+    const int Np = c->ops.Np;
+    std::vector<double> &geo = ma.geo;
+    std::vector<int4> &conn = ma.conn;
+    std::vector<int2> &walls = ma.walls;
+    std::vector<double> &wxy = ma.wxy;
     // --- device buffers
     c->K = K;
     const size_t nd = static_cast<size_t>(K) * 4 * Np;
@@ -607,22 +510,13 @@ dg_status dg_check_finite(dg_ctx *c, int *ok)
 
 dg_status dg_rigid_step(const double coeff[3], double F, double dt, double state[3], double *v_b)
 {
-    // Newmark average acceleration (beta = 1/4, gamma = 1/2) for
-    // M y'' + C y' + K y = F: solve for the new acceleration from the
-    // effective equation, then update displacement and velocity.
     if (!coeff || !state || !v_b || !(dt > 0.0)) return DG_EINVAL;
-    const double M = coeff[0], C = coeff[1], Kr = coeff[2];
-    const double y = state[0], yd = state[1], ydd = state[2];
-    const double meff = M + 0.5 * dt * C + 0.25 * dt * dt * Kr;
-    if (!(std::fabs(meff) > 0.0)) return DG_EINVAL;
-    const double rhs = F - C * (yd + 0.5 * dt * ydd) - Kr * (y + dt * yd + 0.25 * dt * dt * ydd);
-    const double a = rhs / meff;
-    const double yn = y + dt * yd + 0.25 * dt * dt * (ydd + a);
-    const double vn = yd + 0.5 * dt * (ydd + a);
-    *v_b = (yn - y) / dt;
-    state[0] = yn;
-    state[1] = vn;
-    state[2] = a;
+    double y = state[0], yd = state[1], ydd = state[2], vb = 0.0;
+    if (!dg::newmark_step(coeff[0], coeff[1], coeff[2], F, dt, y, yd, ydd, vb)) return DG_EINVAL;
+    *v_b = vb;
+    state[0] = y;
+    state[1] = yd;
+    state[2] = ydd;
     return DG_OK;
 }
 

@@ -32,6 +32,20 @@ namespace dg {
 enum { STAGE_UPDATE = 0, STAGE_RHS_ONLY = 1 };
 enum { BCT_INTERIOR = 0, BCT_WALL = 1, BCT_FARFIELD = 2 };
 
+// Per-case quantities of a batch of independent cases (Algorithm 3 state kept
+// on the device): time step and time, rigid-body state with its mesh
+// velocity v_b, oscillator coefficients, latest wall forces, viscosity.
+struct BatchCase {
+    double dt, t;
+    double y, yd, ydd, vb;        // transverse displacement, velocity, acceleration; v_b
+    double Mr, Cr, Kr, mass;      // M_r y'' + C_r y' + K_r y = F_r with F_r = lift / mass
+    double Fx, Fy, Mz;            // drag, lift, moment of the last force evaluation
+    double mu;                    // viscosity of the case
+    double lam;                   // max_K Lambda_K of the last time-step bound
+    int bad;                      // set once the bound was not finite (the case is frozen)
+    int pad;
+};
+
 struct StageParams {
     const double *K0in;
     double *K0out;
@@ -54,6 +68,11 @@ struct StageParams {
     double uinf[4];            // far-field conserved state in FP64 (mixed theta variant)
     int mode;
     int first_stage;           // A == 0: K1 is not read
+    // batch variant: tile table (first element, element count, case, 0), the
+    // per-case quantities (dt, v_b, mu are read per tile) and the tile count
+    const int4 *tiles;
+    const BatchCase *cases;
+    long long ntiles;
 };
 
 template <int P>

@@ -84,7 +84,7 @@ struct MixedLayout {
 __device__ __forceinline__ void f4_to(const float4 &a, float o[4]) { o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; }
 __device__ __forceinline__ float4 to_f4(const float o[4]) { return make_float4(o[0], o[1], o[2], o[3]); }
 
-template <int P, bool TH>
+template <int P, bool TH, bool BATCH = false>
 __global__ void __launch_bounds__(Shape<P>::NT, TH ? 2 : 3)
 stage_mixed_kernel(StageParams sp, Phys<float> ph)
 {
@@ -126,12 +126,12 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
     }
     const float *geo = static_cast<const float *>(sp.geo);
     const long long K = sp.K;
-    const long long ntiles = (K + E - 1) / E;
+    const long long ntiles = BATCH ? sp.ntiles : (K + E - 1) / E;
     const double gm1d = sp.gm1;
     const float cinv_fac = 0.5f * float(P + 1) * float(P + 2);
     const float sig_fac = static_cast<float>(sp.sig_fac);
     const float theta = static_cast<float>(sp.theta);
-    const float dtr = static_cast<float>(sp.dt);
+    float dtr = static_cast<float>(sp.dt);
     const bool update = sp.mode == STAGE_UPDATE;
     const bool need_k1 = update && !sp.first_stage;
     __syncthreads();
@@ -141,8 +141,19 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
     const int ff = fm / Nfp, fi = fm - (fm / Nfp) * Nfp;
 
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const long long k0 = tile * E;
-        const int ne = static_cast<int>((K - k0) < E ? (K - k0) : E);
+        long long k0 = tile * E;
+        int ne = static_cast<int>((K - k0) < E ? (K - k0) : E);
+        if constexpr (BATCH) {
+            // tiles never straddle two cases: take the case's viscosity, mesh
+            // velocity (transverse, from its Newmark step) and time step
+            const int4 td = sp.tiles[tile];
+            k0 = td.x;
+            ne = td.y;
+            const BatchCase &cs = sp.cases[td.z];
+            ph.mu = static_cast<float>(cs.mu);
+            ph.vw2 = static_cast<float>(cs.vb);
+            dtr = static_cast<float>(cs.dt);
+        }
         // ---- P1a: connectivity of the tile (needed to address the neighbours)
         if (tid < ne) sConn[tid] = sp.conn[k0 + tid];
         __syncthreads();
@@ -453,6 +464,107 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
                 sp.Pout[(k0 + ve) * NpP + vi] = pressure<float>(un, knew[3], gm1d);
             }
         }
+    }
+}
+
+// Lambda_K of Eq. rayleigh_bound in FP32 from the FP32 state copy and the
+// FP64-recovered pressures, one block per tile (same node / face-node thread
+// map as the stage kernel).  Same readings as the FP64 time-step kernel:
+// C_inv,2 = p^4 / rho_K^2 with rho_K = 2|K| / perimeter, G_K and sigma_K the
+// largest over the faces of K, C_inv,K the largest over its faces, beta_K the
+// largest |b_ns|_2 over its nodes, beta'_K = 0.  Batch: the tile table gives
+// the elements and the case (mu, v_b); otherwise tiles are E consecutive
+// elements and ph holds mu and v_w.
+template <int P>
+__global__ void __launch_bounds__(Shape<P>::NT)
+dt_lambda_mixed_kernel(const float4 *S, const float *Pr, const float *geo, const int4 *conn, const int *fmask,
+                       const int4 *tiles, const BatchCase *cases, long long K, Phys<float> ph, float sig_fac,
+                       double *lam)
+{
+    using Sh = Shape<P>;
+    constexpr int Np = Sh::Np, Nfp = Sh::Nfp, NF = Sh::NF, E = Sh::E, NT = Sh::NT;
+    constexpr int NpP = (Np + 3) & ~3;
+    __shared__ float sNorm[E * NF];
+    __shared__ float sBeta[E * Np];
+    __shared__ int sFm[NF];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < NF; i += NT) sFm[i] = fmask[i];
+    long long k0 = static_cast<long long>(blockIdx.x) * E;
+    int ne = static_cast<int>((K - k0) < E ? (K - k0) : E);
+    if (tiles) {
+        const int4 td = tiles[blockIdx.x];
+        k0 = td.x;
+        ne = td.y;
+        ph.mu = static_cast<float>(cases[td.z].mu);
+        ph.vw2 = static_cast<float>(cases[td.z].vb);
+    }
+    __syncthreads();
+    const int fe = tid / NF, fm = tid - (tid / NF) * NF;
+    if (fe < ne) {
+        const long long k = k0 + fe;
+        const int ff = fm / Nfp, fi = fm - ff * Nfp;
+        const int4 cn = conn[k];
+        const int f2 = (cn.w >> (2 * ff)) & 3, bt = (cn.w >> (8 + 2 * ff)) & 3;
+        const int vm = sFm[ff * Nfp + fi], vp = sFm[f2 * Nfp + (Nfp - 1 - fi)];
+        const float *g = geo + k * 16;
+        const float n1 = g[G_NX + ff], n2 = g[G_NY + ff];
+        const float4 u = S[k * Np + vm];
+        const float ir = 1.0f / u.x;
+        const float a = penalty_norm(u.x, u.y * ir, u.z * ir, u.w * ir, n1, n2, ph);
+        float b;
+        if (bt == BCT_INTERIOR) {
+            const long long nb = (ff == 0) ? cn.x : (ff == 1 ? cn.y : cn.z);
+            const float4 w = S[nb * Np + vp];
+            const float iw = 1.0f / w.x;
+            b = penalty_norm(w.x, w.y * iw, w.z * iw, w.w * iw, n1, n2, ph);
+        } else if (bt == BCT_FARFIELD) {
+            const float iw = 1.0f / ph.Uinf[0];
+            b = penalty_norm(ph.Uinf[0], ph.Uinf[1] * iw, ph.Uinf[2] * iw, ph.Uinf[3] * iw, n1, n2, ph);
+        } else {
+            const float pw = Pr[k * NpP + vm];
+            const float eb = (pw / ph.gm1 + 0.5f * u.x * (ph.vw1 * ph.vw1 + ph.vw2 * ph.vw2)) * ir;
+            b = penalty_norm(u.x, ph.vw1, ph.vw2, eb, n1, n2, ph);
+        }
+        sNorm[fe * NF + fm] = fmaxf(a, b);
+    }
+    const int ve = tid / Np, vi = tid - (tid / Np) * Np;
+    if (ve < ne) {
+        const long long k = k0 + ve;
+        const float4 u = S[k * Np + vi];
+        const float ir = 1.0f / u.x;
+        const float c = sqrtf(ph.gamma * Pr[k * NpP + vi] * ir);
+        const float b1 = fabsf(u.y * ir - ph.vw1) + c, b2 = fabsf(u.z * ir - ph.vw2) + c;
+        sBeta[ve * Np + vi] = sqrtf(b1 * b1 + b2 * b2);
+    }
+    __syncthreads();
+    if (tid < ne) {
+        const long long k = k0 + tid;
+        const float *g = geo + k * 16;
+        const int4 cn = conn[k];
+        const float pp = float((P + 1) * (P + 2));
+        float GK = 0.f, sigK = 0.f, ciK = 0.f, perim = 0.f, beta = 0.f;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            float gbar = 0.f;
+            for (int i = 0; i < Nfp; ++i) gbar = fmaxf(gbar, sNorm[tid * NF + f * Nfp + i]);
+            const float fs = g[G_FS + f];
+            const float ci = 0.5f * pp * fs;
+            float cmax = ci;
+            if (((cn.w >> (8 + 2 * f)) & 3) == BCT_INTERIOR) {
+                const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
+                const int f2 = (cn.w >> (2 * f)) & 3;
+                cmax = fmaxf(ci, 0.5f * pp * geo[nb * 16 + G_FS + f2]);
+            }
+            GK = fmaxf(GK, gbar);
+            sigK = fmaxf(sigK, sig_fac * gbar * cmax);
+            ciK = fmaxf(ciK, ci);
+            perim += 2.0f * fs * g[G_J];
+        }
+        for (int i = 0; i < Np; ++i) beta = fmaxf(beta, sBeta[tid * Np + i]);
+        const float rhoK = 2.0f * (2.0f * g[G_J]) / perim;
+        const float p4 = float(P) * float(P) * float(P) * float(P);
+        const float cinv2 = p4 / (rhoK * rhoK);
+        lam[k] = cvt_f2d(1.5f * cinv2 * GK + 3.0f * ciK * (3.0f * sigK + beta));
     }
 }
 

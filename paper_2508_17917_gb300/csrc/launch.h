@@ -8,6 +8,7 @@
 namespace dg {
 
 struct StageParams;
+struct BatchCase;
 
 struct LaunchShape {
     bool theta = false;      // kernel variant with the theta terms of the IP flux
@@ -25,14 +26,30 @@ cudaError_t launch_stage_fp64(int p, const LaunchShape &ls, const StageParams &s
                               const Phys<double> &ph, cudaStream_t st);
 cudaError_t launch_stage_mixed(int p, const LaunchShape &ls, const StageParams &sp,
                                const Phys<float> &ph, cudaStream_t st);
+// batch variant of the mixed kernel (IIP): grid for `ntiles` tiles of a tile table
+cudaError_t stage_shape_mixed_batch(int p, long long ntiles, LaunchShape &out);
+cudaError_t launch_stage_mixed_batch(int p, const LaunchShape &ls, const StageParams &sp,
+                                     const Phys<float> &ph, cudaStream_t st);
+// Lambda_K in FP32 from the FP32 state copy (mixed path); tiles == nullptr:
+// K elements in tiles of E, ph carries mu and v_w; otherwise the batch tile
+// table and per-case mu, v_b
+cudaError_t launch_dt_lambda_mixed(int p, const float4 *S, const float *Pr, const float *geo, const int4 *conn,
+                                   const int *fmask, const int4 *tiles, long long ntiles, const BatchCase *cases,
+                                   long long K, const Phys<float> &ph, float sig_fac, double *lam, cudaStream_t st);
+// elements per tile of the mixed kernel for degree p
+int stage_tile_elems(int p);
 // FP32 copy [K][Np] float4 and FP64-recovered pressure [K][NpP] of a state
 cudaError_t launch_make_shadow(int p, const double *K0, long long K, double gm1, float4 *S,
                                float *Pr, cudaStream_t st);
 // padded pressure row length: Np rounded up to a multiple of 4
 inline int pressure_row(int p) { return (((p + 1) * (p + 2) / 2) + 3) & ~3; }
 
+struct BatchCase;
+
 struct AuxMesh {
     const double *U;          // [K][4][Np]
+    const int *elem_case = nullptr;         // batch: case of every element (mu, v_b)
+    const BatchCase *cases = nullptr;
     const double *geo;        // double[16] per element
     const int4 *conn;
     const double *Dr, *Ds;    // Np*Np
@@ -53,6 +70,19 @@ cudaError_t launch_wall_force_faces(const AuxMesh &m, const Phys<double> &ph, co
                                     const double *face_xy, const double *wface, int nwall,
                                     double xc, double yc, double *partial, cudaStream_t st);
 cudaError_t launch_sum3(const double *partial, int n, double *out, cudaStream_t st);
+
+// batch: one block per case, max of lam over the case's element range
+// [seg[2i], seg[2i+1]) -> cases[i].lam and dt = cfl / lam (0 and bad = 1 if not finite)
+cudaError_t launch_batch_dt(const double *lam, const long long *seg, BatchCase *cases, int ncases, double cfl,
+                            cudaStream_t st);
+// batch: Newmark step of every case with its lagged lift and its dt; sets v_b, advances t
+cudaError_t launch_batch_newmark(BatchCase *cases, int ncases, cudaStream_t st);
+// batch: one block per case, sum of the wall-face partials [wseg[2i], wseg[2i+1]) -> Fx, Fy, Mz
+cudaError_t launch_batch_forces(const double *partial, const int *wseg, BatchCase *cases, int ncases,
+                                cudaStream_t st);
+// batch: append (t, dt, y, y', v_b, Fx, Fy, lam) of every case to hist at row *counter, then ++*counter
+cudaError_t launch_batch_record(const BatchCase *cases, int ncases, double *hist, int cap, int *counter,
+                                cudaStream_t st);
 
 // *flag = 1 if any of x[0..n) is not finite (flag must be zeroed first)
 cudaError_t launch_nonfinite(const double *x, long long n, int *flag, cudaStream_t st);

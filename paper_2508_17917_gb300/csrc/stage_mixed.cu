@@ -43,6 +43,38 @@ cudaError_t launch_p(const LaunchShape &ls, const StageParams &sp, const Phys<fl
 }
 
 template <int P>
+cudaError_t shape_batch_p(long long ntiles, LaunchShape &ls)
+{
+    using L = MixedLayout<P, false>;
+    auto kern = stage_mixed_kernel<P, false, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(L::bytes));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Shape<P>::NT, L::bytes);
+    if (e != cudaSuccess) return e;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (per_sm < 1) per_sm = 1;
+    long long grid = static_cast<long long>(sms) * per_sm;
+    ls.grid = static_cast<int>(ntiles < grid ? ntiles : grid);
+    ls.threads = Shape<P>::NT;
+    ls.smem = L::bytes;
+    ls.elems_per_tile = Shape<P>::E;
+    ls.theta = false;
+    return cudaSuccess;
+}
+
+template <int P>
+cudaError_t launch_batch_p(const LaunchShape &ls, const StageParams &sp, const Phys<float> &ph, cudaStream_t st)
+{
+    stage_mixed_kernel<P, false, true><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
+    return cudaGetLastError();
+}
+
+template <int P>
 cudaError_t shadow_p(const double *K0, long long K, double gm1, float4 *S, float *Pr, cudaStream_t st)
 {
     constexpr int Np = (P + 1) * (P + 2) / 2;
@@ -78,6 +110,55 @@ cudaError_t launch_stage_mixed(int p, const LaunchShape &ls, const StageParams &
 #define C_(P) launch_p<P>(ls, sp, ph, st)
     DG_SWITCH_P(p, C_)
 #undef C_
+}
+
+cudaError_t stage_shape_mixed_batch(int p, long long ntiles, LaunchShape &out)
+{
+#define C_(P) shape_batch_p<P>(ntiles, out)
+    DG_SWITCH_P(p, C_)
+#undef C_
+}
+
+cudaError_t launch_stage_mixed_batch(int p, const LaunchShape &ls, const StageParams &sp,
+                                     const Phys<float> &ph, cudaStream_t st)
+{
+#define C_(P) launch_batch_p<P>(ls, sp, ph, st)
+    DG_SWITCH_P(p, C_)
+#undef C_
+}
+
+template <int P>
+cudaError_t dt_mixed_p(const float4 *S, const float *Pr, const float *geo, const int4 *conn, const int *fmask,
+                       const int4 *tiles, long long ntiles, const BatchCase *cases, long long K,
+                       const Phys<float> &ph, float sig_fac, double *lam, cudaStream_t st)
+{
+    const long long nblk = tiles ? ntiles : (K + Shape<P>::E - 1) / Shape<P>::E;
+    if (nblk < 1) return cudaSuccess;
+    dt_lambda_mixed_kernel<P><<<static_cast<unsigned>(nblk), Shape<P>::NT, 0, st>>>(S, Pr, geo, conn, fmask, tiles,
+                                                                                   cases, K, ph, sig_fac, lam);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dt_lambda_mixed(int p, const float4 *S, const float *Pr, const float *geo, const int4 *conn,
+                                   const int *fmask, const int4 *tiles, long long ntiles, const BatchCase *cases,
+                                   long long K, const Phys<float> &ph, float sig_fac, double *lam, cudaStream_t st)
+{
+#define C_(P) dt_mixed_p<P>(S, Pr, geo, conn, fmask, tiles, ntiles, cases, K, ph, sig_fac, lam, st)
+    DG_SWITCH_P(p, C_)
+#undef C_
+}
+
+int stage_tile_elems(int p)
+{
+    switch (p) {
+    case 1: return Shape<1>::E;
+    case 2: return Shape<2>::E;
+    case 3: return Shape<3>::E;
+    case 4: return Shape<4>::E;
+    case 5: return Shape<5>::E;
+    case 6: return Shape<6>::E;
+    default: return 0;
+    }
 }
 
 cudaError_t launch_make_shadow(int p, const double *K0, long long K, double gm1, float4 *S, float *Pr,

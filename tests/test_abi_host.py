@@ -1,5 +1,5 @@
 """CPU tests of the C-ABI library: it loads, exports every symbol declared in
-include/dg.h, and its host-only entry points agree with the oracle.  No GPU
+include/*.h, and its host-only entry points agree with the oracle.  No GPU
 call is made here; a context cannot be created without a device and must say
 so with DG_ECUDA rather than fall back to the CPU."""
 import os
@@ -24,14 +24,18 @@ def dg():
 
 
 def declared_functions():
-    text = open(os.path.join(ROOT, "include", "dg.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(dg_[a-z0-9_]+)\s*\(", text)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(dg_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(dg):
     names = declared_functions()
-    assert len(names) >= 17
+    assert len(names) >= 28
     out = subprocess.run(["nm", "-D", "--defined-only", dg.library_path], capture_output=True,
                          text=True, check=True).stdout
     exported = set(re.findall(r"\bT\s+(dg_[a-z0-9_]+)", out))
@@ -96,3 +100,19 @@ def test_no_cpu_fallback_without_gpu(dg):
     with pytest.raises(dg.DGError) as e:
         dg.dg_create(ok)
     assert e.value.status == -3
+
+
+def test_batch_create_rejects_bad_input_without_gpu(dg):
+    import dg_inputs
+    m = dg_inputs.ogrid_cylinder(12, 3, 0.5, 3.0, seed=0)
+    ok = dict(mesh=m, p=3, mu=0.01, M_r=1.0, C_r=0.01, K_r=1.6, mass=7.85)
+    common = dict(p_inf=17.857142857142858)
+    for bad in (dict(ok, p=7), dict(ok, mass=0.0), dict(ok, mu=-1.0)):
+        with pytest.raises(dg.DGError) as e:
+            dg.BatchSolver([bad], **common)
+        assert e.value.status == -1
+    import torch
+    if not torch.cuda.is_available():
+        with pytest.raises(dg.DGError) as e:
+            dg.BatchSolver([ok], **common)
+        assert e.value.status == -3 and "device" in str(e.value)

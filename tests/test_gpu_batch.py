@@ -1,0 +1,192 @@
+"""GPU parity of the batch: independent cylinder / VIV cases advanced together
+(Algorithm 3 per case on the device) against the oracle's loop run case by
+case, and the CUDA-graph replay against plain launches.
+
+Structure (Sec. 3.3 definitions): M_r = 1, C_r = 4 pi f_n zeta,
+K_r = (1 + 1/m*)(2 pi f_n)^2, F_r = lift / m, m = m* rho pi D^2 / 4,
+f_n = U / (U* D); D = 1, rho_inf = |v_inf| = 1, M = 0.2.
+"""
+import numpy as np
+import pytest
+
+import dg_inputs
+import oracle
+from dg_inputs.states import to_kcn
+
+pytestmark = pytest.mark.gpu
+GAMMA, MACH = 1.4, 0.2
+P_INF = 1.0 / (GAMMA * MACH * MACH)
+FAR = dict(rho_inf=1.0, u_inf=1.0, v_inf=0.0, p_inf=P_INF)
+TOL = 1e-4          # mixed path, relative to the largest value over the window
+
+
+@pytest.fixture(scope="module")
+def dg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_17917_gb300 import build
+    build.build()
+    import paper_2508_17917_gb300 as dg
+    return dg
+
+
+def structure(ustar, mstar, zeta):
+    fn = 1.0 / ustar
+    return dict(M_r=1.0, C_r=4 * np.pi * fn * zeta, K_r=(1 + 1 / mstar) * (2 * np.pi * fn) ** 2,
+                mass=mstar * np.pi / 4.0)
+
+
+def start_state(x, y, seed):
+    r = np.hypot(x, y)
+    U = to_kcn(dg_inputs.free_stream(x.shape, rho=1.0, u=1.0, v=0.0, p=P_INF))
+    damp = np.tanh(4.0 * (r - 0.5))
+    U[:, 1] *= damp
+    U[:, 2] = 0.05 * damp * np.sin(np.arctan2(y, x))
+    U[:, 3] = P_INF / (GAMMA - 1) + 0.5 * (U[:, 1] ** 2 + U[:, 2] ** 2) / U[:, 0]
+    return dg_inputs.perturb(U, seed=seed, amp=1e-3)
+
+
+SMALL = [  # (n_theta, n_r, r1, mesh seed, p, U*, Re, y0)
+    (24, 6, 4.0, 1, 3, 4.0, 100.0, 0.05),
+    (32, 5, 5.0, 2, 4, 5.5, 120.0, -0.02),
+    (20, 8, 4.0, 3, 4, 7.0, 150.0, 0.0),
+    (28, 4, 3.0, 4, 5, 3.2, 110.0, 0.03),
+    (16, 5, 3.0, 5, 6, 8.0, 140.0, 0.01),
+]
+
+
+def small_cases():
+    out = []
+    for n_theta, n_r, r1, seed, p, ustar, re, y0 in SMALL:
+        mesh = dg_inputs.ogrid_cylinder(n_theta, n_r, 0.5, r1, seed=seed)
+        out.append(dict(mesh=mesh, p=p, mu=1.0 / re, y0=y0, ydot0=0.0, **structure(ustar, 10.0, 1e-3)))
+    return out
+
+
+def oracle_loop(case, U0, nsteps, cfl=0.3):
+    """Algorithm 3 for one case with the oracle (dt, Newmark with lagged lift,
+    LSRK with v_w = (0, v_b), forces)."""
+    P = oracle.Problem(case["mesh"], case["p"], mu=case["mu"], **FAR)
+    coeff = (case["M_r"], case["C_r"], case["K_r"])
+    U, st, vb, t = U0.copy(), np.array([case.get("y0", 0.0), case.get("ydot0", 0.0), 0.0]), 0.0, 0.0
+    F = P.wall_forces(U)
+    rows = []
+    for _ in range(nsteps):
+        dt, _ = P.dt(U, cfl, (0.0, vb))
+        st, vb = oracle.newmark_step(coeff, F[1] / case["mass"], dt, st)
+        U = P.lsrk_step(U, t, dt, (0.0, vb))
+        t += dt
+        F = P.wall_forces(U)
+        rows.append((t, dt, st[0], st[1], vb, F[0], F[1]))
+    return np.array(rows), U, P
+
+
+def rel_err(got, ref):
+    return np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def small_run(dg):
+    import torch
+    cases = small_cases()
+    nsteps = 12
+    res = {}
+    for use_graph in (True, False):
+        b = dg.BatchSolver(cases, **FAR)
+        states = []
+        for i in range(len(cases)):
+            x, y = b.node_coords(i)
+            U0 = start_state(x, y, seed=10 + i)
+            states.append(U0)
+            b.set_state(i, U0)
+        hist = torch.zeros((nsteps, len(cases), 8), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()          # the batch runs on its own stream
+        b.reset_history()
+        b.run(0.3, nsteps, use_graph=use_graph, hist=hist)
+        res[use_graph] = (hist.cpu().numpy(), [b.get_state(i) for i in range(len(cases))], b.rigid(),
+                          b.launches)
+    return cases, states, nsteps, res
+
+
+def test_batch_graph_replay_is_bit_identical(small_run):
+    cases, states, nsteps, res = small_run
+    hg, Ug, rg, _ = res[True]
+    hp, Up, rp, _ = res[False]
+    assert np.array_equal(hg, hp)
+    assert all(np.array_equal(a, b) for a, b in zip(Ug, Up))
+    assert np.array_equal(rg, rp)
+
+
+@pytest.mark.parametrize("i", range(len(SMALL)))
+def test_batch_case_matches_oracle_loop(small_run, i):
+    cases, states, nsteps, res = small_run
+    hist, Us, rigid, _ = res[True]
+    ref, U_ref, P = oracle_loop(cases[i], states[i], nsteps)
+    got = hist[:, i, :]
+    # dt from the mixed-path state: FP64 bound of a state that differs at the 1e-6 level
+    assert rel_err(got[:, 1], ref[:, 1]) <= 1e-5
+    assert rel_err(got[:, 0], ref[:, 0]) <= 1e-5
+    for col, name in ((2, "y"), (3, "y'"), (4, "v_b"), (6, "lift")):
+        assert rel_err(got[:, col], ref[:, col]) <= TOL, (name, rel_err(got[:, col], ref[:, col]))
+    # drag relative to its mean
+    assert np.abs(got[:, 5] - ref[:, 5]).max() <= TOL * np.abs(ref[:, 5]).mean()
+    d = Us[i] - U_ref
+    J, M = P.geo["J"], P.ops["M"]
+    err = np.sqrt(np.einsum("k,kcn,nm,kcm->c", J, d, M, d) / np.einsum("k,kcn,nm,kcm->c", J, U_ref, M, U_ref))
+    assert np.all(err <= 2e-5), err
+    assert rigid[i, 9] == 0
+
+
+def test_batch_launch_count(small_run):
+    cases, states, nsteps, res = small_run
+    groups = len({c["p"] for c in cases})
+    # initial forces (groups + 1), then per step: dt per group, dt reduce, Newmark,
+    # 5 stages per group, forces per group, force sum, record
+    per_step = 6 * groups + 3 + groups + 1
+    for use_graph in (True, False):
+        launches = res[use_graph][3]
+        assert launches == len(cases) + (groups + 1) + nsteps * per_step, launches
+
+
+def test_batch_rejects_bad_mesh(dg):
+    cases = small_cases()[:1]
+    with pytest.raises(dg.DGError) as e:
+        bad = dict(cases[0])
+        m = bad["mesh"]
+        EToV = m.EToV.copy()
+        EToV[0, 1], EToV[0, 2] = EToV[0, 2], EToV[0, 1]       # clockwise element
+        bad["mesh"] = dg_inputs.Mesh(m.vx, m.vy, EToV, m.EToE, m.EToF, m.bc, m.period)
+        dg.BatchSolver([cases[0], bad], **FAR)
+    assert e.value.status == -2 and "case 1" in str(e.value)
+
+
+def test_full_sweep_sampled_cases(dg):
+    """The 64-case sweep (10k-60k triangles, p = 3..6; the bench's workload):
+    two steps of the whole batch, then the smallest case of each degree
+    against the oracle."""
+    sweep = dg_inputs.viv_sweep()
+    cases = []
+    for c in sweep:
+        cases.append(dict(mesh=dg_inputs.sweep_mesh(c), p=c["p"], mu=1.0 / c["re"],
+                          **structure(c["ustar"], c["mstar"], c["zeta"])))
+    b = dg.BatchSolver(cases, **FAR)
+    states = []
+    for i in range(len(cases)):
+        x, y = b.node_coords(i)
+        U0 = start_state(x, y, seed=100 + i)
+        states.append(U0)
+        b.set_state(i, U0)
+    b.run(0.3, 2, use_graph=True)
+    rigid = b.rigid()
+    picks = {}
+    for i, c in enumerate(cases):
+        if c["p"] not in picks or c["mesh"].K < cases[picks[c["p"]]]["mesh"].K:
+            picks[c["p"]] = i
+    for p, i in sorted(picks.items()):
+        ref, U_ref, P = oracle_loop(cases[i], states[i], 2)
+        assert rel_err(rigid[i, 7], ref[-1, 6]) <= TOL, (p, i)
+        d = b.get_state(i) - U_ref
+        J, M = P.geo["J"], P.ops["M"]
+        err = np.sqrt(np.einsum("k,kcn,nm,kcm->c", J, d, M, d) / np.einsum("k,kcn,nm,kcm->c", J, U_ref, M, U_ref))
+        assert np.all(err <= 2e-5), (p, i, err)
