@@ -21,7 +21,10 @@ __all__ = ["DG_OK", "DG_PRECISION_FP64", "DG_PRECISION_MIXED", "DG_SOURCE_NONE",
            "DgCase", "dg_batch_create", "dg_batch_destroy", "dg_batch_last_error",
            "dg_batch_kernel_launches", "dg_batch_stream", "dg_batch_case_size", "dg_batch_node_coords",
            "dg_batch_set_state", "dg_batch_get_state", "dg_batch_run", "dg_batch_reset_history",
-           "dg_batch_rigid", "BatchSolver"]
+           "dg_batch_rigid", "BatchSolver",
+           "dg_mlp_create", "dg_mlp_destroy", "dg_mlp_last_error", "dg_mlp_param_count",
+           "dg_mlp_kernel_launches", "dg_mlp_set_params", "dg_mlp_get_params", "dg_mlp_forward",
+           "dg_mlp_loss_grad", "dg_mlp_train", "Mlp"]
 
 DG_OK = 0
 DG_PRECISION_FP64, DG_PRECISION_MIXED = 0, 1
@@ -91,6 +94,17 @@ EXPORTED = {
     "dg_batch_run": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_void_p, C.c_int]),
     "dg_batch_reset_history": (C.c_int, [C.c_void_p]),
     "dg_batch_rigid": (C.c_int, [C.c_void_p, _dp]),
+    # include/dg_mlp.h
+    "dg_mlp_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(C.c_void_p)]),
+    "dg_mlp_destroy": (C.c_int, [C.c_void_p]),
+    "dg_mlp_last_error": (C.c_char_p, [C.c_void_p]),
+    "dg_mlp_param_count": (C.c_int64, [C.c_void_p]),
+    "dg_mlp_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "dg_mlp_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "dg_mlp_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "dg_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "dg_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "dg_mlp_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_float, C.c_void_p]),
 }
 
 _lib = None
@@ -461,3 +475,118 @@ class BatchSolver:
     @property
     def stream(self):
         return dg_batch_stream(self.b)
+
+
+# ---- include/dg_mlp.h -----------------------------------------------------
+
+def _mcheck(st, m):
+    if st != DG_OK:
+        raise DGError(st, lib().dg_mlp_last_error(m).decode() if m else "")
+
+
+def _f32_dev(x):
+    """Pointer of a contiguous float32 CUDA tensor; the network runs on its
+    own stream, so the caller's stream is synchronised first."""
+    import torch
+    if not (hasattr(x, "data_ptr") and x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    torch.cuda.current_stream(x.device).synchronize()
+    return C.c_void_p(x.data_ptr())
+
+
+def dg_mlp_create(n_in, width, depth, n_out, max_batch, seed=0):
+    out = C.c_void_p()
+    _mcheck(lib().dg_mlp_create(int(n_in), int(width), int(depth), int(n_out), int(max_batch), int(seed),
+                                C.byref(out)), None)
+    return out
+
+
+def dg_mlp_destroy(m):
+    return lib().dg_mlp_destroy(m)
+
+
+def dg_mlp_last_error(m):
+    return lib().dg_mlp_last_error(m).decode()
+
+
+def dg_mlp_param_count(m):
+    return int(lib().dg_mlp_param_count(m))
+
+
+def dg_mlp_kernel_launches(m):
+    return int(lib().dg_mlp_kernel_launches(m))
+
+
+def dg_mlp_set_params(m, params):
+    if isinstance(params, np.ndarray):
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        _mcheck(lib().dg_mlp_set_params(m, a.ctypes.data_as(C.c_void_p), 0), m)
+    else:
+        _mcheck(lib().dg_mlp_set_params(m, _f32_dev(params), 1), m)
+
+
+def dg_mlp_get_params(m):
+    out = np.zeros(dg_mlp_param_count(m), dtype=np.float32)
+    _mcheck(lib().dg_mlp_get_params(m, out.ctypes.data_as(C.c_void_p), 0), m)
+    return out
+
+
+def dg_mlp_forward(m, X, Y):
+    _mcheck(lib().dg_mlp_forward(m, _f32_dev(X), int(X.shape[0]), _f32_dev(Y)), m)
+
+
+def dg_mlp_loss_grad(m, X, T, grad, loss):
+    _mcheck(lib().dg_mlp_loss_grad(m, _f32_dev(X), _f32_dev(T), int(X.shape[0]), _f32_dev(grad), _f32_dev(loss)), m)
+
+
+def dg_mlp_train(m, X, T, nsteps, lr, loss_hist=None):
+    lh = _f32_dev(loss_hist) if loss_hist is not None else None
+    _mcheck(lib().dg_mlp_train(m, _f32_dev(X), _f32_dev(T), int(X.shape[0]), int(nsteps), float(lr), lh), m)
+
+
+class Mlp:
+    """The surrogate network: the dg_mlp_* calls as methods (torch CUDA
+    float32 tensors in and out)."""
+
+    def __init__(self, n_in, width=128, depth=3, n_out=2, max_batch=8192, seed=0):
+        self.n_in, self.n_out = n_in, n_out
+        self.m = dg_mlp_create(n_in, width, depth, n_out, max_batch, seed)
+
+    def __del__(self):
+        m = getattr(self, "m", None)
+        if m is not None and _lib is not None:
+            dg_mlp_destroy(m)
+            self.m = None
+
+    @property
+    def nparams(self):
+        return dg_mlp_param_count(self.m)
+
+    def set_params(self, p):
+        dg_mlp_set_params(self.m, p)
+
+    def get_params(self):
+        return dg_mlp_get_params(self.m)
+
+    def forward(self, X):
+        import torch
+        Y = torch.empty((X.shape[0], self.n_out), dtype=torch.float32, device=X.device)
+        dg_mlp_forward(self.m, X, Y)
+        return Y
+
+    def loss_grad(self, X, T):
+        import torch
+        g = torch.empty(self.nparams, dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        dg_mlp_loss_grad(self.m, X, T, g, loss)
+        return float(loss.item()), g
+
+    def train(self, X, T, nsteps, lr):
+        import torch
+        hist = torch.empty(max(nsteps, 1), dtype=torch.float32, device=X.device)
+        dg_mlp_train(self.m, X, T, nsteps, lr, hist)
+        return hist[:nsteps]
+
+    @property
+    def launches(self):
+        return dg_mlp_kernel_launches(self.m)

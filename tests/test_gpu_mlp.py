@@ -1,0 +1,114 @@
+"""GPU parity of the surrogate MLP kernels (include/dg_mlp.h) against the
+oracle (oracle/mlp.py) run with the same bfloat16 rounding of every
+matrix-product input.
+
+Tolerances: both sides round the same values to bfloat16, but the GPU forms
+them in FP32 (different summation order) and the oracle in FP64, so a value
+within ~1e-7 of a rounding boundary can land one bfloat16 ulp (2^-8
+relative) apart on one side; such flips touch a small fraction of the
+elements, which keeps the relative L2 difference of outputs and gradients
+below 2e-3.  The Adam kernel is compared on the GPU's own gradient: FP32
+against FP64 arithmetic, 1e-5 relative.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+N_IN, WIDTH, DEPTH, N_OUT = 67, 128, 3, 2
+
+
+@pytest.fixture(scope="module")
+def dg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2508_17917_gb300 import build
+    build.build()
+    import paper_2508_17917_gb300 as dg
+    return dg
+
+
+def sizes():
+    return omlp.layer_sizes(N_IN, WIDTH, DEPTH, N_OUT)
+
+
+def rel_l2(a, b):
+    return np.linalg.norm(np.asarray(a, float) - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("B", [1, 77, 300, 4096])
+def test_forward_matches_oracle(dg, B):
+    import torch
+    net = dg.Mlp(N_IN, WIDTH, DEPTH, N_OUT, max_batch=4096, seed=3)
+    p = net.get_params().astype(np.float64)
+    rng = np.random.default_rng(B)
+    x = rng.normal(size=(B, N_IN)).astype(np.float32)
+    y = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref, _ = omlp.forward(p, sizes(), x, bf16=True)
+    assert rel_l2(y, ref) <= 2e-3, rel_l2(y, ref)
+
+
+def test_init_is_seeded_uniform(dg):
+    a = dg.Mlp(N_IN, WIDTH, DEPTH, N_OUT, seed=5).get_params()
+    b = dg.Mlp(N_IN, WIDTH, DEPTH, N_OUT, seed=5).get_params()
+    c = dg.Mlp(N_IN, WIDTH, DEPTH, N_OUT, seed=6).get_params()
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    Ws, bs = omlp.unpack(a.astype(np.float64), sizes())
+    for W, (ni, no) in zip(Ws, sizes()):
+        lim = np.sqrt(6.0 / (ni + no))
+        assert np.abs(W).max() <= lim and np.abs(W).max() > 0.9 * lim
+        assert abs(W.mean()) < 0.05 * lim
+    assert all(np.all(b == 0) for b in bs)
+
+
+@pytest.mark.parametrize("B", [5, 513])
+def test_loss_and_gradient_match_oracle(dg, B):
+    import torch
+    net = dg.Mlp(N_IN, WIDTH, DEPTH, N_OUT, max_batch=1024, seed=7)
+    rng = np.random.default_rng(11 + B)
+    p = net.get_params().astype(np.float64)
+    p += 0.05 * rng.normal(size=p.size)           # non-zero biases too
+    net.set_params(p.astype(np.float32))
+    p = p.astype(np.float32).astype(np.float64)
+    x = rng.normal(size=(B, N_IN)).astype(np.float32)
+    t = rng.normal(size=(B, N_OUT)).astype(np.float32)
+    loss, g = net.loss_grad(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    ref_loss, ref_g = omlp.loss_and_grad(p, sizes(), x, t, bf16=True)
+    assert abs(loss - ref_loss) <= 1e-3 * ref_loss
+    g = g.cpu().numpy()
+    assert rel_l2(g, ref_g) <= 2e-3, rel_l2(g, ref_g)
+    # every layer's weight and bias block on its own
+    o = 0
+    for ni, no in sizes():
+        for n in (ni * no, no):
+            assert rel_l2(g[o:o + n], ref_g[o:o + n]) <= 5e-3
+            o += n
+
+
+def test_adam_step_matches_oracle(dg):
+    import torch
+    net = dg.Mlp(N_IN, WIDTH, DEPTH, N_OUT, max_batch=1024, seed=9)
+    rng = np.random.default_rng(4)
+    x = torch.from_numpy(rng.normal(size=(256, N_IN)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.normal(size=(256, N_OUT)).astype(np.float32)).cuda()
+    p0 = net.get_params().astype(np.float64)
+    _, g = net.loss_grad(x, t)
+    g = g.cpu().numpy().astype(np.float64)
+    net.train(x, t, 1, 1e-3)
+    p1 = net.get_params().astype(np.float64)
+    ref, _, _ = omlp.adam_step(p0, g, np.zeros_like(p0), np.zeros_like(p0), 1, 1e-3)
+    assert np.abs(p1 - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+
+
+def test_training_fits_a_smooth_map(dg):
+    import torch
+    net = dg.Mlp(8, 64, 2, 2, max_batch=2048, seed=1)
+    rng = np.random.default_rng(0)
+    x = rng.uniform(-1, 1, size=(2048, 8)).astype(np.float32)
+    t = np.stack([np.sin(2 * x[:, 0] + x[:, 1]), x[:, 2] * x[:, 3]], axis=1).astype(np.float32)
+    X, T = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    hist = net.train(X, T, 600, 3e-3).cpu().numpy()
+    assert hist[-1] < 0.05 * hist[0], (hist[0], hist[-1])
+    assert np.all(np.isfinite(hist))
