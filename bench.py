@@ -301,6 +301,9 @@ def run_ours(args):
     if not args.no_large:
         batch = run_batch(dg, torch, dg_inputs, to_kcn, np, peak, steps=max(10, args.steps // 50))
 
+    # --- surrogate MLP (67 -> 3 x 128 GELU -> 2): full-batch Adam steps at B = 4096
+    mlp_line = run_mlp(dg, torch, np) if not args.no_large else None
+
     # --- end to end through the C ABI with host buffers (pinned)
     host_in = torch.empty((K, 4, NP), dtype=torch.float64, pin_memory=True)
     host_in.copy_(torch.from_numpy(U0))
@@ -341,6 +344,7 @@ def run_ours(args):
             "sip_path": sip,
             "p6_large": p6,
             "batch_viv": batch,
+            "mlp": mlp_line,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk.summary(),
@@ -397,6 +401,26 @@ def run_batch(dg, torch, dg_inputs, to_kcn, np, peak, steps):
            "gpu_launches": int(b.launches - n0), "finite": bool(ok)}
     del b
     return out
+
+
+def run_mlp(dg, torch, np, B=4096, steps=200):
+    """Training throughput of the surrogate network's kernels (host clock
+    around dg_mlp_train, which synchronises its stream before returning)."""
+    net = dg.Mlp(67, 128, 3, 2, max_batch=B, seed=0)
+    rng = np.random.default_rng(0)
+    X = torch.from_numpy(rng.normal(size=(B, 67)).astype(np.float32)).cuda()
+    T = torch.from_numpy(rng.normal(size=(B, 2)).astype(np.float32)).cuda()
+    net.train(X, T, 5, 1e-3)                               # warm-up
+    n0 = net.launches
+    t0 = time.perf_counter()
+    net.train(X, T, steps, 1e-3)
+    el = time.perf_counter() - t0
+    macs = 67 * 128 + 2 * 128 * 128 + 128 * 2              # per sample, forward
+    flops = 2 * B * macs * 3 - 2 * B * 67 * 128            # forward, weight and input gradients (none for x)
+    return {"workload": "load-surrogate MLP 67 -> 3 x 128 GELU -> 2, full-batch Adam, B = 4096, bf16 MMA "
+                        "with FP32 accumulation", "samples_per_s": B * steps / el, "ms_per_step": el / steps * 1e3,
+            "tflops": flops * steps / el / 1e12, "launches_per_step": (net.launches - n0) / steps,
+            "timing": "host clock around a synchronising call"}
 
 
 def cpu_baseline(budget_s=20.0):
