@@ -101,6 +101,18 @@ dg_status dg_set_mesh(dg_ctx *ctx, int64_t Nv, const double *vx, const double *v
                       int64_t K, const int32_t *EToV, const int32_t *EToE,
                       const int32_t *EToF, const int32_t *bc);
 
+/* Tile shape of the mixed-precision IIP stage kernel (no counterpart in the
+ * paper): 1 = one volume node and one face node per thread (256 threads),
+ * 2 = two volume nodes and two face nodes of one face per thread (128
+ * threads), 0 = time both (residual-only launches on the current state) at
+ * the first time step after a mesh upload and keep the faster (the default).  Other paths have one kernel and
+ * accept 0 and 1.  Errors: DG_EINVAL (variant outside 0..2),
+ * DG_EUNSUPPORTED (2 on the FP64 or theta != 0 path). */
+dg_status dg_set_stage_variant(dg_ctx *ctx, int variant);
+
+/* The tile shape in use: 1 or 2 (the single-node kernel until tuned). */
+int dg_stage_variant(const dg_ctx *ctx);
+
 /* Copy the state in ([K][4][Np] FP64; host pointer if on_device == 0, device
  * pointer otherwise) and clear the Runge-Kutta register.
  * Errors: DG_EINVAL (null, no mesh yet), DG_ECUDA. */

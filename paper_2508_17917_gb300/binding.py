@@ -18,6 +18,7 @@ __all__ = ["DG_OK", "DG_PRECISION_FP64", "DG_PRECISION_MIXED", "DG_SOURCE_NONE",
            "dg_wall_forces_noalloc", "DG_NOALLOC_MAX_WALL_FACES", "dg_rigid_step",
            "dg_check_finite", "dg_set_source", "dg_node_coords", "dg_reference_operators",
            "dg_kernel_launches", "dg_last_error", "Solver", "EXPORTED",
+           "dg_set_stage_variant", "dg_stage_variant",
            "DgCase", "dg_batch_create", "dg_batch_destroy", "dg_batch_last_error",
            "dg_batch_kernel_launches", "dg_batch_stream", "dg_batch_case_size", "dg_batch_node_coords",
            "dg_batch_set_state", "dg_batch_get_state", "dg_batch_run", "dg_batch_reset_history",
@@ -80,6 +81,8 @@ EXPORTED = {
     "dg_node_coords": (C.c_int, [C.c_void_p, _dp, _dp]),
     "dg_reference_operators": (C.c_int, [C.c_int, _dp, _dp, _dp, _dp, _dp, _ip]),
     "dg_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "dg_set_stage_variant": (C.c_int, [C.c_void_p, C.c_int]),
+    "dg_stage_variant": (C.c_int, [C.c_void_p]),
     "dg_last_error": (C.c_char_p, [C.c_void_p]),
     # include/dg_batch.h
     "dg_batch_create": (C.c_int, [C.POINTER(DgParams), C.c_int, C.POINTER(DgCase), C.POINTER(C.c_void_p)]),
@@ -267,6 +270,14 @@ def dg_kernel_launches(ctx):
     return int(lib().dg_kernel_launches(ctx))
 
 
+def dg_set_stage_variant(ctx, variant):
+    _check(lib().dg_set_stage_variant(ctx, int(variant)), ctx)
+
+
+def dg_stage_variant(ctx):
+    return int(lib().dg_stage_variant(ctx))
+
+
 def dg_last_error(ctx):
     return lib().dg_last_error(ctx).decode()
 
@@ -332,6 +343,14 @@ class Solver:
     @property
     def launches(self):
         return dg_kernel_launches(self.ctx)
+
+    def set_variant(self, v):
+        """Stage-kernel tile shape: 0 = tuned on first step, 1 or 2 forced."""
+        dg_set_stage_variant(self.ctx, v)
+
+    @property
+    def variant(self):
+        return dg_stage_variant(self.ctx)
 
 
 # ---- include/dg_batch.h ---------------------------------------------------

@@ -50,7 +50,10 @@ struct dg_ctx {
     dg::DevBuf<int2> wall;
     int nwall = 0;
     bool cur_is_a = true;
-    dg::LaunchShape shape;
+    dg::LaunchShape shape;    // stage kernel in use
+    dg::LaunchShape shape1, shape2;   // mixed IIP: one / two nodes per thread
+    int variant_req = 0;      // 0: pick by timing on first use, 1 or 2: forced
+    bool tuned = false;
     int source_kind = DG_SOURCE_NONE;
 
     double *cur() { return cur_is_a ? K0a.ptr : K0b.ptr; }
@@ -176,7 +179,9 @@ dg_status run_stage(dg_ctx *c, int s, double t, double dt, const double vw[2], i
     } else {
         sp.geo = c->geo32.ptr;
         sp.ops = c->ops32.ptr;
-        e = dg::launch_stage_mixed(c->prm.p, c->shape, sp, make_phys<float>(c->prm, vw), c->stream);
+        e = (c->shape.variant == 2)
+                ? dg::launch_stage_mixed2(c->prm.p, false, c->shape, sp, make_phys<float>(c->prm, vw), c->stream)
+                : dg::launch_stage_mixed(c->prm.p, c->shape, sp, make_phys<float>(c->prm, vw), c->stream);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
     c->launches += 1;
@@ -280,6 +285,22 @@ const char *dg_last_error(const dg_ctx *ctx) { return ctx ? ctx->err.c_str() : "
 
 int64_t dg_kernel_launches(const dg_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
+dg_status dg_set_stage_variant(dg_ctx *c, int variant)
+{
+    if (!c) return DG_EINVAL;
+    c->err.clear();
+    if (variant < 0 || variant > 2) return fail(c, DG_EINVAL, "variant must be 0, 1 or 2");
+    if (variant == 2 && (c->prm.precision != DG_PRECISION_MIXED || c->prm.theta != 0.0))
+        return fail(c, DG_EUNSUPPORTED, "the two-node kernel is the mixed-precision IIP kernel");
+    c->variant_req = variant;
+    c->tuned = (variant != 0);
+    if (c->K > 0 && c->prm.precision == DG_PRECISION_MIXED && c->prm.theta == 0.0)
+        c->shape = (variant == 2) ? c->shape2 : c->shape1;
+    return DG_OK;
+}
+
+int dg_stage_variant(const dg_ctx *c) { return c ? c->shape.variant : 0; }
+
 dg_status dg_set_mesh(dg_ctx *c, int64_t Nv, const double *vx, const double *vy, int64_t K,
                       const int32_t *EToV, const int32_t *EToE, const int32_t *EToF, const int32_t *bc)
 {
@@ -340,6 +361,13 @@ dg_status dg_set_mesh(dg_ctx *c, int64_t Nv, const double *vx, const double *vy,
     cudaError_t e = (c->prm.precision == DG_PRECISION_FP64) ? dg::stage_shape_fp64(c->prm.p, K, th, c->shape)
                                                              : dg::stage_shape_mixed(c->prm.p, K, th, c->shape);
     if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel configuration");
+    c->shape1 = c->shape;
+    c->tuned = false;
+    if (c->prm.precision == DG_PRECISION_MIXED && !th) {
+        e = dg::stage_shape_mixed2(c->prm.p, K, false, c->shape2);
+        if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel configuration");
+        if (c->variant_req == 2) c->shape = c->shape2;
+    }
     return DG_OK;
 }
 
@@ -414,6 +442,43 @@ dg_status dg_set_source(dg_ctx *c, int kind, const double *params)
     return DG_OK;
 }
 
+// Mixed IIP path, first use: time both stage kernels (one and two nodes per
+// thread) on the current state in residual-only mode and keep the faster.
+static dg_status tune_stage(dg_ctx *c, const double vw[2])
+{
+    if (c->tuned || c->prm.precision != DG_PRECISION_MIXED || c->prm.theta != 0.0 || c->variant_req != 0) {
+        c->tuned = true;
+        return DG_OK;
+    }
+    if (c->rtmp.n != ndof(c)) DG_CUDA(c, c->rtmp.alloc(ndof(c)));
+    cudaEvent_t e0, e1;
+    DG_CUDA(c, cudaEventCreate(&e0));
+    DG_CUDA(c, cudaEventCreate(&e1));
+    float best = 0.f;
+    dg::LaunchShape pick = c->shape1;
+    for (const dg::LaunchShape *cand : {&c->shape1, &c->shape2}) {
+        c->shape = *cand;
+        float ms = 0.f;
+        for (int rep = 0; rep < 5; ++rep) {
+            if (rep == 2) DG_CUDA(c, cudaEventRecord(e0, c->stream));
+            dg_status st = run_stage(c, -1, 0.0, 0.0, vw, dg::STAGE_RHS_ONLY, c->cur(), nullptr, c->rtmp.ptr);
+            if (st != DG_OK) return st;
+        }
+        DG_CUDA(c, cudaEventRecord(e1, c->stream));
+        DG_CUDA(c, cudaEventSynchronize(e1));
+        DG_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+        if (cand == &c->shape1 || ms < best) {
+            best = ms;
+            pick = *cand;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->shape = pick;
+    c->tuned = true;
+    return DG_OK;
+}
+
 dg_status dg_rhs(dg_ctx *c, double t, const double vw[2], double *dUdt, int on_device)
 {
     if (!c) return DG_EINVAL;
@@ -439,6 +504,10 @@ dg_status dg_lsrk_step(dg_ctx *c, double t, double dt, const double vw[2])
     c->err.clear();
     if (c->K < 1) return fail(c, DG_EINVAL, "no mesh");
     if (!std::isfinite(dt) || !std::isfinite(t)) return fail(c, DG_EINVAL, "t and dt must be finite");
+    if (!c->tuned) {
+        dg_status st = tune_stage(c, vw);
+        if (st != DG_OK) return st;
+    }
     for (int s = 0; s < 5; ++s) {
         dg_status st = run_stage(c, s, t + kRkC[s] * dt, dt, vw, dg::STAGE_UPDATE, c->cur(), c->other(), nullptr);
         if (st != DG_OK) return st;

@@ -54,10 +54,10 @@ __device__ __forceinline__ void cp_async16(unsigned dst, const void *src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
 }
 
-template <int P, bool TH = false>
+template <int P, bool TH = false, int EE = Shape<P>::E>
 struct MixedLayout {
     using S = Shape<P>;
-    static constexpr int Np = S::Np, NF = S::NF, E = S::E;
+    static constexpr int Np = S::Np, NF = S::NF, E = EE;
     static constexpr int NpP = (Np + 3) & ~3;                                 // padded pressure row
     static constexpr size_t al(size_t b) { return (b + 15) & ~size_t(15); }
     static constexpr size_t oD = 0;                                           // float2 Np*Np (Dr, Ds)

@@ -12,6 +12,7 @@ struct BatchCase;
 
 struct LaunchShape {
     bool theta = false;      // kernel variant with the theta terms of the IP flux
+    int variant = 1;         // mixed IIP kernel: 1 node per thread (1) or 2 nodes per thread (2)
     int grid = 0;
     int threads = 0;
     size_t smem = 0;
@@ -36,6 +37,13 @@ cudaError_t launch_stage_mixed_batch(int p, const LaunchShape &ls, const StagePa
 cudaError_t launch_dt_lambda_mixed(int p, const float4 *S, const float *Pr, const float *geo, const int4 *conn,
                                    const int *fmask, const int4 *tiles, long long ntiles, const BatchCase *cases,
                                    long long K, const Phys<float> &ph, float sig_fac, double *lam, cudaStream_t st);
+// the mixed IIP kernel with two nodes per thread: units = K elements (single
+// mesh) or the tile count of a tile table (batch); its tiles hold
+// stage_tile_elems2(p) elements
+cudaError_t stage_shape_mixed2(int p, long long units, bool batch, LaunchShape &out);
+cudaError_t launch_stage_mixed2(int p, bool batch, const LaunchShape &ls, const StageParams &sp,
+                                const Phys<float> &ph, cudaStream_t st);
+int stage_tile_elems2(int p);
 // elements per tile of the mixed kernel for degree p
 int stage_tile_elems(int p);
 // FP32 copy [K][Np] float4 and FP64-recovered pressure [K][NpP] of a state

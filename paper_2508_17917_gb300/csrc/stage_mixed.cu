@@ -1,6 +1,7 @@
 // stage_mixed.cu -- mixed-precision stage kernel instantiations (p = 1..6):
 // FP32 arithmetic, FP64 state in HBM, FP64 pressure recovery and registers.
 #include "dg_stage_mixed.cuh"
+#include "dg_stage_mixed2.cuh"
 #include "launch.h"
 
 namespace dg {
@@ -71,6 +72,42 @@ template <int P>
 cudaError_t launch_batch_p(const LaunchShape &ls, const StageParams &sp, const Phys<float> &ph, cudaStream_t st)
 {
     stage_mixed_kernel<P, false, true><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
+    return cudaGetLastError();
+}
+
+// two nodes per thread (IIP): shape for `ntiles` tiles (batch) or for K elements
+template <int P, bool BATCH>
+cudaError_t shape2_p(long long units, LaunchShape &ls)
+{
+    using S2 = Shape2<P>;
+    using L = MixedLayout<P, false, S2::E>;
+    auto kern = stage_mixed2_kernel<P, BATCH>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(L::bytes));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S2::NT, L::bytes);
+    if (e != cudaSuccess) return e;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (per_sm < 1) per_sm = 1;
+    const long long ntiles = BATCH ? units : (units + S2::E - 1) / S2::E;
+    long long grid = static_cast<long long>(sms) * per_sm;
+    ls.grid = static_cast<int>(ntiles < grid ? ntiles : grid);
+    ls.threads = S2::NT;
+    ls.smem = L::bytes;
+    ls.elems_per_tile = S2::E;
+    ls.theta = false;
+    ls.variant = 2;
+    return cudaSuccess;
+}
+
+template <int P, bool BATCH>
+cudaError_t launch2_p(const LaunchShape &ls, const StageParams &sp, const Phys<float> &ph, cudaStream_t st)
+{
+    stage_mixed2_kernel<P, BATCH><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
     return cudaGetLastError();
 }
 
@@ -146,6 +183,34 @@ cudaError_t launch_dt_lambda_mixed(int p, const float4 *S, const float *Pr, cons
 #define C_(P) dt_mixed_p<P>(S, Pr, geo, conn, fmask, tiles, ntiles, cases, K, ph, sig_fac, lam, st)
     DG_SWITCH_P(p, C_)
 #undef C_
+}
+
+cudaError_t stage_shape_mixed2(int p, long long units, bool batch, LaunchShape &out)
+{
+#define C_(P) (batch ? shape2_p<P, true>(units, out) : shape2_p<P, false>(units, out))
+    DG_SWITCH_P(p, C_)
+#undef C_
+}
+
+cudaError_t launch_stage_mixed2(int p, bool batch, const LaunchShape &ls, const StageParams &sp,
+                                const Phys<float> &ph, cudaStream_t st)
+{
+#define C_(P) (batch ? launch2_p<P, true>(ls, sp, ph, st) : launch2_p<P, false>(ls, sp, ph, st))
+    DG_SWITCH_P(p, C_)
+#undef C_
+}
+
+int stage_tile_elems2(int p)
+{
+    switch (p) {
+    case 1: return Shape2<1>::E;
+    case 2: return Shape2<2>::E;
+    case 3: return Shape2<3>::E;
+    case 4: return Shape2<4>::E;
+    case 5: return Shape2<5>::E;
+    case 6: return Shape2<6>::E;
+    default: return 0;
+    }
 }
 
 int stage_tile_elems(int p)
