@@ -76,6 +76,15 @@ const char *dg_batch_last_error(const dg_batch *b);
  * kernels they contain). */
 int64_t dg_batch_kernel_launches(const dg_batch *b);
 
+/* Tile shape of the stage kernel per degree group (see dg_set_stage_variant):
+ * 0 = time both shapes per group at the next dg_batch_run (the default),
+ * 1 or 2 = forced for every group.  Drops captured graphs.
+ * Errors: DG_EINVAL. */
+dg_status dg_batch_set_stage_variant(dg_batch *b, int variant);
+
+/* The tile shape the group of case i uses (1 or 2); 0 for a bad argument. */
+int dg_batch_stage_variant(const dg_batch *b, int i);
+
 /* The cudaStream_t the batch runs on (for events a caller records around
  * dg_batch_run); NULL for a NULL batch. */
 void *dg_batch_stream(const dg_batch *b);

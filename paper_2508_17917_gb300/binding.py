@@ -20,7 +20,8 @@ __all__ = ["DG_OK", "DG_PRECISION_FP64", "DG_PRECISION_MIXED", "DG_SOURCE_NONE",
            "dg_kernel_launches", "dg_last_error", "Solver", "EXPORTED",
            "dg_set_stage_variant", "dg_stage_variant",
            "DgCase", "dg_batch_create", "dg_batch_destroy", "dg_batch_last_error",
-           "dg_batch_kernel_launches", "dg_batch_stream", "dg_batch_case_size", "dg_batch_node_coords",
+           "dg_batch_kernel_launches", "dg_batch_stream", "dg_batch_case_size",
+           "dg_batch_set_stage_variant", "dg_batch_stage_variant", "dg_batch_node_coords",
            "dg_batch_set_state", "dg_batch_get_state", "dg_batch_run", "dg_batch_reset_history",
            "dg_batch_rigid", "BatchSolver",
            "dg_mlp_create", "dg_mlp_destroy", "dg_mlp_last_error", "dg_mlp_param_count",
@@ -90,6 +91,8 @@ EXPORTED = {
     "dg_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "dg_batch_kernel_launches": (C.c_int64, [C.c_void_p]),
     "dg_batch_stream": (C.c_void_p, [C.c_void_p]),
+    "dg_batch_set_stage_variant": (C.c_int, [C.c_void_p, C.c_int]),
+    "dg_batch_stage_variant": (C.c_int, [C.c_void_p, C.c_int]),
     "dg_batch_case_size": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
     "dg_batch_node_coords": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp]),
     "dg_batch_set_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
@@ -380,6 +383,14 @@ def dg_batch_kernel_launches(b):
     return int(lib().dg_batch_kernel_launches(b))
 
 
+def dg_batch_set_stage_variant(b, variant):
+    _bcheck(lib().dg_batch_set_stage_variant(b, int(variant)), b)
+
+
+def dg_batch_stage_variant(b, i):
+    return int(lib().dg_batch_stage_variant(b, int(i)))
+
+
 def dg_batch_stream(b):
     """Integer handle of the batch's cudaStream_t."""
     return int(lib().dg_batch_stream(b) or 0)
@@ -494,6 +505,12 @@ class BatchSolver:
     @property
     def stream(self):
         return dg_batch_stream(self.b)
+
+    def set_variant(self, v):
+        dg_batch_set_stage_variant(self.b, v)
+
+    def variant(self, i):
+        return dg_batch_stage_variant(self.b, i)
 
 
 # ---- include/dg_mlp.h -----------------------------------------------------

@@ -36,12 +36,13 @@ struct Group {
     long long lam_base = 0;          // first entry in the batch's Lambda_K array
     int wall_base = 0;               // first entry in the batch's wall partials
     int nwall = 0;
-    long long ntiles = 0;
-    dg::LaunchShape shape;
+    long long ntiles = 0, ntiles2 = 0;
+    dg::LaunchShape shape, shape2;   // one / two nodes per thread
+    int variant = 1;
     DevBuf<double> K0a, K0b, K1, geo64, Dr64, Ds64, wface, fxy;
     DevBuf<float> geo32, ops32, P0a, P0b;
     DevBuf<float4> S0a, S0b;
-    DevBuf<int4> conn, tiles;
+    DevBuf<int4> conn, tiles, tiles2;
     DevBuf<int> fmask, elem_case;
     DevBuf<int2> walls;
 };
@@ -71,6 +72,8 @@ struct dg_batch {
     DevBuf<int> wseg, counter;
     bool cur_is_a = true;
     bool forces_stale = true;
+    int variant_req = 0;             // 0: tuned per degree group on the first run; 1, 2: forced
+    bool tuned = false;
     // graphs: [0] starts from buffers a, [1] from buffers b
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t graph_launches = 0;
@@ -207,10 +210,16 @@ dg_status enqueue_step(dg_batch *b, double cfl, double *hist, int rows)
             sp.sig_fac = sf;
             sp.mode = dg::STAGE_UPDATE;
             sp.first_stage = (s == 0) ? 1 : 0;
-            sp.tiles = g.tiles.ptr;
             sp.cases = b->dcases.ptr;
-            sp.ntiles = g.ntiles;
-            B_CUDA(b, dg::launch_stage_mixed_batch(g.p, g.shape, sp, ph32, b->stream));
+            if (g.variant == 2) {
+                sp.tiles = g.tiles2.ptr;
+                sp.ntiles = g.ntiles2;
+                B_CUDA(b, dg::launch_stage_mixed2(g.p, true, g.shape2, sp, ph32, b->stream));
+            } else {
+                sp.tiles = g.tiles.ptr;
+                sp.ntiles = g.ntiles;
+                B_CUDA(b, dg::launch_stage_mixed_batch(g.p, g.shape, sp, ph32, b->stream));
+            }
             b->launches += 1;
         }
         b->cur_is_a = !b->cur_is_a;
@@ -221,6 +230,70 @@ dg_status enqueue_step(dg_batch *b, double cfl, double *hist, int rows)
         B_CUDA(b, dg::launch_batch_record(b->dcases.ptr, n, hist, rows, b->counter.ptr, b->stream));
         b->launches += 1;
     }
+    return DG_OK;
+}
+
+// First run: per degree group, time both stage-kernel shapes on the current
+// states in residual-only launches (into a scratch array) and keep the faster.
+dg_status tune_groups(dg_batch *b)
+{
+    if (b->tuned) return DG_OK;
+    const dg::Phys<float> ph32 = phys_of<float>(b->prm);
+    cudaEvent_t e0, e1;
+    B_CUDA(b, cudaEventCreate(&e0));
+    B_CUDA(b, cudaEventCreate(&e1));
+    for (auto &g : b->groups) {
+        if (b->variant_req != 0) {
+            g.variant = b->variant_req;
+            continue;
+        }
+        DevBuf<double> scratch;
+        B_CUDA(b, scratch.alloc(static_cast<size_t>(g.K) * 4 * g.ops.Np));
+        float best = 0.f;
+        for (int v = 1; v <= 2; ++v) {
+            dg::StageParams sp{};
+            const bool a = b->cur_is_a;
+            sp.K0in = a ? g.K0a.ptr : g.K0b.ptr;
+            sp.K1 = g.K1.ptr;
+            sp.Rout = scratch.ptr;
+            sp.geo = g.geo32.ptr;
+            sp.conn = g.conn.ptr;
+            sp.ops = g.ops32.ptr;
+            sp.fmask = g.fmask.ptr;
+            sp.Sin = a ? g.S0a.ptr : g.S0b.ptr;
+            sp.Pin = a ? g.P0a.ptr : g.P0b.ptr;
+            sp.K = g.K;
+            sp.gm1 = b->prm.gamma - 1.0;
+            sp.sig_fac = sigma_factor(b->prm);
+            sp.mode = dg::STAGE_RHS_ONLY;
+            sp.first_stage = 1;
+            sp.cases = b->dcases.ptr;
+            float ms = 0.f;
+            for (int rep = 0; rep < 5; ++rep) {
+                if (rep == 2) B_CUDA(b, cudaEventRecord(e0, b->stream));
+                if (v == 2) {
+                    sp.tiles = g.tiles2.ptr;
+                    sp.ntiles = g.ntiles2;
+                    B_CUDA(b, dg::launch_stage_mixed2(g.p, true, g.shape2, sp, ph32, b->stream));
+                } else {
+                    sp.tiles = g.tiles.ptr;
+                    sp.ntiles = g.ntiles;
+                    B_CUDA(b, dg::launch_stage_mixed_batch(g.p, g.shape, sp, ph32, b->stream));
+                }
+                b->launches += 1;
+            }
+            B_CUDA(b, cudaEventRecord(e1, b->stream));
+            B_CUDA(b, cudaEventSynchronize(e1));
+            B_CUDA(b, cudaEventElapsedTime(&ms, e0, e1));
+            if (v == 1 || ms < best) {
+                best = ms;
+                g.variant = v;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->tuned = true;
     return DG_OK;
 }
 
@@ -283,12 +356,12 @@ dg_status dg_batch_create(const dg_params *common, int ncases, const dg_case *ca
         g.p = degrees[gi];
         if (!dg::build_reference_operators(g.p, g.ops)) return bail(DG_EINVAL);
         const int Np = g.ops.Np, Nfp = g.ops.Nfp, NF = 3 * Nfp;
-        const int E = dg::stage_tile_elems(g.p);
+        const int E = dg::stage_tile_elems(g.p), E2 = dg::stage_tile_elems2(g.p);
         std::vector<double> geo;
         std::vector<int4> conn;
         std::vector<int2> walls;
         std::vector<double> wxy;
-        std::vector<int4> tiles;
+        std::vector<int4> tiles, tiles2;
         std::vector<int> ecase;
         g.lam_base = lam_total;
         g.wall_base = wall_total;
@@ -326,6 +399,9 @@ dg_status dg_batch_create(const dg_params *common, int ncases, const dg_case *ca
             for (long long k0 = 0; k0 < c.K; k0 += E)
                 tiles.push_back(make_int4(static_cast<int>(off + k0), static_cast<int>(std::min<long long>(E, c.K - k0)),
                                           i, 0));
+            for (long long k0 = 0; k0 < c.K; k0 += E2)
+                tiles2.push_back(make_int4(static_cast<int>(off + k0),
+                                           static_cast<int>(std::min<long long>(E2, c.K - k0)), i, 0));
             ecase.insert(ecase.end(), static_cast<size_t>(c.K), i);
             g.K += c.K;
             dg::BatchCase &bc = b->init[i];
@@ -340,6 +416,7 @@ dg_status dg_batch_create(const dg_params *common, int ncases, const dg_case *ca
         }
         g.nwall = static_cast<int>(walls.size());
         g.ntiles = static_cast<long long>(tiles.size());
+        g.ntiles2 = static_cast<long long>(tiles2.size());
         lam_total += g.K;
         wall_total += g.nwall;
         const size_t nd = static_cast<size_t>(g.K) * 4 * Np;
@@ -363,6 +440,7 @@ dg_status dg_batch_create(const dg_params *common, int ncases, const dg_case *ca
         chk(g.geo32.alloc(g32.size()));
         chk(g.conn.alloc(conn.size()));
         chk(g.tiles.alloc(tiles.size()));
+        chk(g.tiles2.alloc(tiles2.size()));
         chk(g.elem_case.alloc(ecase.size()));
         chk(g.ops32.alloc(o32.size()));
         chk(g.Dr64.alloc(static_cast<size_t>(Np) * Np));
@@ -378,6 +456,7 @@ dg_status dg_batch_create(const dg_params *common, int ncases, const dg_case *ca
         chk(cudaMemcpy(g.geo32.ptr, g32.data(), g32.size() * sizeof(float), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(g.conn.ptr, conn.data(), conn.size() * sizeof(int4), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(g.tiles.ptr, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(g.tiles2.ptr, tiles2.data(), tiles2.size() * sizeof(int4), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(g.elem_case.ptr, ecase.data(), ecase.size() * sizeof(int), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(g.ops32.ptr, o32.data(), o32.size() * sizeof(float), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(g.Dr64.ptr, g.ops.Dr.data(), g.ops.Dr.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -396,6 +475,7 @@ dg_status dg_batch_create(const dg_params *common, int ncases, const dg_case *ca
         chk(cudaMemset(g.P0a.ptr, 0, npp * sizeof(float)));
         chk(cudaMemset(g.P0b.ptr, 0, npp * sizeof(float)));
         chk(dg::stage_shape_mixed_batch(g.p, g.ntiles, g.shape));
+        chk(dg::stage_shape_mixed2(g.p, g.ntiles2, true, g.shape2));
         if (e != cudaSuccess) return bail(DG_ECUDA);
     }
     cudaError_t e = cudaSuccess;
@@ -426,6 +506,24 @@ dg_status dg_batch_destroy(dg_batch *b)
 const char *dg_batch_last_error(const dg_batch *b) { return b ? b->err.c_str() : g_create_err.c_str(); }
 
 int64_t dg_batch_kernel_launches(const dg_batch *b) { return b ? b->launches : 0; }
+
+dg_status dg_batch_set_stage_variant(dg_batch *b, int variant)
+{
+    if (!b) return DG_EINVAL;
+    b->err.clear();
+    if (variant < 0 || variant > 2) return bfail(b, DG_EINVAL, "variant must be 0, 1 or 2");
+    b->variant_req = variant;
+    b->tuned = false;
+    b->drop_graphs();
+    b->graph_cfl = 0.0;
+    return DG_OK;
+}
+
+int dg_batch_stage_variant(const dg_batch *b, int i)
+{
+    if (!b || i < 0 || i >= static_cast<int>(b->cases.size())) return 0;
+    return b->groups[b->cases[i].group].variant;
+}
 
 void *dg_batch_stream(const dg_batch *b) { return b ? static_cast<void *>(b->stream) : nullptr; }
 
@@ -511,6 +609,10 @@ dg_status dg_batch_run(dg_batch *b, double cfl, int nsteps, int use_graph, doubl
         dg_status st = enqueue_forces(b);
         if (st != DG_OK) return st;
         b->forces_stale = false;
+    }
+    if (!b->tuned) {
+        dg_status st = tune_groups(b);
+        if (st != DG_OK) return st;
     }
     if (use_graph && nsteps > 0) {
         if (b->graph_cfl != cfl || b->graph_hist != hist || b->graph_rows != hist_rows) {

@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -47,8 +48,12 @@ __device__ __forceinline__ unsigned pack2(const bf16 *p) { return *reinterpret_c
 // four warps of 32 x 32 (2 x 4 mma tiles of 16 x 8), K staged by 32.
 template <int ALAY, int BLAY, int EPI>
 __global__ void __launch_bounds__(NTHR)
-gemm_bf16_kernel(const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb, int M, int N, int K, Epi ep)
+gemm_bf16_kernel(const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb, int M, int N, int K,
+                 int kchunk, Epi ep)
 {
+    // split K: block z sums k in [z kchunk, (z + 1) kchunk); EPI_STORE writes slice z
+    const int kbeg = blockIdx.z * kchunk;
+    const int kend = min(K, kbeg + kchunk);
     __shared__ __align__(16) bf16 As[BM][BK + PAD];
     __shared__ __align__(16) bf16 Bs[BN][BK + PAD];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -63,14 +68,14 @@ gemm_bf16_kernel(const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B
 #pragma unroll
             for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
     const bf16 zero = __float2bfloat16(0.f);
-    for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
         for (int idx = tid; idx < BM * BK; idx += NTHR) {
             int m, k;
             if (ALAY == LAY_MK) { m = idx / BK; k = idx % BK; }
             else { k = idx / BM; m = idx % BM; }
             const int gm = m0 + m, gk = k0 + k;
             bf16 v = zero;
-            if (gm < M && gk < K) v = (ALAY == LAY_MK) ? A[static_cast<long long>(gm) * lda + gk]
+            if (gm < M && gk < kend) v = (ALAY == LAY_MK) ? A[static_cast<long long>(gm) * lda + gk]
                                                       : A[static_cast<long long>(gk) * lda + gm];
             As[m][k] = v;
         }
@@ -80,7 +85,7 @@ gemm_bf16_kernel(const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B
             else { k = idx / BN; n = idx % BN; }
             const int gn = n0 + n, gk = k0 + k;
             bf16 v = zero;
-            if (gn < N && gk < K) v = (BLAY == LAY_NK) ? B[static_cast<long long>(gn) * ldb + gk]
+            if (gn < N && gk < kend) v = (BLAY == LAY_NK) ? B[static_cast<long long>(gn) * ldb + gk]
                                                       : B[static_cast<long long>(gk) * ldb + gn];
             Bs[n][k] = v;
         }
@@ -138,9 +143,20 @@ gemm_bf16_kernel(const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B
                     ep.DZ32[o] = dz;
                     ep.DZ16[o] = __float2bfloat16_rn(dz);
                 } else {
-                    ep.Y[o] = v;
+                    ep.Y[static_cast<long long>(blockIdx.z) * M * N + o] = v;
                 }
             }
+}
+
+// sum of `splits` slices of n values (split-K partial products), fixed order
+__global__ void sum_slices_kernel(const float *ws, int splits, long long n, float *out)
+{
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        float a = 0.f;
+        for (int z = 0; z < splits; ++z) a += ws[z * n + i];
+        out[i] = a;
+    }
 }
 
 __global__ void to_bf16_kernel(const float *x, long long n, bf16 *out)
@@ -186,20 +202,22 @@ __global__ void finish_loss_kernel(const float *partial, int nb, long long n, fl
     if (threadIdx.x == 0) *out = s[0] / static_cast<float>(n);
 }
 
-// column sums of dz [B][N] (bias gradients): 32 columns x 8 row phases per block
-__global__ void colsum_kernel(const float *dz, int B, int N, float *out)
+// column sums of dz [B][N] (bias gradients): block (x, y) sums 32 columns over
+// the rows of chunk y into slice y of out [gridDim.y][N]
+__global__ void colsum_kernel(const float *dz, int B, int N, int rows_per_chunk, float *out)
 {
     __shared__ float s[8][33];
     const int c = blockIdx.x * 32 + threadIdx.x;
+    const int b0 = blockIdx.y * rows_per_chunk, b1 = min(B, b0 + rows_per_chunk);
     float a = 0.f;
     if (c < N)
-        for (int b = threadIdx.y; b < B; b += 8) a += dz[static_cast<long long>(b) * N + c];
+        for (int b = b0 + threadIdx.y; b < b1; b += 8) a += dz[static_cast<long long>(b) * N + c];
     s[threadIdx.y][threadIdx.x] = a;
     __syncthreads();
     if (threadIdx.y == 0 && c < N) {
         float t = 0.f;
         for (int y = 0; y < 8; ++y) t += s[y][threadIdx.x];
-        out[c] = t;
+        out[static_cast<long long>(blockIdx.y) * N + c] = t;
     }
 }
 
@@ -246,7 +264,7 @@ struct dg_mlp {
     std::string err;
     int64_t launches = 0;
     long long step = 0;
-    dg::DevBuf<float> p, m, v, g, lossbuf, partial;
+    dg::DevBuf<float> p, m, v, g, lossbuf, partial, ws;   // ws: split-K slices
     dg::DevBuf<bf16> wq;
     dg::DevBuf<long long> dwoff, dwlen, dqoff;
     std::vector<dg::DevBuf<float>> Z, DZ32;            // per hidden layer / per layer
@@ -271,12 +289,28 @@ dg_status mfail(dg_mlp *m, dg_status st, const std::string &msg)
         if (e_ != cudaSuccess) return mfail(mm, DG_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+constexpr int KSPLIT_MAX = 32;
+
 template <int AL, int BL, int EPI>
 cudaError_t gemm(dg_mlp *m, const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K, const Epi &ep)
 {
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    gemm_bf16_kernel<AL, BL, EPI><<<grid, NTHR, 0, m->stream>>>(A, lda, B, ldb, M, N, K, ep);
+    // long sums (the weight gradients sum over the batch) are split into up to
+    // 32 slices of at least 256 terms, written to a workspace and added in order
+    int splits = 1;
+    if (EPI == EPI_STORE) splits = std::max(1, std::min(KSPLIT_MAX, K / 256));
+    const int kchunk = ((K + splits - 1) / splits + BK - 1) / BK * BK;
+    splits = (K + kchunk - 1) / kchunk;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
+    Epi e = ep;
+    if (EPI == EPI_STORE && splits > 1) e.Y = m->ws.ptr;
+    gemm_bf16_kernel<AL, BL, EPI><<<grid, NTHR, 0, m->stream>>>(A, lda, B, ldb, M, N, K, kchunk, e);
     m->launches += 1;
+    if (EPI == EPI_STORE && splits > 1) {
+        const long long n = static_cast<long long>(M) * N;
+        sum_slices_kernel<<<static_cast<int>(std::min<long long>((n + 255) / 256, 4096)), 256, 0, m->stream>>>(
+            m->ws.ptr, splits, n, ep.Y);
+        m->launches += 1;
+    }
     return cudaGetLastError();
 }
 
@@ -326,8 +360,14 @@ dg_status loss_grad(dg_mlp *m, const float *X, const float *T, int B, float *gra
         Epi eg{};
         eg.Y = grad + m->woff[l];
         M_CUDA(m, (gemm<LAY_KM, LAY_KN, EPI_STORE>(m, m->DZ16[l].ptr, no, m->H[l].ptr, ni, no, ni, B, eg)));
-        colsum_kernel<<<(no + 31) / 32, dim3(32, 8), 0, m->stream>>>(m->DZ32[l].ptr, B, no, grad + m->boff[l]);
-        m->launches += 1;
+        {
+            const int chunks = std::max(1, std::min(KSPLIT_MAX, B / 128));
+            const int rows = (B + chunks - 1) / chunks;
+            colsum_kernel<<<dim3((no + 31) / 32, chunks), dim3(32, 8), 0, m->stream>>>(m->DZ32[l].ptr, B, no, rows,
+                                                                                      m->ws.ptr);
+            sum_slices_kernel<<<(no + 255) / 256, 256, 0, m->stream>>>(m->ws.ptr, chunks, no, grad + m->boff[l]);
+            m->launches += 2;
+        }
         M_CUDA(m, cudaGetLastError());
         if (l > 0) {
             // dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1})
@@ -417,6 +457,11 @@ dg_status dg_mlp_create(int n_in, int width, int depth, int n_out, int max_batch
     chk(m->wq.alloc(q));
     chk(m->lossbuf.alloc(1));
     chk(m->partial.alloc(256));
+    {
+        long long mx = 0;
+        for (int l = 0; l < m->nl; ++l) mx = std::max(mx, static_cast<long long>(m->din[l]) * m->dout[l]);
+        chk(m->ws.alloc(static_cast<size_t>(mx) * KSPLIT_MAX));
+    }
     chk(m->dwoff.alloc(m->nl));
     chk(m->dwlen.alloc(m->nl));
     chk(m->dqoff.alloc(m->nl));

@@ -86,14 +86,18 @@ def rel_err(got, ref):
     return np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
 
 
+RUNS = [("graph", 1), ("plain", 1), ("graph", 2), ("graph", 0)]     # (launch mode, tile shape; 0 = tuned)
+
+
 @pytest.fixture(scope="module")
 def small_run(dg):
     import torch
     cases = small_cases()
     nsteps = 12
     res = {}
-    for use_graph in (True, False):
+    for mode, variant in RUNS:
         b = dg.BatchSolver(cases, **FAR)
+        b.set_variant(variant)
         states = []
         for i in range(len(cases)):
             x, y = b.node_coords(i)
@@ -103,28 +107,30 @@ def small_run(dg):
         hist = torch.zeros((nsteps, len(cases), 8), dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()          # the batch runs on its own stream
         b.reset_history()
-        b.run(0.3, nsteps, use_graph=use_graph, hist=hist)
-        res[use_graph] = (hist.cpu().numpy(), [b.get_state(i) for i in range(len(cases))], b.rigid(),
-                          b.launches)
+        b.run(0.3, nsteps, use_graph=(mode == "graph"), hist=hist)
+        res[(mode, variant)] = (hist.cpu().numpy(), [b.get_state(i) for i in range(len(cases))], b.rigid(),
+                                b.launches, [b.variant(i) for i in range(len(cases))])
     return cases, states, nsteps, res
 
 
 def test_batch_graph_replay_is_bit_identical(small_run):
     cases, states, nsteps, res = small_run
-    hg, Ug, rg, _ = res[True]
-    hp, Up, rp, _ = res[False]
+    hg, Ug, rg, _, _ = res[("graph", 1)]
+    hp, Up, rp, _, _ = res[("plain", 1)]
     assert np.array_equal(hg, hp)
     assert all(np.array_equal(a, b) for a, b in zip(Ug, Up))
     assert np.array_equal(rg, rp)
 
 
+@pytest.mark.parametrize("run", [("graph", 1), ("graph", 2), ("graph", 0)])
 @pytest.mark.parametrize("i", range(len(SMALL)))
-def test_batch_case_matches_oracle_loop(small_run, i):
+def test_batch_case_matches_oracle_loop(small_run, i, run):
     cases, states, nsteps, res = small_run
-    hist, Us, rigid, _ = res[True]
+    hist, Us, rigid, _, variants = res[run]
+    assert variants[i] == (run[1] or variants[i]) and variants[i] in (1, 2)
     ref, U_ref, P = oracle_loop(cases[i], states[i], nsteps)
     got = hist[:, i, :]
-    # dt from the mixed-path state: FP64 bound of a state that differs at the 1e-6 level
+    # dt from the mixed-path state: FP32 bound of a state that differs at the 1e-6 level
     assert rel_err(got[:, 1], ref[:, 1]) <= 1e-5
     assert rel_err(got[:, 0], ref[:, 0]) <= 1e-5
     for col, name in ((2, "y"), (3, "y'"), (4, "v_b"), (6, "lift")):
@@ -141,12 +147,14 @@ def test_batch_case_matches_oracle_loop(small_run, i):
 def test_batch_launch_count(small_run):
     cases, states, nsteps, res = small_run
     groups = len({c["p"] for c in cases})
-    # initial forces (groups + 1), then per step: dt per group, dt reduce, Newmark,
-    # 5 stages per group, forces per group, force sum, record
+    # set_state per case, initial forces (groups + 1), then per step: dt per group,
+    # dt reduce, Newmark, 5 stages per group, forces per group, force sum, record;
+    # the tuned run adds five residual-only launches per shape and group
     per_step = 6 * groups + 3 + groups + 1
-    for use_graph in (True, False):
-        launches = res[use_graph][3]
-        assert launches == len(cases) + (groups + 1) + nsteps * per_step, launches
+    for run in RUNS:
+        launches = res[run][3]
+        tune = 10 * groups if run[1] == 0 else 0
+        assert launches == len(cases) + (groups + 1) + tune + nsteps * per_step, (run, launches)
 
 
 def test_batch_rejects_bad_mesh(dg):
