@@ -62,17 +62,21 @@ def algorithmic_bytes_per_step(K, geo_bytes):
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("dg_stage.cuh", "dg_stage_mixed.cuh", "dg_device.cuh", "stage_mixed.cu"):
+    for f in ("dg_stage.cuh", "dg_stage_mixed.cuh", "dg_stage_mixed2.cuh", "dg_device.cuh", "stage_mixed.cu"):
         with open(os.path.join(ROOT, "paper_2508_17917_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per DOF-stage of the mixed stage kernel from the committed
-    ncu summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "stage_kernel_mixed_p4.md")
-    if not os.path.exists(path):
+PROFILE_OF_VARIANT = {1: "stage_kernel_mixed_p4.md", 2: "stage_kernel_mixed2_p4.md"}
+KERNEL_OF_VARIANT = {1: "dg::stage_mixed_kernel<4, false>", 2: "dg::stage_mixed2_kernel<4, false>"}
+
+
+def recorded_traffic(variant):
+    """DRAM bytes per DOF-stage of the mixed stage kernel in use, from its
+    committed ncu summary, if that was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", PROFILE_OF_VARIANT.get(variant, ""))
+    if not os.path.isfile(path):
         return None
     text = open(path).read()
     m = re.search(r"dram_bytes_per_dof_stage:\s*([0-9.eE+-]+)\s*\(kernel_hash\s+([0-9a-f]+)\)", text)
@@ -233,12 +237,14 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     bytes_step = algorithmic_bytes_per_step(K, GEO_BYTES_MIXED)
     achieved = bytes_step / 5.0 / (stage_ms * 1e-3) / 1e9
-    traffic = recorded_traffic()
+    variant = s.variant
+    traffic = recorded_traffic(variant)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
                 "traffic": (traffic * dof * 5 / 5.0) if traffic is not None else None,
                 "algorithmic_bytes_per_launch": bytes_step / 5.0,
-                "kernel": "dg::stage_mixed_kernel<4, false>"}
+                "kernel": KERNEL_OF_VARIANT.get(variant, str(variant)),
+                "tile_shape": "two nodes per thread" if variant == 2 else "one node per thread"}
 
     # --- FP64 path, same workload
     s64, U64, dt64 = solvers["fp64"]
