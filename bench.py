@@ -252,6 +252,15 @@ def run_ours(args):
     t64, _ = timed_steps(dg, torch, s64, dt64, max(3, args.steps // 20), 2, flush, stream)
     v64 = dof * 5 * len(t64) / (sum(t64) * 1e-3)
 
+    # --- fused steps: the same mixed path as one cooperative launch per step
+    s.set_fused(True)
+    s.set_state(U0)
+    tf, lf = timed_steps(dg, torch, s, dt, max(5, args.steps // 10), 5, flush, stream)
+    s.set_fused(False)
+    fused = {"workload": "same mesh, state and kernel; five stages per cooperative launch with grid barriers",
+             "value": dof * 5 * len(tf) / (sum(tf) * 1e-3), "unit": UNIT, "ms_per_step": sum(tf) / len(tf),
+             "launches_per_step": lf / len(tf)}
+
     # --- SIP variant (theta = 1, Eq. ip_flux), mixed path, same workload
     ssip = dg.Solver(mesh, P, "mixed", stream=sh, mu=1e-3, theta=1.0, C1=0.05)
     ssip.set_state(U0)
@@ -347,6 +356,7 @@ def run_ours(args):
             "fp64_path": {"value": v64, "unit": UNIT, "ms_per_step": sum(t64) / len(t64),
                           "mixed_over_fp64": value / ws / v64},
             "large_mesh": large,
+            "fused_steps": fused,
             "sip_path": sip,
             "p6_large": p6,
             "batch_viv": batch,

@@ -113,6 +113,27 @@ dg_status dg_set_stage_variant(dg_ctx *ctx, int variant);
 /* The tile shape in use: 1 or 2 (the single-node kernel until tuned). */
 int dg_stage_variant(const dg_ctx *ctx);
 
+/* Fused steps (mixed-precision IIP path; no counterpart in the paper): on != 0
+ * runs each dg_lsrk_step as one cooperative launch whose blocks do all five
+ * stages of Algorithm 1 with a grid-wide barrier between stages (the same
+ * arithmetic as five launches; the fused kernel is compiled separately, so a
+ * multiply-add may be contracted differently and results can differ in the
+ * last FP32 bit of a residual).  Every barrier wait is bounded: after
+ * dg_set_barrier_limit waits of about 100 ns it gives up, the launch ends
+ * early, and the next dg_barrier_status, dg_get_state or dg_check_finite
+ * returns DG_ETIMEOUT (the state is then not valid).
+ * Errors: DG_EUNSUPPORTED (FP64 or theta != 0), DG_ECUDA. */
+dg_status dg_set_fused_steps(dg_ctx *ctx, int on);
+
+/* Waits of about 100 ns before a fused step's barrier gives up (default
+ * 2^24, about 1.7 s; 0 makes every wait give up at once). */
+dg_status dg_set_barrier_limit(dg_ctx *ctx, uint32_t waits);
+
+/* DG_ETIMEOUT if a barrier of a fused step since the last check gave up
+ * (then clears the flag), DG_OK otherwise.  Synchronises when fused steps
+ * ran.  Errors: DG_EINVAL, DG_ECUDA. */
+dg_status dg_barrier_status(dg_ctx *ctx);
+
 /* Copy the state in ([K][4][Np] FP64; host pointer if on_device == 0, device
  * pointer otherwise) and clear the Runge-Kutta register.
  * Errors: DG_EINVAL (null, no mesh yet), DG_ECUDA. */

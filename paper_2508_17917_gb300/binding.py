@@ -18,7 +18,8 @@ __all__ = ["DG_OK", "DG_PRECISION_FP64", "DG_PRECISION_MIXED", "DG_SOURCE_NONE",
            "dg_wall_forces_noalloc", "DG_NOALLOC_MAX_WALL_FACES", "dg_rigid_step",
            "dg_check_finite", "dg_set_source", "dg_node_coords", "dg_reference_operators",
            "dg_kernel_launches", "dg_last_error", "Solver", "EXPORTED",
-           "dg_set_stage_variant", "dg_stage_variant",
+           "dg_set_stage_variant", "dg_stage_variant", "dg_set_fused_steps", "dg_set_barrier_limit",
+           "dg_barrier_status",
            "DgCase", "dg_batch_create", "dg_batch_destroy", "dg_batch_last_error",
            "dg_batch_kernel_launches", "dg_batch_stream", "dg_batch_case_size",
            "dg_batch_set_stage_variant", "dg_batch_stage_variant", "dg_batch_node_coords",
@@ -84,6 +85,9 @@ EXPORTED = {
     "dg_kernel_launches": (C.c_int64, [C.c_void_p]),
     "dg_set_stage_variant": (C.c_int, [C.c_void_p, C.c_int]),
     "dg_stage_variant": (C.c_int, [C.c_void_p]),
+    "dg_set_fused_steps": (C.c_int, [C.c_void_p, C.c_int]),
+    "dg_set_barrier_limit": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "dg_barrier_status": (C.c_int, [C.c_void_p]),
     "dg_last_error": (C.c_char_p, [C.c_void_p]),
     # include/dg_batch.h
     "dg_batch_create": (C.c_int, [C.POINTER(DgParams), C.c_int, C.POINTER(DgCase), C.POINTER(C.c_void_p)]),
@@ -281,6 +285,18 @@ def dg_stage_variant(ctx):
     return int(lib().dg_stage_variant(ctx))
 
 
+def dg_set_fused_steps(ctx, on):
+    _check(lib().dg_set_fused_steps(ctx, int(bool(on))), ctx)
+
+
+def dg_set_barrier_limit(ctx, waits):
+    _check(lib().dg_set_barrier_limit(ctx, int(waits)), ctx)
+
+
+def dg_barrier_status(ctx):
+    _check(lib().dg_barrier_status(ctx), ctx)
+
+
 def dg_last_error(ctx):
     return lib().dg_last_error(ctx).decode()
 
@@ -354,6 +370,10 @@ class Solver:
     @property
     def variant(self):
         return dg_stage_variant(self.ctx)
+
+    def set_fused(self, on):
+        """One cooperative launch per step (five stages, grid barriers)."""
+        dg_set_fused_steps(self.ctx, on)
 
 
 # ---- include/dg_batch.h ---------------------------------------------------

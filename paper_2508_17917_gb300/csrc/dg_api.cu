@@ -54,6 +54,14 @@ struct dg_ctx {
     dg::LaunchShape shape1, shape2;   // mixed IIP: one / two nodes per thread
     int variant_req = 0;      // 0: pick by timing on first use, 1 or 2: forced
     bool tuned = false;
+    // fused steps: five stages in one cooperative launch with grid barriers
+    bool fused = false;
+    dg::LaunchShape fshape;
+    int fshape_variant = 0;
+    dg::DevBuf<unsigned> bar;
+    dg::DevBuf<int> bar_err;
+    unsigned bar_limit = 1u << 24;
+    bool bar_used = false;
     int source_kind = DG_SOURCE_NONE;
 
     double *cur() { return cur_is_a ? K0a.ptr : K0b.ptr; }
@@ -285,6 +293,45 @@ const char *dg_last_error(const dg_ctx *ctx) { return ctx ? ctx->err.c_str() : "
 
 int64_t dg_kernel_launches(const dg_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
+dg_status dg_set_fused_steps(dg_ctx *c, int on)
+{
+    if (!c) return DG_EINVAL;
+    c->err.clear();
+    if (on && (c->prm.precision != DG_PRECISION_MIXED || c->prm.theta != 0.0))
+        return fail(c, DG_EUNSUPPORTED, "fused steps use the mixed-precision IIP kernels");
+    if (on && !c->bar.ptr) {
+        DG_CUDA(c, c->bar.alloc(2));
+        DG_CUDA(c, c->bar_err.alloc(1));
+        DG_CUDA(c, cudaMemset(c->bar.ptr, 0, 2 * sizeof(unsigned)));
+        DG_CUDA(c, cudaMemset(c->bar_err.ptr, 0, sizeof(int)));
+    }
+    c->fused = on != 0;
+    return DG_OK;
+}
+
+dg_status dg_set_barrier_limit(dg_ctx *c, uint32_t waits)
+{
+    if (!c) return DG_EINVAL;
+    c->bar_limit = waits;
+    return DG_OK;
+}
+
+dg_status dg_barrier_status(dg_ctx *c)
+{
+    if (!c) return DG_EINVAL;
+    c->err.clear();
+    if (!c->bar_used) return DG_OK;
+    int e = 0;
+    DG_CUDA(c, cudaMemcpyAsync(&e, c->bar_err.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    DG_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->bar_used = false;
+    if (e) {
+        DG_CUDA(c, cudaMemset(c->bar_err.ptr, 0, sizeof(int)));
+        return fail(c, DG_ETIMEOUT, "a grid barrier of a fused step gave up waiting; the state is not valid");
+    }
+    return DG_OK;
+}
+
 dg_status dg_set_stage_variant(dg_ctx *c, int variant)
 {
     if (!c) return DG_EINVAL;
@@ -409,6 +456,10 @@ dg_status dg_get_state(dg_ctx *c, double *U, int on_device)
 {
     if (!c) return DG_EINVAL;
     c->err.clear();
+    {
+        dg_status bs = dg_barrier_status(c);
+        if (bs != DG_OK) return bs;
+    }
     if (!U || c->K < 1) return fail(c, DG_EINVAL, "null state or no mesh");
     DG_CUDA(c, cudaMemcpyAsync(U, c->cur(), ndof(c) * sizeof(double),
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
@@ -498,6 +549,51 @@ dg_status dg_rhs(dg_ctx *c, double t, const double vw[2], double *dUdt, int on_d
     return DG_OK;
 }
 
+// One step as a single cooperative launch of the mixed IIP kernel (fused
+// stages); the barrier counters are reset before every launch.
+static dg_status run_fused_step(dg_ctx *c, double dt, const double vw[2])
+{
+    if (c->fshape_variant != c->shape.variant) {
+        cudaError_t e = dg::stage_shape_mixed_fused(c->prm.p, c->shape.variant, false, c->K, c->fshape);
+        if (e != cudaSuccess) return cuda_fail(c, e, "fused stage kernel configuration");
+        c->fshape_variant = c->shape.variant;
+    }
+    dg::StageParams sp{};
+    sp.K0in = c->cur();
+    sp.K0out = c->other();
+    sp.K1 = c->K1.ptr;
+    sp.conn = c->conn.ptr;
+    sp.fmask = c->fmask.ptr;
+    sp.src = (c->source_kind != DG_SOURCE_NONE) ? c->src.ptr : nullptr;
+    sp.Sin = c->scur();
+    sp.Pin = c->pcur();
+    sp.Sout = c->sother();
+    sp.Pout = c->pother();
+    sp.K = c->K;
+    for (int i = 0; i < 5; ++i) {
+        sp.A5[i] = kRkA[i];
+        sp.B5[i] = kRkB[i];
+    }
+    sp.A = kRkA[0];
+    sp.B = kRkB[0];
+    sp.dt = dt;
+    sp.gm1 = c->prm.gamma - 1.0;
+    sp.sig_fac = sigma_factor(c->prm);
+    sp.mode = dg::STAGE_UPDATE;
+    sp.first_stage = 1;
+    sp.geo = c->geo32.ptr;
+    sp.ops = c->ops32.ptr;
+    sp.bar = c->bar.ptr;
+    sp.bar_err = c->bar_err.ptr;
+    sp.bar_limit = c->bar_limit;
+    DG_CUDA(c, cudaMemsetAsync(c->bar.ptr, 0, 2 * sizeof(unsigned), c->stream));
+    DG_CUDA(c, dg::launch_stage_mixed_fused(c->prm.p, false, c->fshape, sp, make_phys<float>(c->prm, vw), c->stream));
+    c->launches += 1;
+    c->cur_is_a = !c->cur_is_a;   // five swaps
+    c->bar_used = true;
+    return DG_OK;
+}
+
 dg_status dg_lsrk_step(dg_ctx *c, double t, double dt, const double vw[2])
 {
     if (!c) return DG_EINVAL;
@@ -508,6 +604,7 @@ dg_status dg_lsrk_step(dg_ctx *c, double t, double dt, const double vw[2])
         dg_status st = tune_stage(c, vw);
         if (st != DG_OK) return st;
     }
+    if (c->fused) return run_fused_step(c, dt, vw);
     for (int s = 0; s < 5; ++s) {
         dg_status st = run_stage(c, s, t + kRkC[s] * dt, dt, vw, dg::STAGE_UPDATE, c->cur(), c->other(), nullptr);
         if (st != DG_OK) return st;
@@ -566,6 +663,10 @@ dg_status dg_check_finite(dg_ctx *c, int *ok)
 {
     if (!c) return DG_EINVAL;
     c->err.clear();
+    {
+        dg_status bs = dg_barrier_status(c);
+        if (bs != DG_OK) return bs;
+    }
     if (!ok || c->K < 1) return fail(c, DG_EINVAL, "null output or no mesh");
     DG_CUDA(c, cudaMemsetAsync(c->flag.ptr, 0, sizeof(int), c->stream));
     DG_CUDA(c, dg::launch_nonfinite(c->cur(), static_cast<long long>(ndof(c)), c->flag.ptr, c->stream));

@@ -73,6 +73,13 @@ struct StageParams {
     const int4 *tiles;
     const BatchCase *cases;
     long long ntiles;
+    // fused variant: the five stages of one step (Algorithm 1) in one
+    // cooperative launch, a grid barrier between stages; the K0 / FP32-copy /
+    // pressure buffers swap roles after every stage
+    double A5[5], B5[5];
+    unsigned *bar;             // [0] arrivals, [1] generation
+    int *bar_err;              // set to 1 when a barrier wait gave up
+    unsigned bar_limit;        // waits of about 100 ns before giving up
 };
 
 template <int P>

@@ -54,6 +54,69 @@ __device__ __forceinline__ void cp_async16(unsigned dst, const void *src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
 }
 
+// Grid-wide barrier for the fused (cooperative) launch.  Thread 0 of every
+// block makes the block's writes visible, counts the block in and waits for
+// the generation to advance; the last block in resets the count and advances
+// it.  Each wait gives up after `limit` sleeps of about 100 ns, sets *err and
+// the kernel returns; blocks already waiting see *err and return too.  All
+// blocks of a cooperative launch are resident, so a wait can only run out
+// when the limit is (deliberately) too small.  Returns false on an error.
+__device__ __forceinline__ bool grid_sync(unsigned *bar, int *err, unsigned nblocks, unsigned limit)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = bar + 1;
+        volatile int *verr = err;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned prev = atomicAdd(bar, 1u);
+        int ok = 1;
+        if (prev == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned it = 0;
+            while (*vgen == gen) {
+                if (*verr || it >= limit) {
+                    ok = 0;
+                    break;
+                }
+                ++it;
+                __nanosleep(100);
+            }
+        }
+        if (!ok) atomicExch(err, 1);
+        __threadfence();
+        s_ok = ok && !*verr;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Switch the stage-dependent fields of a fused launch to stage `stg`:
+// ping-pong buffers, Runge-Kutta coefficients, first-stage flag.
+__device__ __forceinline__ void fused_stage(StageParams &sp, int stg)
+{
+    if (stg > 0) {
+        double *o = const_cast<double *>(sp.K0in);
+        sp.K0in = sp.K0out;
+        sp.K0out = o;
+        float4 *so = const_cast<float4 *>(sp.Sin);
+        sp.Sin = sp.Sout;
+        sp.Sout = so;
+        float *po = const_cast<float *>(sp.Pin);
+        sp.Pin = sp.Pout;
+        sp.Pout = po;
+    }
+    // constant indices only: a dynamically indexed parameter array would be
+    // copied to local memory
+    sp.A = stg == 0 ? sp.A5[0] : stg == 1 ? sp.A5[1] : stg == 2 ? sp.A5[2] : stg == 3 ? sp.A5[3] : sp.A5[4];
+    sp.B = stg == 0 ? sp.B5[0] : stg == 1 ? sp.B5[1] : stg == 2 ? sp.B5[2] : stg == 3 ? sp.B5[3] : sp.B5[4];
+    sp.first_stage = (stg == 0) ? 1 : 0;
+}
+
 template <int P, bool TH = false, int EE = Shape<P>::E>
 struct MixedLayout {
     using S = Shape<P>;
@@ -84,7 +147,7 @@ struct MixedLayout {
 __device__ __forceinline__ void f4_to(const float4 &a, float o[4]) { o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; }
 __device__ __forceinline__ float4 to_f4(const float o[4]) { return make_float4(o[0], o[1], o[2], o[3]); }
 
-template <int P, bool TH, bool BATCH = false>
+template <int P, bool TH, bool BATCH = false, bool FUSE = false>
 __global__ void __launch_bounds__(Shape<P>::NT, TH ? 2 : 3)
 stage_mixed_kernel(StageParams sp, Phys<float> ph)
 {
@@ -133,13 +196,19 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
     const float theta = static_cast<float>(sp.theta);
     float dtr = static_cast<float>(sp.dt);
     const bool update = sp.mode == STAGE_UPDATE;
-    const bool need_k1 = update && !sp.first_stage;
+    bool need_k1 = update && !sp.first_stage;
     __syncthreads();
 
     const int ve = tid / Np, vi = tid - (tid / Np) * Np;
     const int fe = tid / NF, fm = tid - (tid / NF) * NF;
     const int ff = fm / Nfp, fi = fm - (fm / Nfp) * Nfp;
 
+    for (int stg = 0; stg < (FUSE ? 5 : 1); ++stg) {
+    if constexpr (FUSE) {
+        if (stg > 0 && !grid_sync(sp.bar, sp.bar_err, gridDim.x, sp.bar_limit)) return;
+        fused_stage(sp, stg);
+        need_k1 = update && stg > 0;
+    }
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         long long k0 = tile * E;
         int ne = static_cast<int>((K - k0) < E ? (K - k0) : E);
@@ -465,6 +534,7 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
             }
         }
     }
+    }  // stages
 }
 
 // Lambda_K of Eq. rayleigh_bound in FP32 from the FP32 state copy and the

@@ -26,7 +26,7 @@ struct Shape2 {
     static constexpr int E = NT / W;
 };
 
-template <int P, bool BATCH>
+template <int P, bool BATCH, bool FUSE = false>
 __global__ void __launch_bounds__(128, 4)
 stage_mixed2_kernel(StageParams sp, Phys<float> ph)
 {
@@ -69,7 +69,7 @@ stage_mixed2_kernel(StageParams sp, Phys<float> ph)
     const float sig_fac = static_cast<float>(sp.sig_fac);
     float dtr = static_cast<float>(sp.dt);
     const bool update = sp.mode == STAGE_UPDATE;
-    const bool need_k1 = update && !sp.first_stage;
+    bool need_k1 = update && !sp.first_stage;
     __syncthreads();
 
     const int el = tid / W, q = tid - (tid / W) * W;
@@ -83,6 +83,12 @@ stage_mixed2_kernel(StageParams sp, Phys<float> ph)
     const int fi0 = rr, fi1 = (rr + HF < Nfp) ? rr + HF : rr;
     const bool f1 = fslot && (rr + HF < Nfp);
 
+    for (int stg = 0; stg < (FUSE ? 5 : 1); ++stg) {
+    if constexpr (FUSE) {
+        if (stg > 0 && !grid_sync(sp.bar, sp.bar_err, gridDim.x, sp.bar_limit)) return;
+        fused_stage(sp, stg);
+        need_k1 = update && stg > 0;
+    }
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         long long k0 = tile * E;
         int ne = static_cast<int>((K - k0) < E ? (K - k0) : E);
@@ -370,6 +376,7 @@ stage_mixed2_kernel(StageParams sp, Phys<float> ph)
             }
         }
     }
+    }  // stages
 }
 
 }  // namespace dg

@@ -44,6 +44,11 @@ cudaError_t stage_shape_mixed2(int p, long long units, bool batch, LaunchShape &
 cudaError_t launch_stage_mixed2(int p, bool batch, const LaunchShape &ls, const StageParams &sp,
                                 const Phys<float> &ph, cudaStream_t st);
 int stage_tile_elems2(int p);
+// five stages per cooperative launch (mixed IIP, shape `variant`): grid of
+// co-resident blocks for `units` (K, or the tile count of a batch table)
+cudaError_t stage_shape_mixed_fused(int p, int variant, bool batch, long long units, LaunchShape &out);
+cudaError_t launch_stage_mixed_fused(int p, bool batch, const LaunchShape &ls, const StageParams &sp,
+                                     const Phys<float> &ph, cudaStream_t st);
 // elements per tile of the mixed kernel for degree p
 int stage_tile_elems(int p);
 // FP32 copy [K][Np] float4 and FP64-recovered pressure [K][NpP] of a state

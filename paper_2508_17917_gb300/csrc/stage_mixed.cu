@@ -111,6 +111,64 @@ cudaError_t launch2_p(const LaunchShape &ls, const StageParams &sp, const Phys<f
     return cudaGetLastError();
 }
 
+// fused variant: five stages per cooperative launch; the grid is the number
+// of co-resident blocks of that instantiation (capped by the tile count)
+template <int P, int V, bool BATCH>
+cudaError_t fused_shape_p(long long units, LaunchShape &ls)
+{
+    const void *kern;
+    int nt;
+    size_t smem;
+    long long ntiles;
+    if (V == 2) {
+        kern = reinterpret_cast<const void *>(stage_mixed2_kernel<P, BATCH, true>);
+        nt = Shape2<P>::NT;
+        smem = MixedLayout<P, false, Shape2<P>::E>::bytes;
+        ntiles = BATCH ? units : (units + Shape2<P>::E - 1) / Shape2<P>::E;
+        ls.elems_per_tile = Shape2<P>::E;
+    } else {
+        kern = reinterpret_cast<const void *>(stage_mixed_kernel<P, false, BATCH, true>);
+        nt = Shape<P>::NT;
+        smem = MixedLayout<P, false>::bytes;
+        ntiles = BATCH ? units : (units + Shape<P>::E - 1) / Shape<P>::E;
+        ls.elems_per_tile = Shape<P>::E;
+    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long grid = static_cast<long long>(sms) * per_sm;
+    ls.grid = static_cast<int>(ntiles < grid ? ntiles : grid);
+    ls.threads = nt;
+    ls.smem = smem;
+    ls.theta = false;
+    ls.variant = V;
+    return cudaSuccess;
+}
+
+template <int P, int V, bool BATCH>
+cudaError_t fused_launch_p(const LaunchShape &ls, const StageParams &sp, const Phys<float> &ph, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ls.grid);
+    cfg.blockDim = dim3(ls.threads);
+    cfg.dynamicSmemBytes = ls.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (V == 2) return cudaLaunchKernelEx(&cfg, stage_mixed2_kernel<P, BATCH, true>, sp, ph);
+    return cudaLaunchKernelEx(&cfg, stage_mixed_kernel<P, false, BATCH, true>, sp, ph);
+}
+
 template <int P>
 cudaError_t shadow_p(const double *K0, long long K, double gm1, float4 *S, float *Pr, cudaStream_t st)
 {
@@ -196,6 +254,25 @@ cudaError_t launch_stage_mixed2(int p, bool batch, const LaunchShape &ls, const 
                                 const Phys<float> &ph, cudaStream_t st)
 {
 #define C_(P) (batch ? launch2_p<P, true>(ls, sp, ph, st) : launch2_p<P, false>(ls, sp, ph, st))
+    DG_SWITCH_P(p, C_)
+#undef C_
+}
+
+cudaError_t stage_shape_mixed_fused(int p, int variant, bool batch, long long units, LaunchShape &out)
+{
+#define C_(P) (variant == 2 ? (batch ? fused_shape_p<P, 2, true>(units, out) : fused_shape_p<P, 2, false>(units, out)) \
+                            : (batch ? fused_shape_p<P, 1, true>(units, out) : fused_shape_p<P, 1, false>(units, out)))
+    DG_SWITCH_P(p, C_)
+#undef C_
+}
+
+cudaError_t launch_stage_mixed_fused(int p, bool batch, const LaunchShape &ls, const StageParams &sp,
+                                     const Phys<float> &ph, cudaStream_t st)
+{
+#define C_(P) (ls.variant == 2 ? (batch ? fused_launch_p<P, 2, true>(ls, sp, ph, st)                 \
+                                        : fused_launch_p<P, 2, false>(ls, sp, ph, st))               \
+                               : (batch ? fused_launch_p<P, 1, true>(ls, sp, ph, st)                 \
+                                        : fused_launch_p<P, 1, false>(ls, sp, ph, st)))
     DG_SWITCH_P(p, C_)
 #undef C_
 }
