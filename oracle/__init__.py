@@ -87,7 +87,8 @@ class _Problem(C.Structure):
                 ("theta", C.c_double), ("C1", C.c_double),
                 ("rho_inf", C.c_double), ("u_inf", C.c_double), ("v_inf", C.c_double),
                 ("p_inf", C.c_double), ("adiabatic_zero_heatflux", C.c_longlong),
-                ("source_kind", C.c_longlong), ("src_kappa", C.c_double), ("src_C2", C.c_double)]
+                ("source_kind", C.c_longlong), ("src_kappa", C.c_double), ("src_C2", C.c_double),
+                ("Nq", C.c_longlong), ("Vq", _dp), ("Vqr", _dp), ("Vqs", _dp), ("wq", _dp)]
 
 
 class Problem:
@@ -96,7 +97,7 @@ class Problem:
 
     def __init__(self, mesh, p, gamma=1.4, Pr=0.72, mu=1e-3, C1=0.01, theta=0.0,
                  rho_inf=1.0, u_inf=1.0, v_inf=0.0, p_inf=1.0, adiabatic_zero_heatflux=1,
-                 source=None):
+                 source=None, overint=0):
         if not 1 <= p <= 6:
             raise ValueError("oracle supports 1 <= p <= 6")
         ops = refelem.operators(p)
@@ -126,6 +127,12 @@ class Problem:
         s.adiabatic_zero_heatflux = int(adiabatic_zero_heatflux)
         if source is not None:          # ("manufactured", kappa, C2) of Sec. 3.1
             s.source_kind, s.src_kappa, s.src_C2 = 1, float(source[1]), float(source[2])
+        if overint:                     # volume flux integrated with cubature(overint)
+            oi = refelem.overint_operators(p, int(overint))
+            for name in ("Vq", "Vqr", "Vqs", "wq"):
+                keep[name] = _f64(oi[name])
+                setattr(s, name, keep[name].ctypes.data_as(_dp))
+            s.Nq = int(oi["Nq"])
         self._s = s
         self.params = dict(gamma=gamma, Pr=Pr, mu=mu, C1=C1, theta=theta, rho_inf=rho_inf,
                            u_inf=u_inf, v_inf=v_inf, p_inf=p_inf,

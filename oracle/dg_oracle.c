@@ -61,6 +61,11 @@ typedef struct {
     long long adiabatic_zero_heatflux;
     long long source_kind;                  /* 0 none, 1 manufactured solution of Sec. 3.1 */
     double src_kappa, src_C2;
+    /* over-integration of the volume term (Sec. 2.2, weak matrices): Nq > 0
+     * evaluates the flux at Nq cubature points, with the nodal basis values
+     * Vq and derivatives Vqr, Vqs [Nq][Np] there and weights wq [Nq] */
+    long long Nq;
+    const double *Vq, *Vqr, *Vqs, *wq;
 } oracle_problem;
 
 enum { BC_INTERIOR = 0, BC_WALL = 1, BC_FARFIELD = 2 };
@@ -623,6 +628,38 @@ int oracle_rhs(const oracle_problem *P, const double *U, double t, const double 
         }
         /* weak volume term (Dr^T M F) scaled by the metric, then M^-1 */
         double rx = P->rx[k], ry = P->ry[k], sx = P->sx[k], sy = P->sy[k], J = P->J[k];
+        /* over-integrated volume term: int F . grad l_m = sum_q w_q F(U_q, grad U_q) . grad l_m(x_q) */
+        double oiv[4][32];
+        if (P->Nq > 0) {
+            memset(oiv, 0, sizeof oiv);
+            for (long long qn = 0; qn < P->Nq; ++qn) {
+                double u[4], ur[4], us[4], ux[4], uy[4], cx[4], cy[4], vx[4], vy[4];
+                for (int c = 0; c < 4; ++c) {
+                    double a = 0, b = 0, d = 0;
+                    for (int j = 0; j < Np; ++j) {
+                        double uj = U[(k * 4 + c) * Np + j];
+                        a += P->Vq[qn * Np + j] * uj;
+                        b += P->Vqr[qn * Np + j] * uj;
+                        d += P->Vqs[qn * Np + j] * uj;
+                    }
+                    u[c] = a;
+                    ur[c] = b;
+                    us[c] = d;
+                    ux[c] = rx * b + sx * d;
+                    uy[c] = ry * b + sy * d;
+                }
+                (void)ur;
+                (void)us;
+                adv_flux(u, vw, P->gamma, cx, cy);
+                visc_flux(u, ux, uy, P->gamma, P->Pr, P->mu, vx, vy);
+                for (int m = 0; m < Np; ++m) {
+                    double lx = rx * P->Vqr[qn * Np + m] + sx * P->Vqs[qn * Np + m];
+                    double ly = ry * P->Vqr[qn * Np + m] + sy * P->Vqs[qn * Np + m];
+                    for (int c = 0; c < 4; ++c)
+                        oiv[c][m] += P->wq[qn] * (lx * (cx[c] - vx[c]) + ly * (cy[c] - vy[c]));
+                }
+            }
+        }
         for (int c = 0; c < 4; ++c) {
             double a[32], b[32], vol[32];
             for (int j = 0; j < Np; ++j) {
@@ -639,6 +676,7 @@ int oracle_rhs(const oracle_problem *P, const double *U, double t, const double 
                 for (int j = 0; j < Np; ++j)
                     acc += (rx * P->Dr[j * Np + m] + sx * P->Ds[j * Np + m]) * a[j]
                          + (ry * P->Dr[j * Np + m] + sy * P->Ds[j * Np + m]) * b[j];
+                if (P->Nq > 0) acc = oiv[c][m];
                 /* (1/J) M^-1 of [ J * vol - face + theta terms ] */
                 vol[m] = acc - q[c][m] / J + th[c][m] / J;
             }

@@ -185,3 +185,33 @@ def operators(p: int):
     LIFT = Minv @ Emat
     return dict(p=p, Np=Np, Nfp=Nfp, r=r, s=s, V=V, Dr=Dr, Ds=Ds, M=M,
                 Minv=Minv, Fmask=Fmask, M1D=M1D, Emat=Emat, LIFT=LIFT)
+
+
+@functools.lru_cache(maxsize=None)
+def cubature(deg: int):
+    """Collapsed-coordinate Gauss rule on the reference triangle, exact for
+    polynomials of total degree <= deg: N = ceil((deg + 1) / 2) Gauss-Legendre
+    points in a and N Gauss-Jacobi (1, 0) points in b, r = (1 + a)(1 - b)/2 - 1,
+    s = b, weight w_a w_b / 2 (dr ds = (1 - b)/2 da db)."""
+    n = (deg + 2) // 2
+    a, wa = roots_jacobi(n, 0.0, 0.0)
+    b, wb = roots_jacobi(n, 1.0, 0.0)
+    A, B = np.meshgrid(a, b, indexing="ij")
+    W = np.outer(wa, wb) / 2.0
+    r = (1.0 + A) * (1.0 - B) / 2.0 - 1.0
+    return r.ravel(), B.ravel(), W.ravel()
+
+
+@functools.lru_cache(maxsize=None)
+def overint_operators(p: int, deg: int):
+    """Nodal basis values and (r, s) derivatives at the cubature points of
+    `cubature(deg)`: Vq, Vqr, Vqs [Nq][Np] (ell_j and its derivatives at x_q)
+    and the weights wq [Nq]."""
+    ops = operators(p)
+    rq, sq, wq = cubature(deg)
+    modes = _modes(p)
+    Vinv = np.linalg.inv(ops["V"])
+    Vq = np.column_stack([pkd(rq, sq, i, j) for (i, j) in modes]) @ Vinv
+    Vqr = np.column_stack([pkd_grad(rq, sq, i, j)[0] for (i, j) in modes]) @ Vinv
+    Vqs = np.column_stack([pkd_grad(rq, sq, i, j)[1] for (i, j) in modes]) @ Vinv
+    return dict(rq=rq, sq=sq, wq=wq, Vq=Vq, Vqr=Vqr, Vqs=Vqs, Nq=rq.size)
