@@ -113,6 +113,20 @@ dg_status dg_set_stage_variant(dg_ctx *ctx, int variant);
 /* The tile shape in use: 1 or 2 (the single-node kernel until tuned). */
 int dg_stage_variant(const dg_ctx *ctx);
 
+/* Over-integration of the volume term (Sec. 2.2, weak matrices: the paper
+ * evaluates F(U_h) with a cubature rule to curb aliasing): on != 0 makes the
+ * FP64 path integrate int_K F(U_h, grad U_h) . grad l_i with a collapsed
+ * Gauss rule of total degree dg_overint_degree(p) = min(3p, 15) (at most 64
+ * points) instead of through the nodal interpolant of F; the residual is
+ * then R = M^-1 sum_q w_q grad l(x_q) . F_q - LIFT (Fscale H) (weak form).
+ * Face fluxes stay at the LGL face nodes; the time-step bound is unchanged.
+ * Errors: DG_EUNSUPPORTED (mixed precision or theta != 0), DG_ECUDA. */
+dg_status dg_set_overintegration(dg_ctx *ctx, int on);
+
+/* Degree of the over-integration rule for polynomial degree p (0 if p is
+ * outside 1..6). */
+int dg_overint_degree(int p);
+
 /* Fused steps (mixed-precision IIP path; no counterpart in the paper): on != 0
  * runs each dg_lsrk_step as one cooperative launch whose blocks do all five
  * stages of Algorithm 1 with a grid-wide barrier between stages (the same

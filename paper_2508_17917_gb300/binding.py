@@ -19,7 +19,7 @@ __all__ = ["DG_OK", "DG_PRECISION_FP64", "DG_PRECISION_MIXED", "DG_SOURCE_NONE",
            "dg_check_finite", "dg_set_source", "dg_node_coords", "dg_reference_operators",
            "dg_kernel_launches", "dg_last_error", "Solver", "EXPORTED",
            "dg_set_stage_variant", "dg_stage_variant", "dg_set_fused_steps", "dg_set_barrier_limit",
-           "dg_barrier_status",
+           "dg_barrier_status", "dg_set_overintegration", "dg_overint_degree",
            "DgCase", "dg_batch_create", "dg_batch_destroy", "dg_batch_last_error",
            "dg_batch_kernel_launches", "dg_batch_stream", "dg_batch_case_size",
            "dg_batch_set_stage_variant", "dg_batch_stage_variant", "dg_batch_node_coords",
@@ -86,6 +86,8 @@ EXPORTED = {
     "dg_set_stage_variant": (C.c_int, [C.c_void_p, C.c_int]),
     "dg_stage_variant": (C.c_int, [C.c_void_p]),
     "dg_set_fused_steps": (C.c_int, [C.c_void_p, C.c_int]),
+    "dg_set_overintegration": (C.c_int, [C.c_void_p, C.c_int]),
+    "dg_overint_degree": (C.c_int, [C.c_int]),
     "dg_set_barrier_limit": (C.c_int, [C.c_void_p, C.c_uint32]),
     "dg_barrier_status": (C.c_int, [C.c_void_p]),
     "dg_last_error": (C.c_char_p, [C.c_void_p]),
@@ -285,6 +287,14 @@ def dg_stage_variant(ctx):
     return int(lib().dg_stage_variant(ctx))
 
 
+def dg_set_overintegration(ctx, on):
+    _check(lib().dg_set_overintegration(ctx, int(bool(on))), ctx)
+
+
+def dg_overint_degree(p):
+    return int(lib().dg_overint_degree(int(p)))
+
+
 def dg_set_fused_steps(ctx, on):
     _check(lib().dg_set_fused_steps(ctx, int(bool(on))), ctx)
 
@@ -370,6 +380,10 @@ class Solver:
     @property
     def variant(self):
         return dg_stage_variant(self.ctx)
+
+    def set_overint(self, on):
+        """Cubature-integrated volume term (FP64 path)."""
+        dg_set_overintegration(self.ctx, on)
 
     def set_fused(self, on):
         """One cooperative launch per step (five stages, grid barriers)."""

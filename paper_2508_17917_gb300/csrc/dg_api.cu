@@ -55,6 +55,7 @@ struct dg_ctx {
     int variant_req = 0;      // 0: pick by timing on first use, 1 or 2: forced
     bool tuned = false;
     // fused steps: five stages in one cooperative launch with grid barriers
+    bool overint = false;     // FP64 path: over-integrated volume term
     bool fused = false;
     dg::LaunchShape fshape;
     int fshape_variant = 0;
@@ -260,6 +261,15 @@ dg_status dg_create(const dg_params *params, void *cuda_stream, dg_ctx **out)
     o64.insert(o64.end(), c->ops.LIFT.begin(), c->ops.LIFT.end());
     o64.insert(o64.end(), c->ops.Wr.begin(), c->ops.Wr.end());
     o64.insert(o64.end(), c->ops.Ws.begin(), c->ops.Ws.end());
+    {
+        // over-integration operators, used by the FP64 kernel when enabled
+        dg::OverintOps oi;
+        if (!dg::build_overint_operators(c->ops, dg::overint_degree(p.p), oi)) {
+            delete c;
+            return DG_EINVAL;
+        }
+        for (const auto *v : {&oi.Vq, &oi.Vqr, &oi.Vqs, &oi.Sr, &oi.Ss}) o64.insert(o64.end(), v->begin(), v->end());
+    }
     std::vector<float> o32(o64.begin(), o64.end());
     if (c->ops64.alloc(o64.size()) != cudaSuccess || c->ops32.alloc(o32.size()) != cudaSuccess ||
         c->Dr64.alloc(Np * Np) != cudaSuccess || c->Ds64.alloc(Np * Np) != cudaSuccess ||
@@ -292,6 +302,22 @@ dg_status dg_destroy(dg_ctx *ctx)
 const char *dg_last_error(const dg_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 int64_t dg_kernel_launches(const dg_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+dg_status dg_set_overintegration(dg_ctx *c, int on)
+{
+    if (!c) return DG_EINVAL;
+    c->err.clear();
+    if (on && (c->prm.precision != DG_PRECISION_FP64 || c->prm.theta != 0.0))
+        return fail(c, DG_EUNSUPPORTED, "over-integration is implemented in the FP64 IIP kernel");
+    c->overint = on != 0;
+    if (c->K > 0 && c->prm.precision == DG_PRECISION_FP64) {
+        cudaError_t e = dg::stage_shape_fp64(c->prm.p, c->K, false, c->shape, c->overint);
+        if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel configuration");
+    }
+    return DG_OK;
+}
+
+int dg_overint_degree(int p) { return (p >= 1 && p <= 6) ? dg::overint_degree(p) : 0; }
 
 dg_status dg_set_fused_steps(dg_ctx *c, int on)
 {
@@ -405,7 +431,7 @@ dg_status dg_set_mesh(dg_ctx *c, int64_t Nv, const double *vx, const double *vy,
     c->geo64h.swap(geo);
     c->source_kind = DG_SOURCE_NONE;
     const bool th = c->prm.theta != 0.0;
-    cudaError_t e = (c->prm.precision == DG_PRECISION_FP64) ? dg::stage_shape_fp64(c->prm.p, K, th, c->shape)
+    cudaError_t e = (c->prm.precision == DG_PRECISION_FP64) ? dg::stage_shape_fp64(c->prm.p, K, th, c->shape, c->overint)
                                                              : dg::stage_shape_mixed(c->prm.p, K, th, c->shape);
     if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel configuration");
     c->shape1 = c->shape;

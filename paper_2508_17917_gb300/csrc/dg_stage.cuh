@@ -95,12 +95,24 @@ struct Shape {
 // geometry record (real[16]) per element
 enum { G_RX = 0, G_RY = 1, G_SX = 2, G_SY = 3, G_J = 4, G_NX = 5, G_NY = 8, G_FS = 11 };
 
-template <int P, typename real, bool TH = false>
+// Over-integration rule of degree p: collapsed Gauss rule of degree
+// min(3p, 15), N = deg / 2 + 1 points per direction, Nq = N^2 <= 64.
+template <int P>
+struct OIShape {
+    static constexpr int deg = (3 * P < 15) ? 3 * P : 15;
+    static constexpr int N = deg / 2 + 1;
+    static constexpr int Nq = N * N;
+};
+
+template <int P, typename real, bool TH = false, bool OI = false>
 struct Smem {
     using S = Shape<P>;
     static constexpr int Np = S::Np, NF = S::NF, E = S::E;
+    static constexpr int Nq = OI ? OIShape<P>::Nq : 0;
     // sizes in elements of `real`
     static constexpr int ops = 2 * Np * Np + Np * NF + (TH ? 2 * Np * Np : 0);
+    static constexpr int oiops = 5 * Nq * Np;           // Vq, Vqr, Vqs [Nq][Np]; Sr, Ss [Np][Nq]
+    static constexpr int fq = 2 * E * 4 * Nq;           // contravariant fluxes at the cubature points
     static constexpr int u = E * 4 * Np;
     static constexpr int gx = E * 4 * Np;
     static constexpr int gy = E * 4 * Np;
@@ -113,17 +125,18 @@ struct Smem {
     static constexpr int geo = E * 16;
     static constexpr int ngeo = E * 3 * 8;
     static constexpr int th = TH ? E * NF * 8 : 0;
-    static constexpr int total_real = ops + u + gx + gy + fr + fs + pr + nb + norm + dh + geo + ngeo + th;
+    static constexpr int total_real = ops + u + gx + gy + fr + fs + pr + nb + norm + dh + geo + ngeo + th + oiops + fq;
     static constexpr size_t bytes = total_real * sizeof(real) + NF * sizeof(int) + 16;
 };
 
-template <int P, typename real, bool TH>
+template <int P, typename real, bool TH, bool OI = false>
 __global__ void __launch_bounds__(Shape<P>::NT)
 stage_kernel(StageParams sp, Phys<real> ph)
 {
     using S = Shape<P>;
     constexpr int Np = S::Np, Nfp = S::Nfp, NF = S::NF, E = S::E, NT = S::NT;
-    using L = Smem<P, real, TH>;
+    using L = Smem<P, real, TH, OI>;
+    constexpr int Nq = L::Nq;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *sDr = reinterpret_cast<real *>(smem_raw);
     real *sDs = sDr + Np * Np;
@@ -142,13 +155,24 @@ stage_kernel(StageParams sp, Phys<real> ph)
     real *sGeo = sDH + L::dh;
     real *sNGeo = sGeo + L::geo;
     real *sTH = sNGeo + L::ngeo;               // theta variant: Fscale theta w (t_x, t_y)
-    int *sFm = reinterpret_cast<int *>(sTH + L::th);
+    real *sVq = sTH + L::th;                   // over-integration: Vq | Vqr | Vqs | Sr | Ss
+    real *sVqr = sVq + Nq * Np;
+    real *sVqs = sVqr + Nq * Np;
+    real *sSr = sVqs + Nq * Np;
+    real *sSs = sSr + Np * Nq;
+    real *sFq = sVq + L::oiops;                // [E][4][Nq] x (r, s)
+    int *sFm = reinterpret_cast<int *>(sFq + L::fq);
 
     const int tid = threadIdx.x;
     {
         const real *ops = static_cast<const real *>(sp.ops);
         for (int i = tid; i < L::ops; i += NT) sDr[i] = ops[i];
         for (int i = tid; i < NF; i += NT) sFm[i] = sp.fmask[i];
+        if constexpr (OI) {
+            // the operator buffer holds Dr | Ds | LIFT | Wr | Ws | Vq | Vqr | Vqs | Sr | Ss
+            const real *oi = ops + 4 * Np * Np + Np * NF;
+            for (int i = tid; i < L::oiops; i += NT) sVq[i] = oi[i];
+        }
     }
     const real *geo = static_cast<const real *>(sp.geo);
     const long long K = sp.K;
@@ -228,6 +252,44 @@ stage_kernel(StageParams sp, Phys<real> ph)
                 sFs[(ve * 4 + c) * Np + vi] = sx * Fx + sy * Fy;
             }
         }
+        if constexpr (OI) {
+            // flux at the cubature points from the state and broken gradient
+            // interpolated there (the polynomial U_h itself, not nodal values)
+            if (vol) {
+                const real *u_e = sU + ve * 4 * Np;
+                const real *g = sGeo + ve * 16;
+                const real rx = g[G_RX], ry = g[G_RY], sx = g[G_SX], sy = g[G_SY];
+                for (int q = vi; q < Nq; q += Np) {
+                    real u[4] = {0, 0, 0, 0}, ur[4] = {0, 0, 0, 0}, us[4] = {0, 0, 0, 0};
+                    for (int j = 0; j < Np; ++j) {
+                        const real a = sVq[q * Np + j], b = sVqr[q * Np + j], d = sVqs[q * Np + j];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const real uj = u_e[c * Np + j];
+                            u[c] += a * uj;
+                            ur[c] += b * uj;
+                            us[c] += d * uj;
+                        }
+                    }
+                    real gxq[4], gyq[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        gxq[c] = rx * ur[c] + sx * us[c];
+                        gyq[c] = ry * ur[c] + sy * us[c];
+                    }
+                    const real pq = pressure<real>(u, to_f64<real>(u[3]), gm1d);
+                    real cx[4], cy[4], vx[4], vy[4];
+                    adv_flux(u, pq, ph, cx, cy);
+                    visc_flux(u, gxq, gyq, ph, vx, vy);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const real Fx = cx[c] - vx[c], Fy = cy[c] - vy[c];
+                        sFq[((ve * 4 + c) * Nq + q) * 2] = rx * Fx + ry * Fy;
+                        sFq[((ve * 4 + c) * Nq + q) * 2 + 1] = sx * Fx + sy * Fy;
+                    }
+                }
+            }
+        }
         const int fe = tid / NF, fm = tid - (tid / NF) * NF;
         const bool face = fe < ne;
         const int ff = fm / Nfp, fi = fm - (fm / Nfp) * Nfp;
@@ -269,7 +331,7 @@ stage_kernel(StageParams sp, Phys<real> ph)
 
         // ---- P3: divergence (volume) and face flux (face nodes)
         real R[4] = {0, 0, 0, 0};
-        if (vol) {
+        if (vol && !OI) {
             const real *fr = sFr + ve * 4 * Np;
             const real *fs = sFs + ve * 4 * Np;
 #pragma unroll
@@ -277,6 +339,17 @@ stage_kernel(StageParams sp, Phys<real> ph)
                 real dr = sDr[vi * Np + j], ds = sDs[vi * Np + j];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) R[c] -= dr * fr[c * Np + j] + ds * fs[c * Np + j];
+            }
+        }
+        if constexpr (OI) {
+            // weak volume term: sum_q Sr_iq Fr_q + Ss_iq Fs_q (Sr = M^-1 Vqr^T W)
+            if (vol) {
+                const real *fq = sFq + ve * 4 * Nq * 2;
+                for (int q = 0; q < Nq; ++q) {
+                    const real a = sSr[vi * Nq + q], b = sSs[vi * Nq + q];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) R[c] += a * fq[(c * Nq + q) * 2] + b * fq[(c * Nq + q) * 2 + 1];
+                }
             }
         }
         if (face) {
@@ -379,6 +452,11 @@ stage_kernel(StageParams sp, Phys<real> ph)
                     jmp[c] = up[c] - ub[c];
                 }
                 gs[0] = rb; gs[1] = ph.vw1; gs[2] = ph.vw2; gs[3] = ub[3] / rb;
+            }
+            if constexpr (OI) {
+                // weak form: the face term is -H itself, without the F+.n of the strong form
+#pragma unroll
+                for (int c = 0; c < 4; ++c) dH[c] -= Fnp[c] - (vxp[c] * n1 + vyp[c] * n2);
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c) sDH[(fe * NF + fm) * 4 + c] = fsc * dH[c];

@@ -13,6 +13,7 @@ struct BatchCase;
 struct LaunchShape {
     bool theta = false;      // kernel variant with the theta terms of the IP flux
     int variant = 1;         // mixed IIP kernel: 1 node per thread (1) or 2 nodes per thread (2)
+    bool overint = false;    // FP64 kernel: volume flux integrated with a cubature rule
     int grid = 0;
     int threads = 0;
     size_t smem = 0;
@@ -21,7 +22,7 @@ struct LaunchShape {
 
 // Launch configuration of the fused stage kernel for degree p and K elements
 // on the current device (persistent grid: SMs x resident CTAs, capped by tiles).
-cudaError_t stage_shape_fp64(int p, long long K, bool theta, LaunchShape &out);
+cudaError_t stage_shape_fp64(int p, long long K, bool theta, LaunchShape &out, bool overint = false);
 cudaError_t stage_shape_mixed(int p, long long K, bool theta, LaunchShape &out);
 cudaError_t launch_stage_fp64(int p, const LaunchShape &ls, const StageParams &sp,
                               const Phys<double> &ph, cudaStream_t st);

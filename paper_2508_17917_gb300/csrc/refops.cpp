@@ -155,7 +155,112 @@ double edge_warp(int p, const std::vector<double> &gl, double t)
     return 0.0;
 }
 
+// Orthonormal PKD modes and their (r, s) derivatives at n points (r[k], s[k]),
+// row-major [n][Np]: psi_ij = sqrt2 P_i(a) P_j^(2i+1,0)(b) (1-b)^i with the
+// collapsed coordinates a = 2(1+r)/(1-s) - 1, b = s.
+void vandermonde(int p, const double *rr, const double *ss, int n, std::vector<double> &V,
+                 std::vector<double> &Vr, std::vector<double> &Vs)
+{
+    const int Np = (p + 1) * (p + 2) / 2;
+    V.assign(static_cast<size_t>(n) * Np, 0.0);
+    Vr.assign(V.size(), 0.0);
+    Vs.assign(V.size(), 0.0);
+    for (int nd = 0; nd < n; ++nd) {
+        double r = rr[nd], s = ss[nd];
+        double a = (std::fabs(1.0 - s) > 1e-14) ? 2.0 * (1.0 + r) / (1.0 - s) - 1.0 : -1.0;
+        double b = s, om = 1.0 - b;
+        int col = 0;
+        for (int i = 0; i <= p; ++i)
+            for (int j = 0; j <= p - i; ++j, ++col) {
+                double fa = jacobi(a, 0, 0, i), dfa = jacobi_d(a, 0, 0, i);
+                double gb = jacobi(b, 2.0 * i + 1.0, 0, j), dgb = jacobi_d(b, 2.0 * i + 1.0, 0, j);
+                double omi = std::pow(om, i), omi1 = (i > 0) ? std::pow(om, i - 1) : 0.0;
+                V[nd * Np + col] = std::sqrt(2.0) * fa * gb * omi;
+                // d/dr: da/dr = 2/(1-b)
+                Vr[nd * Np + col] = (i > 0) ? 2.0 * std::sqrt(2.0) * dfa * gb * omi1 : 0.0;
+                // d/ds: da/ds = (1+a)/(1-b), plus the b-dependence of gb (1-b)^i
+                double t1 = (i > 0) ? dfa * (1.0 + a) * gb * omi1 : 0.0;
+                double t2 = fa * (dgb * omi - ((i > 0) ? i * gb * omi1 : 0.0));
+                Vs[nd * Np + col] = std::sqrt(2.0) * (t1 + t2);
+            }
+    }
+}
+
+// n-point Gauss rule of the weight (1-x)^al (1+x)^be on [-1, 1]: the roots
+// of the degree-n orthonormal Jacobi polynomial by Newton's method with
+// deflation, weights 1 / sum_{m<n} P_m(x)^2 (Christoffel numbers).
+void gauss_jacobi(int n, double al, double be, std::vector<double> &x, std::vector<double> &w)
+{
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int k = 0; k < n; ++k) {
+        double t = -std::cos(M_PI * (k + 0.5) / n);
+        if (k > 0 && t <= x[k - 1]) t = x[k - 1] + 1e-3 * (1.0 - x[k - 1]);
+        for (int it = 0; it < 200; ++it) {
+            double P = jacobi(t, al, be, n), dP = jacobi_d(t, al, be, n);
+            double sum = 0.0;
+            for (int j = 0; j < k; ++j) sum += 1.0 / (t - x[j]);
+            double step = P / (dP - P * sum);
+            t -= step;
+            if (std::fabs(step) < 1e-16) break;
+        }
+        x[k] = t;
+    }
+    std::sort(x.begin(), x.end());
+    for (int k = 0; k < n; ++k) {
+        double s = 0.0;
+        for (int m = 0; m < n; ++m) {
+            double v = jacobi(x[k], al, be, m);
+            s += v * v;
+        }
+        w[k] = 1.0 / s;
+    }
+}
+
 }  // namespace
+
+int overint_degree(int p) { return (3 * p < 15) ? 3 * p : 15; }
+
+bool build_overint_operators(const RefOps &o, int deg, OverintOps &out)
+{
+    if (o.Np < 1 || deg < 1) return false;
+    const int p = o.p, Np = o.Np, n = (deg + 2) / 2;
+    std::vector<double> a, wa, b, wb;
+    gauss_jacobi(n, 0.0, 0.0, a, wa);
+    gauss_jacobi(n, 1.0, 0.0, b, wb);
+    const int Nq = n * n;
+    std::vector<double> rq(Nq), sq(Nq);
+    out.deg = deg;
+    out.Nq = Nq;
+    out.wq.assign(Nq, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            const int q = i * n + j;
+            rq[q] = (1.0 + a[i]) * (1.0 - b[j]) / 2.0 - 1.0;
+            sq[q] = b[j];
+            out.wq[q] = wa[i] * wb[j] / 2.0;
+        }
+    std::vector<double> V, Vr, Vs, Q, Qr, Qs, Vinv;
+    vandermonde(p, o.r.data(), o.s.data(), Np, V, Vr, Vs);
+    if (!invert(V, Np, Vinv)) return false;
+    vandermonde(p, rq.data(), sq.data(), Nq, Q, Qr, Qs);
+    out.Vq = matmul(Q, Vinv, Nq, Np, Np);
+    out.Vqr = matmul(Qr, Vinv, Nq, Np, Np);
+    out.Vqs = matmul(Qs, Vinv, Nq, Np, Np);
+    // Sr = M^-1 Vqr^T diag(w), Ss likewise (M^-1 = V V^T)
+    std::vector<double> Vt(static_cast<size_t>(Np) * Np), TrW(static_cast<size_t>(Np) * Nq), TsW(TrW.size());
+    for (int i = 0; i < Np; ++i)
+        for (int j = 0; j < Np; ++j) Vt[j * Np + i] = V[i * Np + j];
+    std::vector<double> Minv = matmul(V, Vt, Np, Np, Np);
+    for (int i = 0; i < Np; ++i)
+        for (int q = 0; q < Nq; ++q) {
+            TrW[i * Nq + q] = out.Vqr[q * Np + i] * out.wq[q];
+            TsW[i * Nq + q] = out.Vqs[q * Np + i] * out.wq[q];
+        }
+    out.Sr = matmul(Minv, TrW, Np, Np, Nq);
+    out.Ss = matmul(Minv, TsW, Np, Np, Nq);
+    return true;
+}
 
 bool build_reference_operators(int p, RefOps &o)
 {
@@ -196,26 +301,8 @@ bool build_reference_operators(int p, RefOps &o)
         }
 
     // Vandermonde and its derivatives
-    std::vector<double> V(Np * Np), Vr(Np * Np), Vs(Np * Np);
-    for (int nd = 0; nd < Np; ++nd) {
-        double r = o.r[nd], s = o.s[nd];
-        double a = (std::fabs(1.0 - s) > 1e-14) ? 2.0 * (1.0 + r) / (1.0 - s) - 1.0 : -1.0;
-        double b = s, om = 1.0 - b;
-        int col = 0;
-        for (int i = 0; i <= p; ++i)
-            for (int j = 0; j <= p - i; ++j, ++col) {
-                double fa = jacobi(a, 0, 0, i), dfa = jacobi_d(a, 0, 0, i);
-                double gb = jacobi(b, 2.0 * i + 1.0, 0, j), dgb = jacobi_d(b, 2.0 * i + 1.0, 0, j);
-                double omi = std::pow(om, i), omi1 = (i > 0) ? std::pow(om, i - 1) : 0.0;
-                V[nd * Np + col] = std::sqrt(2.0) * fa * gb * omi;
-                // d/dr: da/dr = 2/(1-b)
-                Vr[nd * Np + col] = (i > 0) ? 2.0 * std::sqrt(2.0) * dfa * gb * omi1 : 0.0;
-                // d/ds: da/ds = (1+a)/(1-b), plus the b-dependence of gb (1-b)^i
-                double t1 = (i > 0) ? dfa * (1.0 + a) * gb * omi1 : 0.0;
-                double t2 = fa * (dgb * omi - ((i > 0) ? i * gb * omi1 : 0.0));
-                Vs[nd * Np + col] = std::sqrt(2.0) * (t1 + t2);
-            }
-    }
+    std::vector<double> V, Vr, Vs;
+    vandermonde(p, o.r.data(), o.s.data(), Np, V, Vr, Vs);
     std::vector<double> Vinv;
     if (!invert(V, Np, Vinv)) return false;
     o.Dr = matmul(Vr, Vinv, Np, Np, Np);

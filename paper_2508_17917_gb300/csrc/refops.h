@@ -19,4 +19,20 @@ struct RefOps {
 // Builds every operator for degree p (1..6). Returns false on bad p.
 bool build_reference_operators(int p, RefOps &out);
 
+// Over-integration of the volume term (Sec. 2.2, weak matrices): a
+// collapsed-coordinate Gauss rule exact to total degree `deg` (N = floor(deg/2)
+// + 1 Gauss-Legendre points in a times N Gauss-Jacobi (1, 0) points in b),
+// the nodal basis and its (r, s) derivatives at its points, and the weak
+// volume operators Sr = M^-1 Vqr^T W, Ss = M^-1 Vqs^T W.
+struct OverintOps {
+    int deg = 0, Nq = 0;
+    std::vector<double> wq;              // Nq
+    std::vector<double> Vq, Vqr, Vqs;    // Nq*Np
+    std::vector<double> Sr, Ss;          // Np*Nq
+};
+bool build_overint_operators(const RefOps &o, int deg, OverintOps &out);
+
+// The rule degree the library uses for degree p: min(3p, 15), at most 64 points.
+int overint_degree(int p);
+
 }  // namespace dg

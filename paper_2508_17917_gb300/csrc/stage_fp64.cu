@@ -5,11 +5,11 @@
 namespace dg {
 namespace {
 
-template <int P, typename real, bool TH>
+template <int P, typename real, bool TH, bool OI = false>
 cudaError_t shape_p(long long K, LaunchShape &ls)
 {
-    using L = Smem<P, real, TH>;
-    auto kern = stage_kernel<P, real, TH>;
+    using L = Smem<P, real, TH, OI>;
+    auto kern = stage_kernel<P, real, TH, OI>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(L::bytes));
     if (e != cudaSuccess) return e;
@@ -26,13 +26,16 @@ cudaError_t shape_p(long long K, LaunchShape &ls)
     ls.smem = L::bytes;
     ls.elems_per_tile = Shape<P>::E;
     ls.theta = TH;
+    ls.overint = OI;
     return cudaSuccess;
 }
 
 template <int P, typename real>
 cudaError_t launch_p(const LaunchShape &ls, const StageParams &sp, const Phys<real> &ph, cudaStream_t st)
 {
-    if (ls.theta)
+    if (ls.overint)
+        stage_kernel<P, real, false, true><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
+    else if (ls.theta)
         stage_kernel<P, real, true><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
     else
         stage_kernel<P, real, false><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
@@ -52,9 +55,10 @@ cudaError_t launch_p(const LaunchShape &ls, const StageParams &sp, const Phys<re
     default: return cudaErrorInvalidValue;        \
     }
 
-cudaError_t stage_shape_fp64(int p, long long K, bool theta, LaunchShape &out)
+cudaError_t stage_shape_fp64(int p, long long K, bool theta, LaunchShape &out, bool overint)
 {
-#define C_(P) (theta ? shape_p<P, double, true>(K, out) : shape_p<P, double, false>(K, out))
+#define C_(P) (overint ? shape_p<P, double, false, true>(K, out) \
+                       : (theta ? shape_p<P, double, true>(K, out) : shape_p<P, double, false>(K, out)))
     DG_SWITCH_P(p, C_)
 #undef C_
 }
