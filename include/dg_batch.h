@@ -82,6 +82,13 @@ int64_t dg_batch_kernel_launches(const dg_batch *b);
  * Errors: DG_EINVAL. */
 dg_status dg_batch_set_stage_variant(dg_batch *b, int variant);
 
+/* Fused steps for the batch: on != 0 replaces the five stage launches of
+ * each degree group by one cooperative launch with grid barriers between the
+ * stages (as dg_set_fused_steps; every barrier wait is bounded and a wait
+ * that gives up makes dg_batch_run return DG_ETIMEOUT).  Drops captured
+ * graphs.  Errors: DG_EINVAL, DG_ECUDA. */
+dg_status dg_batch_set_fused_steps(dg_batch *b, int on);
+
 /* The tile shape the group of case i uses (1 or 2); 0 for a bad argument. */
 int dg_batch_stage_variant(const dg_batch *b, int i);
 

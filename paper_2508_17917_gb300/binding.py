@@ -22,7 +22,7 @@ __all__ = ["DG_OK", "DG_PRECISION_FP64", "DG_PRECISION_MIXED", "DG_SOURCE_NONE",
            "dg_barrier_status", "dg_set_overintegration", "dg_overint_degree",
            "DgCase", "dg_batch_create", "dg_batch_destroy", "dg_batch_last_error",
            "dg_batch_kernel_launches", "dg_batch_stream", "dg_batch_case_size",
-           "dg_batch_set_stage_variant", "dg_batch_stage_variant", "dg_batch_node_coords",
+           "dg_batch_set_stage_variant", "dg_batch_stage_variant", "dg_batch_set_fused_steps", "dg_batch_node_coords",
            "dg_batch_set_state", "dg_batch_get_state", "dg_batch_run", "dg_batch_reset_history",
            "dg_batch_rigid", "BatchSolver",
            "dg_mlp_create", "dg_mlp_destroy", "dg_mlp_last_error", "dg_mlp_param_count",
@@ -99,6 +99,7 @@ EXPORTED = {
     "dg_batch_stream": (C.c_void_p, [C.c_void_p]),
     "dg_batch_set_stage_variant": (C.c_int, [C.c_void_p, C.c_int]),
     "dg_batch_stage_variant": (C.c_int, [C.c_void_p, C.c_int]),
+    "dg_batch_set_fused_steps": (C.c_int, [C.c_void_p, C.c_int]),
     "dg_batch_case_size": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
     "dg_batch_node_coords": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp]),
     "dg_batch_set_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
@@ -425,6 +426,10 @@ def dg_batch_stage_variant(b, i):
     return int(lib().dg_batch_stage_variant(b, int(i)))
 
 
+def dg_batch_set_fused_steps(b, on):
+    _bcheck(lib().dg_batch_set_fused_steps(b, int(bool(on))), b)
+
+
 def dg_batch_stream(b):
     """Integer handle of the batch's cudaStream_t."""
     return int(lib().dg_batch_stream(b) or 0)
@@ -545,6 +550,10 @@ class BatchSolver:
 
     def variant(self, i):
         return dg_batch_stage_variant(self.b, i)
+
+    def set_fused(self, on):
+        """One cooperative launch per degree group and step."""
+        dg_batch_set_fused_steps(self.b, on)
 
 
 # ---- include/dg_mlp.h -----------------------------------------------------

@@ -39,6 +39,9 @@ struct Group {
     long long ntiles = 0, ntiles2 = 0;
     dg::LaunchShape shape, shape2;   // one / two nodes per thread
     int variant = 1;
+    dg::LaunchShape fshape;          // fused steps: cooperative launch of the chosen shape
+    int fshape_variant = 0;
+    DevBuf<unsigned> bar;            // fused steps: barrier counters of this group
     DevBuf<double> K0a, K0b, K1, geo64, Dr64, Ds64, wface, fxy;
     DevBuf<float> geo32, ops32, P0a, P0b;
     DevBuf<float4> S0a, S0b;
@@ -74,6 +77,9 @@ struct dg_batch {
     bool forces_stale = true;
     int variant_req = 0;             // 0: tuned per degree group on the first run; 1, 2: forced
     bool tuned = false;
+    bool fused = false;              // one cooperative launch per degree group and step
+    DevBuf<int> bar_err;
+    unsigned bar_limit = 1u << 24;
     // graphs: [0] starts from buffers a, [1] from buffers b
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t graph_launches = 0;
@@ -188,7 +194,7 @@ dg_status enqueue_step(dg_batch *b, double cfl, double *hist, int rows)
     B_CUDA(b, dg::launch_batch_dt(b->lam.ptr, b->seg.ptr, b->dcases.ptr, n, cfl, b->stream));
     B_CUDA(b, dg::launch_batch_newmark(b->dcases.ptr, n, b->stream));
     b->launches += 2;
-    for (int s = 0; s < 5; ++s) {
+    for (int s = 0; s < (b->fused ? 1 : 5); ++s) {
         for (auto &g : b->groups) {
             dg::StageParams sp{};
             const bool a = b->cur_is_a;
@@ -211,7 +217,24 @@ dg_status enqueue_step(dg_batch *b, double cfl, double *hist, int rows)
             sp.mode = dg::STAGE_UPDATE;
             sp.first_stage = (s == 0) ? 1 : 0;
             sp.cases = b->dcases.ptr;
-            if (g.variant == 2) {
+            if (b->fused) {
+                // the five stages in one cooperative launch (grid barriers between stages)
+                sp.tiles = (g.variant == 2) ? g.tiles2.ptr : g.tiles.ptr;
+                sp.ntiles = (g.variant == 2) ? g.ntiles2 : g.ntiles;
+                if (g.fshape_variant != g.variant) {
+                    B_CUDA(b, dg::stage_shape_mixed_fused(g.p, g.variant, true, sp.ntiles, g.fshape));
+                    g.fshape_variant = g.variant;
+                }
+                for (int i = 0; i < 5; ++i) {
+                    sp.A5[i] = dg::kRkA[i];
+                    sp.B5[i] = dg::kRkB[i];
+                }
+                sp.bar = g.bar.ptr;
+                sp.bar_err = b->bar_err.ptr;
+                sp.bar_limit = b->bar_limit;
+                B_CUDA(b, cudaMemsetAsync(g.bar.ptr, 0, 2 * sizeof(unsigned), b->stream));
+                B_CUDA(b, dg::launch_stage_mixed_fused(g.p, true, g.fshape, sp, ph32, b->stream));
+            } else if (g.variant == 2) {
                 sp.tiles = g.tiles2.ptr;
                 sp.ntiles = g.ntiles2;
                 B_CUDA(b, dg::launch_stage_mixed2(g.p, true, g.shape2, sp, ph32, b->stream));
@@ -519,6 +542,24 @@ dg_status dg_batch_set_stage_variant(dg_batch *b, int variant)
     return DG_OK;
 }
 
+dg_status dg_batch_set_fused_steps(dg_batch *b, int on)
+{
+    if (!b) return DG_EINVAL;
+    b->err.clear();
+    if (on && !b->bar_err.ptr) {
+        B_CUDA(b, b->bar_err.alloc(1));
+        B_CUDA(b, cudaMemset(b->bar_err.ptr, 0, sizeof(int)));
+        for (auto &g : b->groups) {
+            B_CUDA(b, g.bar.alloc(2));
+            B_CUDA(b, cudaMemset(g.bar.ptr, 0, 2 * sizeof(unsigned)));
+        }
+    }
+    b->fused = on != 0;
+    b->drop_graphs();
+    b->graph_cfl = 0.0;
+    return DG_OK;
+}
+
 int dg_batch_stage_variant(const dg_batch *b, int i)
 {
     if (!b || i < 0 || i >= static_cast<int>(b->cases.size())) return 0;
@@ -644,7 +685,7 @@ dg_status dg_batch_run(dg_batch *b, double cfl, int nsteps, int use_graph, doubl
                 if (e != cudaSuccess) return bcuda(b, e, "cudaGraphInstantiate");
                 // kernels per replay: dt per group, dt reduce, Newmark, 5 stages per group,
                 // forces per group with walls, force sum, record
-                int64_t per = static_cast<int64_t>(b->groups.size()) * 6 + 3 + (hist ? 1 : 0);
+                int64_t per = static_cast<int64_t>(b->groups.size()) * (b->fused ? 2 : 6) + 3 + (hist ? 1 : 0);
                 for (auto &g : b->groups) per += (g.nwall > 0) ? 1 : 0;
                 b->graph_launches = per;
             }
@@ -659,6 +700,14 @@ dg_status dg_batch_run(dg_batch *b, double cfl, int nsteps, int use_graph, doubl
         }
     }
     B_CUDA(b, cudaStreamSynchronize(b->stream));
+    if (b->fused) {
+        int e = 0;
+        B_CUDA(b, cudaMemcpy(&e, b->bar_err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) {
+            B_CUDA(b, cudaMemset(b->bar_err.ptr, 0, sizeof(int)));
+            return bfail(b, DG_ETIMEOUT, "a grid barrier of a fused step gave up waiting; the states are not valid");
+        }
+    }
     std::vector<dg::BatchCase> h(b->cases.size());
     B_CUDA(b, cudaMemcpy(h.data(), b->dcases.ptr, h.size() * sizeof(dg::BatchCase), cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < h.size(); ++i)

@@ -86,7 +86,9 @@ def rel_err(got, ref):
     return np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
 
 
-RUNS = [("graph", 1), ("plain", 1), ("graph", 2), ("graph", 0)]     # (launch mode, tile shape; 0 = tuned)
+# (launch mode, tile shape; 0 = tuned); "fused": one cooperative launch per
+# degree group and step, replayed from the graph
+RUNS = [("graph", 1), ("plain", 1), ("graph", 2), ("graph", 0), ("fused", 1), ("fused", 2)]
 
 
 @pytest.fixture(scope="module")
@@ -98,6 +100,7 @@ def small_run(dg):
     for mode, variant in RUNS:
         b = dg.BatchSolver(cases, **FAR)
         b.set_variant(variant)
+        b.set_fused(mode == "fused")
         states = []
         for i in range(len(cases)):
             x, y = b.node_coords(i)
@@ -107,7 +110,7 @@ def small_run(dg):
         hist = torch.zeros((nsteps, len(cases), 8), dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()          # the batch runs on its own stream
         b.reset_history()
-        b.run(0.3, nsteps, use_graph=(mode == "graph"), hist=hist)
+        b.run(0.3, nsteps, use_graph=(mode != "plain"), hist=hist)
         res[(mode, variant)] = (hist.cpu().numpy(), [b.get_state(i) for i in range(len(cases))], b.rigid(),
                                 b.launches, [b.variant(i) for i in range(len(cases))])
     return cases, states, nsteps, res
@@ -122,7 +125,7 @@ def test_batch_graph_replay_is_bit_identical(small_run):
     assert np.array_equal(rg, rp)
 
 
-@pytest.mark.parametrize("run", [("graph", 1), ("graph", 2), ("graph", 0)])
+@pytest.mark.parametrize("run", [("graph", 1), ("graph", 2), ("graph", 0), ("fused", 2)])
 @pytest.mark.parametrize("i", range(len(SMALL)))
 def test_batch_case_matches_oracle_loop(small_run, i, run):
     cases, states, nsteps, res = small_run
@@ -144,14 +147,27 @@ def test_batch_case_matches_oracle_loop(small_run, i, run):
     assert rigid[i, 9] == 0
 
 
+@pytest.mark.parametrize("variant", [1, 2])
+def test_batch_fused_matches_five_launches(small_run, variant):
+    """Same result as the five stage launches up to the last bit of a
+    separately compiled kernel (1e-9 of the largest value)."""
+    cases, states, nsteps, res = small_run
+    hg, Ug, _, _, _ = res[("graph", variant)]
+    hf, Uf, _, _, _ = res[("fused", variant)]
+    for a, b in zip(Ug, Uf):
+        assert np.abs(a - b).max() <= 1e-9 * np.abs(a).max()
+    assert np.abs(hf - hg).max() <= 1e-9 * np.abs(hg).max()
+
+
 def test_batch_launch_count(small_run):
     cases, states, nsteps, res = small_run
     groups = len({c["p"] for c in cases})
     # set_state per case, initial forces (groups + 1), then per step: dt per group,
     # dt reduce, Newmark, 5 stages per group, forces per group, force sum, record;
     # the tuned run adds five residual-only launches per shape and group
-    per_step = 6 * groups + 3 + groups + 1
     for run in RUNS:
+        stage = groups if run[0] == "fused" else 5 * groups
+        per_step = groups + 2 + stage + groups + 1 + 1
         launches = res[run][3]
         tune = 10 * groups if run[1] == 0 else 0
         assert launches == len(cases) + (groups + 1) + tune + nsteps * per_step, (run, launches)
