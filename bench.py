@@ -407,6 +407,16 @@ def run_batch(dg, torch, dg_inputs, to_kcn, np, peak, steps):
     e1.synchronize()
     ms = e0.elapsed_time(e1)
     ok = not np.any(b.rigid()[:, 9])
+    launches = int(b.launches - n0)
+    # the same with one cooperative launch per degree group and step
+    b.set_fused(True)
+    b.run(0.3, 3, use_graph=True)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(ext)
+    b.run(0.3, steps, use_graph=True)
+    f1.record(ext)
+    f1.synchronize()
+    ms_fused = f0.elapsed_time(f1)
     ach = bytes_step * steps / (ms * 1e-3) / 1e9
     out = {"workload": "64 VIV cases (seeded O-grids, 10k-60k triangles each, 2.25 M in total, p = 3..6 "
                        "cycling, U* in [3, 8], Re in [100, 150], m* = 10, zeta = 1e-3, M = 0.2): dt, "
@@ -414,7 +424,8 @@ def run_batch(dg, torch, dg_inputs, to_kcn, np, peak, steps):
                        "per step",
            "cases": len(cases), "dofs": dof, "steps": steps, "value": dof * 5 * steps / (ms * 1e-3),
            "unit": UNIT, "ms_per_step": ms / steps, "roofline_achieved_gbs": ach, "roofline_frac": ach / peak,
-           "gpu_launches": int(b.launches - n0), "finite": bool(ok)}
+           "gpu_launches": launches, "finite": bool(ok),
+           "fused_steps": {"ms_per_step": ms_fused / steps, "value": dof * 5 * steps / (ms_fused * 1e-3)}}
     del b
     return out
 
