@@ -157,6 +157,24 @@ def dist_env():
     return ws, rank, local
 
 
+def slowest_rank_ms(local_ms, device="cpu"):
+    """Max over the ranks of a timed region (ms); the local value when the
+    job is not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(local_ms)
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank, ws, total_ms):
+    """Whole-job throughput of ws independent replicas: the units all ranks
+    processed over the slowest rank's time."""
+    return ws * units_per_rank / (total_ms * 1e-3)
+
+
 def vortex_problem(n):
     import dg_inputs
     return dg_inputs.periodic_square(n)
@@ -224,14 +242,11 @@ def run_ours(args):
     with ClockSampler(dev) as clk:
         times, launches = timed_steps(dg, torch, s, dt, args.steps, args.warmup, flush, stream)
     torch.cuda.synchronize()
-    total_ms = sum(times)
+    total_ms = slowest_rank_ms(sum(times), device="cuda")
     if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
         torch.distributed.barrier()
     ok = s.check_finite()
-    value = ws * dof * 5 * args.steps / (total_ms * 1e-3)
+    value = replica_value(dof * 5 * args.steps, ws, total_ms)
     ms_step = total_ms / args.steps
     stage_ms = ms_step / 5.0
     peak, peak_kind = measured_peaks()
