@@ -126,8 +126,8 @@ struct MixedLayout {
     static constexpr size_t oD = 0;                                           // float2 Np*Np (Dr, Ds)
     static constexpr size_t oL = oD + al(sizeof(float2) * Np * Np);           // float Np*NF
     static constexpr size_t oFm = oL + al(sizeof(float) * Np * NF);           // int NF
-    static constexpr size_t oConn = oFm + al(sizeof(int) * NF);               // int4 E
-    static constexpr size_t oGeo = oConn + al(sizeof(int4) * E);              // float E*16
+    static constexpr size_t oConn = oFm + al(sizeof(int) * NF);               // int4 2E (two tiles)
+    static constexpr size_t oGeo = oConn + al(sizeof(int4) * E * 2);          // float E*16
     static constexpr size_t oNGeo = oGeo + al(sizeof(float) * E * 16);        // float E*3*16
     static constexpr size_t oU = oNGeo + al(sizeof(float) * E * 3 * 16);      // float4 E*Np
     static constexpr size_t oN = oU + al(sizeof(float4) * E * Np);            // float4 E*3*Np

@@ -89,58 +89,91 @@ stage_mixed2_kernel(StageParams sp, Phys<float> ph)
         fused_stage(sp, stg);
         need_k1 = update && stg > 0;
     }
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        long long k0 = tile * E;
-        int ne = static_cast<int>((K - k0) < E ? (K - k0) : E);
+    // Software pipeline over the block's tiles.  Group A (FP32 state, pressure
+    // and geometry of the tile and its neighbours) of tile t + 1 is copied
+    // while tile t runs its update (P4), which reads none of those buffers;
+    // group B (the FP64 registers K0, K1) of tile t is copied while tile t
+    // runs P2 and P3.  The connectivity is double-buffered.
+    auto tile_at = [&](long long t, long long &k0t, int &net) {
         if constexpr (BATCH) {
-            const int4 td = sp.tiles[tile];
-            k0 = td.x;
-            ne = td.y;
-            const BatchCase &cs = sp.cases[td.z];
+            const int4 td = sp.tiles[t];
+            k0t = td.x;
+            net = td.y;
+        } else {
+            k0t = t * E;
+            net = static_cast<int>((K - k0t) < E ? (K - k0t) : E);
+        }
+    };
+    auto issue_a = [&](long long k0t, int net, const int4 *cnt) {
+        const char *gU = reinterpret_cast<const char *>(sp.Sin + k0t * Np);
+        for (int c = tid; c < net * Np; c += NT) cp_async16(sbase + L::oU + 16u * c, gU + 16 * c);
+        const char *gP = reinterpret_cast<const char *>(sp.Pin + k0t * NpP);
+        for (int c = tid; c < net * (NpP / 4); c += NT) cp_async16(sbase + L::oPo + 16u * c, gP + 16 * c);
+        const char *gG = reinterpret_cast<const char *>(geo + k0t * 16);
+        for (int c = tid; c < net * 4; c += NT) cp_async16(sbase + L::oGeo + 16u * c, gG + 16 * c);
+        for (int c = tid; c < net * 3 * Np; c += NT) {
+            const int seg = c / Np, j = c - (c / Np) * Np;
+            const int4 cn = cnt[seg / 3];
+            const int f = seg - 3 * (seg / 3);
+            const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
+            cp_async16(sbase + L::oN + 16u * c, sp.Sin + nb * Np + j);
+        }
+        for (int c = tid; c < net * 3 * (NpP / 4); c += NT) {
+            const int seg = c / (NpP / 4), qq = c - (c / (NpP / 4)) * (NpP / 4);
+            const int4 cn = cnt[seg / 3];
+            const int f = seg - 3 * (seg / 3);
+            const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
+            cp_async16(sbase + L::oPn + 16u * c, sp.Pin + nb * NpP + 4 * qq);
+        }
+        for (int c = tid; c < net * 3 * 4; c += NT) {
+            const int seg = c >> 2, qq = c & 3;
+            const int4 cn = cnt[seg / 3];
+            const int f = seg - 3 * (seg / 3);
+            const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
+            cp_async16(sbase + L::oNGeo + 16u * c, geo + nb * 16 + 4 * qq);
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+    };
+    long long tile = blockIdx.x;
+    int buf = 0;
+    if (tile < ntiles) {
+        long long k0f;
+        int nef;
+        tile_at(tile, k0f, nef);
+        if (tid < nef) sConn[tid] = sp.conn[k0f + tid];
+        __syncthreads();
+        issue_a(k0f, nef, sConn);
+    }
+    for (; tile < ntiles; tile += gridDim.x, buf ^= 1) {
+        long long k0;
+        int ne;
+        tile_at(tile, k0, ne);
+        if constexpr (BATCH) {
+            const BatchCase &cs = sp.cases[sp.tiles[tile].z];
             ph.mu = static_cast<float>(cs.mu);
             ph.vw2 = static_cast<float>(cs.vb);
             dtr = static_cast<float>(cs.dt);
         }
-        // ---- P1a: connectivity of the tile
-        if (tid < ne) sConn[tid] = sp.conn[k0 + tid];
-        __syncthreads();
-        // ---- P1b: asynchronous 16-byte copies of everything the tile reads
+        const int4 *cnb = sConn + buf * E;
+        int4 *cnx = sConn + (buf ^ 1) * E;
+        const long long tn = tile + gridDim.x;
+        const bool has_next = tn < ntiles;
+        long long k0n = 0;
+        int nen = 0;
+        if (has_next) {
+            tile_at(tn, k0n, nen);
+            if (tid < nen) cnx[tid] = sp.conn[k0n + tid];
+        }
+        // ---- P1: group B of this tile; wait for group A
         {
-            const char *gU = reinterpret_cast<const char *>(sp.Sin + k0 * Np);
-            for (int c = tid; c < ne * Np; c += NT) cp_async16(sbase + L::oU + 16u * c, gU + 16 * c);
-            const char *gP = reinterpret_cast<const char *>(sp.Pin + k0 * NpP);
-            for (int c = tid; c < ne * (NpP / 4); c += NT) cp_async16(sbase + L::oPo + 16u * c, gP + 16 * c);
             const char *gR = reinterpret_cast<const char *>(sp.K0in + k0 * 4 * Np);
             for (int c = tid; c < ne * 2 * Np; c += NT) cp_async16(sbase + L::oRaw + 16u * c, gR + 16 * c);
             if (need_k1) {
                 const char *gK = reinterpret_cast<const char *>(sp.K1 + k0 * 4 * Np);
                 for (int c = tid; c < ne * 2 * Np; c += NT) cp_async16(sbase + L::oK1 + 16u * c, gK + 16 * c);
             }
-            const char *gG = reinterpret_cast<const char *>(geo + k0 * 16);
-            for (int c = tid; c < ne * 4; c += NT) cp_async16(sbase + L::oGeo + 16u * c, gG + 16 * c);
-            for (int c = tid; c < ne * 3 * Np; c += NT) {
-                const int seg = c / Np, j = c - (c / Np) * Np;
-                const int4 cn = sConn[seg / 3];
-                const int f = seg - 3 * (seg / 3);
-                const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
-                cp_async16(sbase + L::oN + 16u * c, sp.Sin + nb * Np + j);
-            }
-            for (int c = tid; c < ne * 3 * (NpP / 4); c += NT) {
-                const int seg = c / (NpP / 4), qq = c - (c / (NpP / 4)) * (NpP / 4);
-                const int4 cn = sConn[seg / 3];
-                const int f = seg - 3 * (seg / 3);
-                const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
-                cp_async16(sbase + L::oPn + 16u * c, sp.Pin + nb * NpP + 4 * qq);
-            }
-            for (int c = tid; c < ne * 3 * 4; c += NT) {
-                const int seg = c >> 2, qq = c & 3;
-                const int4 cn = sConn[seg / 3];
-                const int f = seg - 3 * (seg / 3);
-                const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
-                cp_async16(sbase + L::oNGeo + 16u * c, geo + nb * 16 + 4 * qq);
-            }
             asm volatile("cp.async.commit_group;\n" ::);
-            asm volatile("cp.async.wait_group 0;\n" ::);
+            asm volatile("cp.async.wait_group 1;\n" ::);
         }
         __syncthreads();
 
@@ -187,7 +220,7 @@ stage_mixed2_kernel(StageParams sp, Phys<float> ph)
         }
         int btype = 0, f2 = 0;
         if (live && fslot) {
-            const int4 cn = sConn[el];
+            const int4 cn = cnb[el];
             f2 = (cn.w >> (2 * ff)) & 3;
             btype = (cn.w >> (8 + 2 * ff)) & 3;
             const float *g = sGeo + el * 16;
@@ -326,7 +359,9 @@ stage_mixed2_kernel(StageParams sp, Phys<float> ph)
                 sDH[el * NF + ff * Nfp + fi] = make_float4(fsc * dH[0], fsc * dH[1], fsc * dH[2], fsc * dH[3]);
             }
         }
+        asm volatile("cp.async.wait_group 0;\n" ::);
         __syncthreads();
+        if (has_next) issue_a(k0n, nen, cnx);
 
         // ---- P4: lift, the stage update and the FP32 copy of the new state
         if (live && vslot) {
@@ -375,6 +410,7 @@ stage_mixed2_kernel(StageParams sp, Phys<float> ph)
                 }
             }
         }
+        __syncthreads();
     }
     }  // stages
 }
