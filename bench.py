@@ -60,16 +60,27 @@ def algorithmic_bytes_per_step(K, geo_bytes):
     return state + 5 * K * geo_bytes
 
 
-def kernel_hash():
+# the sources each mixed stage-kernel shape is compiled from
+KERNEL_FILES = {
+    1: ("dg_stage.cuh", "dg_stage_mixed.cuh", "dg_device.cuh", "stage_mixed.cu"),
+    2: ("dg_stage.cuh", "dg_stage_mixed.cuh", "dg_stage_mixed2.cuh", "dg_device.cuh", "stage_mixed.cu"),
+    3: ("dg_stage.cuh", "dg_stage_mixed.cuh", "dg_stage_tc.cuh", "dg_device.cuh", "stage_tc.cu"),
+}
+
+
+def kernel_hash(variant=2):
     h = hashlib.sha256()
-    for f in ("dg_stage.cuh", "dg_stage_mixed.cuh", "dg_stage_mixed2.cuh", "dg_device.cuh", "stage_mixed.cu"):
+    for f in KERNEL_FILES[variant]:
         with open(os.path.join(ROOT, "paper_2508_17917_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-PROFILE_OF_VARIANT = {1: "stage_kernel_mixed_p4.md", 2: "stage_kernel_mixed2_p4.md"}
-KERNEL_OF_VARIANT = {1: "dg::stage_mixed_kernel<4, false>", 2: "dg::stage_mixed2_kernel<4, false>"}
+PROFILE_OF_VARIANT = {1: "stage_kernel_mixed_p4.md", 2: "stage_kernel_mixed2_p4.md", 3: "stage_kernel_tc_p4.md"}
+KERNEL_OF_VARIANT = {1: "dg::stage_mixed_kernel<4, false>", 2: "dg::stage_mixed2_kernel<4, false>",
+                     3: "dg::stage_tc_kernel<4, false, false>"}
+SHAPE_OF_VARIANT = {1: "one node per thread", 2: "two nodes per thread",
+                    3: "one warp per two elements, tensor-core contractions"}
 
 
 def recorded_traffic(variant):
@@ -80,7 +91,7 @@ def recorded_traffic(variant):
         return None
     text = open(path).read()
     m = re.search(r"dram_bytes_per_dof_stage:\s*([0-9.eE+-]+)\s*\(kernel_hash\s+([0-9a-f]+)\)", text)
-    if not m or m.group(2) != kernel_hash():
+    if not m or variant not in KERNEL_FILES or m.group(2) != kernel_hash(variant):
         return None
     return float(m.group(1))
 
@@ -259,7 +270,7 @@ def run_ours(args):
                 "traffic": (traffic * dof * 5 / 5.0) if traffic is not None else None,
                 "algorithmic_bytes_per_launch": bytes_step / 5.0,
                 "kernel": KERNEL_OF_VARIANT.get(variant, str(variant)),
-                "tile_shape": "two nodes per thread" if variant == 2 else "one node per thread"}
+                "tile_shape": SHAPE_OF_VARIANT.get(variant, str(variant))}
 
     # --- FP64 path, same workload
     s64, U64, dt64 = solvers["fp64"]
@@ -275,6 +286,18 @@ def run_ours(args):
     fused = {"workload": "same mesh, state and kernel; five stages per cooperative launch with grid barriers",
              "value": dof * 5 * len(tf) / (sum(tf) * 1e-3), "unit": UNIT, "ms_per_step": sum(tf) / len(tf),
              "launches_per_step": lf / len(tf)}
+
+    # --- the tensor-core kernel forced (the tuner keeps the faster shape)
+    stc = dg.Solver(mesh, P, "mixed", stream=sh, mu=1e-3)
+    stc.set_variant(3)
+    stc.set_state(U0)
+    ttc, _ = timed_steps(dg, torch, stc, dt, max(5, args.steps // 10), 5, flush, stream)
+    vtc = dof * 5 * len(ttc) / (sum(ttc) * 1e-3)
+    tc = {"workload": "same mesh, state and time step; Dr / Ds / LIFT products as mma.sync TF32 "
+                      "(three products of split operands), one warp per two elements",
+          "value": vtc, "unit": UNIT, "ms_per_step": sum(ttc) / len(ttc), "tc_over_tuned": vtc / (value / ws),
+          "kernel": KERNEL_OF_VARIANT[3], "tuned_variant": variant}
+    del stc
 
     # --- SIP variant (theta = 1, Eq. ip_flux), mixed path, same workload
     ssip = dg.Solver(mesh, P, "mixed", stream=sh, mu=1e-3, theta=1.0, C1=0.05)
@@ -373,6 +396,7 @@ def run_ours(args):
             "large_mesh": large,
             "fused_steps": fused,
             "sip_path": sip,
+            "tensor_core_path": tc,
             "p6_large": p6,
             "batch_viv": batch,
             "mlp": mlp_line,
@@ -546,12 +570,15 @@ def run_profile(args):
     import dg_inputs
     import paper_2508_17917_gb300 as dg
     from dg_inputs.states import to_kcn
-    prec, n, theta = {"mixed512": ("mixed", 512, 0.0), "mixed128": ("mixed", 128, 0.0),
-                      "fp64_128": ("fp64", 128, 0.0), "sip128": ("mixed", 128, 1.0)}[args.profile]
+    prec, n, theta, var = {"mixed512": ("mixed", 512, 0.0, 0), "mixed128": ("mixed", 128, 0.0, 0),
+                           "fp64_128": ("fp64", 128, 0.0, 0), "sip128": ("mixed", 128, 1.0, 0),
+                           "tc512": ("mixed", 512, 0.0, 3)}[args.profile]
     torch.cuda.set_device(0)
     mesh = vortex_problem(n)
     s = dg.Solver(mesh, P, prec, stream=torch.cuda.current_stream().cuda_stream, mu=1e-3,
                   theta=theta, C1=0.05 if theta else 0.01)
+    if var:
+        s.set_variant(var)
     x, y = s.node_coords()
     s.set_state(dg_inputs.perturb(to_kcn(dg_inputs.isentropic_vortex(x, y)), seed=0))
     dt = s.dt(0.3)
@@ -571,7 +598,7 @@ def main():
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--profile", choices=["mixed512", "mixed128", "fp64_128", "sip128"], default=None)
+    ap.add_argument("--profile", choices=["mixed512", "mixed128", "fp64_128", "sip128", "tc512"], default=None)
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

@@ -104,13 +104,16 @@ dg_status dg_set_mesh(dg_ctx *ctx, int64_t Nv, const double *vx, const double *v
 /* Tile shape of the mixed-precision IIP stage kernel (no counterpart in the
  * paper): 1 = one volume node and one face node per thread (256 threads),
  * 2 = two volume nodes and two face nodes of one face per thread (128
- * threads), 0 = time both (residual-only launches on the current state) at
- * the first time step after a mesh upload and keep the faster (the default).  Other paths have one kernel and
- * accept 0 and 1.  Errors: DG_EINVAL (variant outside 0..2),
- * DG_EUNSUPPORTED (2 on the FP64 or theta != 0 path). */
+ * threads), 3 = one warp per tile of 4 elements with the Dr / Ds / LIFT
+ * products on the tensor cores (mma.sync TF32, three products of split
+ * operands, about 2^-21 relative; p <= 4 only), 0 = time every available
+ * shape (residual-only launches on the current state) at the first time step
+ * after a mesh upload and keep the fastest (the default).  Other paths have
+ * one kernel and accept 0 and 1.  Errors: DG_EINVAL (variant outside 0..3),
+ * DG_EUNSUPPORTED (2 or 3 on the FP64 or theta != 0 path, 3 with p > 4). */
 dg_status dg_set_stage_variant(dg_ctx *ctx, int variant);
 
-/* The tile shape in use: 1 or 2 (the single-node kernel until tuned). */
+/* The tile shape in use: 1, 2 or 3 (the single-node kernel until tuned). */
 int dg_stage_variant(const dg_ctx *ctx);
 
 /* Over-integration of the volume term (Sec. 2.2, weak matrices: the paper

@@ -375,7 +375,8 @@ class Solver:
         return dg_kernel_launches(self.ctx)
 
     def set_variant(self, v):
-        """Stage-kernel tile shape: 0 = tuned on first step, 1 or 2 forced."""
+        """Stage-kernel tile shape: 0 = tuned on first step, 1, 2 or 3 forced
+        (3: tensor-core warp tiles, p <= 4)."""
         dg_set_stage_variant(self.ctx, v)
 
     @property

@@ -21,7 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 # per-file extra flags: the mixed-precision kernels use fast FP32 division,
 # square root and flush-to-zero (FP64 instructions are not affected)
-FILE_FLAGS = {"stage_mixed.cu": ["--use_fast_math"]}
+FILE_FLAGS = {"stage_mixed.cu": ["--use_fast_math"], "stage_tc.cu": ["--use_fast_math"]}
 
 
 def _nvcc() -> str:

@@ -52,7 +52,10 @@ struct dg_ctx {
     bool cur_is_a = true;
     dg::LaunchShape shape;    // stage kernel in use
     dg::LaunchShape shape1, shape2;   // mixed IIP: one / two nodes per thread
-    int variant_req = 0;      // 0: pick by timing on first use, 1 or 2: forced
+    dg::LaunchShape shape3;           // mixed IIP, p <= 4: tensor-core warp tiles
+    bool has_tc = false;              // shape3 is configured for the current mesh
+    dg::DevBuf<float> tcfrag;         // operator fragments of the tensor-core kernel
+    int variant_req = 0;      // 0: pick by timing on first use, 1, 2 or 3: forced
     bool tuned = false;
     // fused steps: five stages in one cooperative launch with grid barriers
     bool overint = false;     // FP64 path: over-integrated volume term
@@ -77,6 +80,7 @@ struct dg_ctx {
             b->release();
         geo32.release();
         ops32.release();
+        tcfrag.release();
         P0a.release();
         P0b.release();
         S0a.release();
@@ -187,10 +191,13 @@ dg_status run_stage(dg_ctx *c, int s, double t, double dt, const double vw[2], i
         e = dg::launch_stage_fp64(c->prm.p, c->shape, sp, make_phys<double>(c->prm, vw), c->stream);
     } else {
         sp.geo = c->geo32.ptr;
-        sp.ops = c->ops32.ptr;
-        e = (c->shape.variant == 2)
-                ? dg::launch_stage_mixed2(c->prm.p, false, c->shape, sp, make_phys<float>(c->prm, vw), c->stream)
-                : dg::launch_stage_mixed(c->prm.p, c->shape, sp, make_phys<float>(c->prm, vw), c->stream);
+        sp.ops = (c->shape.variant == 3) ? static_cast<const void *>(c->tcfrag.ptr) : c->ops32.ptr;
+        if (c->shape.variant == 3)
+            e = dg::launch_stage_tc(c->prm.p, false, false, c->shape, sp, make_phys<float>(c->prm, vw), c->stream);
+        else if (c->shape.variant == 2)
+            e = dg::launch_stage_mixed2(c->prm.p, false, c->shape, sp, make_phys<float>(c->prm, vw), c->stream);
+        else
+            e = dg::launch_stage_mixed(c->prm.p, c->shape, sp, make_phys<float>(c->prm, vw), c->stream);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
     c->launches += 1;
@@ -281,6 +288,16 @@ dg_status dg_create(const dg_params *params, void *cuda_stream, dg_ctx **out)
     }
     cudaMemcpy(c->ops64.ptr, o64.data(), o64.size() * sizeof(double), cudaMemcpyHostToDevice);
     cudaMemcpy(c->ops32.ptr, o32.data(), o32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (dg::stage_tc_supported(p.p)) {
+        std::vector<float> frag;
+        dg::build_tc_fragments(Np, NF, c->ops.Dr.data(), c->ops.Ds.data(), c->ops.LIFT.data(), frag);
+        if (c->tcfrag.alloc(frag.size()) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return DG_ECUDA;
+        }
+        cudaMemcpy(c->tcfrag.ptr, frag.data(), frag.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
     cudaMemcpy(c->Dr64.ptr, c->ops.Dr.data(), Np * Np * sizeof(double), cudaMemcpyHostToDevice);
     cudaMemcpy(c->Ds64.ptr, c->ops.Ds.data(), Np * Np * sizeof(double), cudaMemcpyHostToDevice);
     cudaMemcpy(c->fmask.ptr, c->ops.Fmask.data(), NF * sizeof(int), cudaMemcpyHostToDevice);
@@ -362,13 +379,15 @@ dg_status dg_set_stage_variant(dg_ctx *c, int variant)
 {
     if (!c) return DG_EINVAL;
     c->err.clear();
-    if (variant < 0 || variant > 2) return fail(c, DG_EINVAL, "variant must be 0, 1 or 2");
-    if (variant == 2 && (c->prm.precision != DG_PRECISION_MIXED || c->prm.theta != 0.0))
-        return fail(c, DG_EUNSUPPORTED, "the two-node kernel is the mixed-precision IIP kernel");
+    if (variant < 0 || variant > 3) return fail(c, DG_EINVAL, "variant must be 0, 1, 2 or 3");
+    if (variant >= 2 && (c->prm.precision != DG_PRECISION_MIXED || c->prm.theta != 0.0))
+        return fail(c, DG_EUNSUPPORTED, "the two-node and tensor-core kernels are mixed-precision IIP kernels");
+    if (variant == 3 && !dg::stage_tc_supported(c->prm.p))
+        return fail(c, DG_EUNSUPPORTED, "the tensor-core kernel covers p <= 4");
     c->variant_req = variant;
     c->tuned = (variant != 0);
     if (c->K > 0 && c->prm.precision == DG_PRECISION_MIXED && c->prm.theta == 0.0)
-        c->shape = (variant == 2) ? c->shape2 : c->shape1;
+        c->shape = (variant == 3) ? c->shape3 : (variant == 2) ? c->shape2 : c->shape1;
     return DG_OK;
 }
 
@@ -440,6 +459,13 @@ dg_status dg_set_mesh(dg_ctx *c, int64_t Nv, const double *vx, const double *vy,
         e = dg::stage_shape_mixed2(c->prm.p, K, false, c->shape2);
         if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel configuration");
         if (c->variant_req == 2) c->shape = c->shape2;
+        c->has_tc = false;
+        if (dg::stage_tc_supported(c->prm.p)) {
+            e = dg::stage_shape_tc(c->prm.p, K, false, false, c->shape3);
+            if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel configuration");
+            c->has_tc = true;
+            if (c->variant_req == 3) c->shape = c->shape3;
+        }
     }
     return DG_OK;
 }
@@ -533,7 +559,8 @@ static dg_status tune_stage(dg_ctx *c, const double vw[2])
     DG_CUDA(c, cudaEventCreate(&e1));
     float best = 0.f;
     dg::LaunchShape pick = c->shape1;
-    for (const dg::LaunchShape *cand : {&c->shape1, &c->shape2}) {
+    for (const dg::LaunchShape *cand : {&c->shape1, &c->shape2, &c->shape3}) {
+        if (cand == &c->shape3 && !c->has_tc) continue;
         c->shape = *cand;
         float ms = 0.f;
         for (int rep = 0; rep < 5; ++rep) {
@@ -580,7 +607,9 @@ dg_status dg_rhs(dg_ctx *c, double t, const double vw[2], double *dUdt, int on_d
 static dg_status run_fused_step(dg_ctx *c, double dt, const double vw[2])
 {
     if (c->fshape_variant != c->shape.variant) {
-        cudaError_t e = dg::stage_shape_mixed_fused(c->prm.p, c->shape.variant, false, c->K, c->fshape);
+        cudaError_t e = (c->shape.variant == 3)
+                            ? dg::stage_shape_tc(c->prm.p, c->K, false, true, c->fshape)
+                            : dg::stage_shape_mixed_fused(c->prm.p, c->shape.variant, false, c->K, c->fshape);
         if (e != cudaSuccess) return cuda_fail(c, e, "fused stage kernel configuration");
         c->fshape_variant = c->shape.variant;
     }
@@ -608,12 +637,15 @@ static dg_status run_fused_step(dg_ctx *c, double dt, const double vw[2])
     sp.mode = dg::STAGE_UPDATE;
     sp.first_stage = 1;
     sp.geo = c->geo32.ptr;
-    sp.ops = c->ops32.ptr;
+    sp.ops = (c->fshape.variant == 3) ? static_cast<const void *>(c->tcfrag.ptr) : c->ops32.ptr;
     sp.bar = c->bar.ptr;
     sp.bar_err = c->bar_err.ptr;
     sp.bar_limit = c->bar_limit;
     DG_CUDA(c, cudaMemsetAsync(c->bar.ptr, 0, 2 * sizeof(unsigned), c->stream));
-    DG_CUDA(c, dg::launch_stage_mixed_fused(c->prm.p, false, c->fshape, sp, make_phys<float>(c->prm, vw), c->stream));
+    if (c->fshape.variant == 3)
+        DG_CUDA(c, dg::launch_stage_tc(c->prm.p, false, true, c->fshape, sp, make_phys<float>(c->prm, vw), c->stream));
+    else
+        DG_CUDA(c, dg::launch_stage_mixed_fused(c->prm.p, false, c->fshape, sp, make_phys<float>(c->prm, vw), c->stream));
     c->launches += 1;
     c->cur_is_a = !c->cur_is_a;   // five swaps
     c->bar_used = true;

@@ -1,0 +1,536 @@
+// dg_stage_tc.cuh -- mixed-precision stage kernel with the operator products
+// on the tensor cores.
+//
+// Same method as dg_stage_mixed.cuh: the strong-form residual of Eq. dg_on_K
+// (IIP, theta = 0) and one stage of Algorithm 1, FP32 arithmetic with FP64
+// state, pressure recovery and registers.  What changes is how the work is
+// laid out:
+//
+// * Every warp owns a tile of WE = 4 elements from load to store.  It stages
+//   its own inputs with cp.async and synchronises with __syncwarp only, so the
+//   warps of a block run independently (no block barrier in the loop).
+// * The contractions -- broken gradient [Dr; Ds] U, divergence Dr Fr + Ds Fs
+//   and lift LIFT (Fscale dH), all batched over the tile's elements as
+//   (16 x 16)(16 x 8) products -- run as mma.sync m16n8k8 TF32 with FP32
+//   accumulation.  Each FP32 operand x is split into x_hi (x with the low 13
+//   mantissa bits rounded off) and x_lo = x - x_hi, and the product takes
+//   A_hi B_hi + A_hi B_lo + A_lo B_hi, about 2^-21 relative to sum |A||B|.
+//   The state and flux operands are taken relative to the element's first
+//   node (perturbation form): Dr 1 = Ds 1 = 0 makes this exact in exact
+//   arithmetic, and it keeps large means (the energy at low Mach) out of the
+//   split.
+// * The face-node gradients of the neighbours (Eq. ip_flux needs
+//   {{G grad U}} on both sides) come from the same MMA applied to the
+//   neighbour's staged state; a boundary face names its own element, so a
+//   wall face gets the own gradient the same way.
+//
+// MMA fragment layout (m16n8k8, row.col, TF32; lane = 4 g + t):
+//   A (16 x 8): a0 = A[g][t], a1 = A[g+8][t], a2 = A[g][t+4], a3 = A[g+8][t+4]
+//   B (8 x 8):  b0 = B[t][g], b1 = B[t+4][g]
+//   C (16 x 8): c0 = C[g][2t], c1 = C[g][2t+1], c2 = C[g+8][2t], c3 = C[g+8][2t+1]
+// Rows are nodes, columns (element of the pair, field): column n = 4 e + c.
+// After a shuffle with lane ^ 1 every lane holds all four fields of one node:
+// node g + 8 (lane & 1) of element (lane >> 1) & 1 of the pair.
+#pragma once
+#include "dg_stage_mixed.cuh"
+
+namespace dg {
+
+template <int P>
+struct ShapeTC {
+    static constexpr int Np = (P + 1) * (P + 2) / 2, Nfp = P + 1, NF = 3 * Nfp;
+    static_assert(Np <= 16 && NF <= 16, "one 16-row MMA tile per operator: p <= 4");
+    static constexpr int WE = 2;                  // elements per warp tile
+    static constexpr int NW = 4;                  // warps per block
+    static constexpr int NT = 32 * NW;
+    static constexpr int NpP = (Np + 3) & ~3;     // padded pressure row
+    static constexpr int US = 20;                 // float4 records per staged element (bank spread)
+    static constexpr int FS = 132;                // floats per element of the flux table
+    static constexpr int HS = 80;                 // floats per element of the dH table
+};
+
+// operator fragment table: [matrix: Dr, Ds, LIFT][k-step][hi, lo][lane] float4
+constexpr int TC_FRAG_FLOAT4 = 3 * 2 * 2 * 32;
+
+template <int P>
+struct TcLayout {
+    using S = ShapeTC<P>;
+    static constexpr int Np = S::Np, NF = S::NF, WE = S::WE, NpP = S::NpP;
+    static constexpr size_t al(size_t b) { return (b + 15) & ~size_t(15); }
+    // block header
+    static constexpr size_t hFrag = 0;                                      // float4 [TC_FRAG_FLOAT4]
+    static constexpr size_t hPos = hFrag + sizeof(float4) * TC_FRAG_FLOAT4; // int [3][16]: place of node j on face f, or -1
+    static constexpr size_t hFm = hPos + al(sizeof(int) * 3 * 16);          // int [NF]
+    static constexpr size_t header = hFm + al(sizeof(int) * NF);
+    // one region per warp
+    static constexpr size_t oConn = 0;                                      // int4 [WE]
+    static constexpr size_t oGeo = oConn + al(16 * WE);                     // float [WE][16]
+    static constexpr size_t oNGeo = oGeo + al(64 * WE);                     // float [3 WE][16]
+    static constexpr size_t oU = oNGeo + al(64 * 3 * WE);                   // float4 [WE][US]
+    static constexpr size_t oN = oU + al(16 * WE * S::US);                  // float4 [3 WE][US]
+    static constexpr size_t oPo = oN + al(16 * 3 * WE * S::US);             // float [WE][NpP]
+    static constexpr size_t oPn = oPo + al(4 * WE * NpP);                   // float [3 WE][NpP]
+    static constexpr size_t oRaw = oPn + al(4 * 3 * WE * NpP);              // double [WE][4][Np]
+    static constexpr size_t oK1 = oRaw + al(8 * WE * 4 * Np);               // double [WE][4][Np]
+    static constexpr size_t oF = oK1 + al(8 * WE * 4 * Np);                 // float [WE][FS]: node j: Fr[4], Fs[4]
+    static constexpr size_t oG = oF + al(4 * WE * S::FS);                   // float [WE][NF][8]: gx[4], gy[4] of the other side
+    static constexpr size_t oNorm = oG + al(4 * WE * NF * 8);               // float [WE][NF]
+    static constexpr size_t oDH = oNorm + al(4 * WE * NF);                  // float [WE][HS]: slot r: Fscale dH[4]
+    static constexpr size_t warp = oDH + al(4 * WE * S::HS);
+    static constexpr size_t bytes = header + S::NW * warp;
+};
+
+__device__ __forceinline__ void mma_tf32(float c[4], const float4 &a, float b0, float b1)
+{
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(__float_as_uint(a.x)), "r"(__float_as_uint(a.y)), "r"(__float_as_uint(a.z)), "r"(__float_as_uint(a.w)),
+          "r"(__float_as_uint(b0)), "r"(__float_as_uint(b1)));
+}
+
+// x = hi + lo: hi is x rounded to TF32 (10 explicit mantissa bits, so
+// |x - hi| <= 2^-11 |x|) and lo = x - hi, exact in FP32; the tensor core
+// reads lo as TF32, dropping at most 2^-11 |lo| <= 2^-22 |x|
+__device__ __forceinline__ void tf32_split(float x, float &hi, float &lo)
+{
+    unsigned h;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(x));
+    hi = __uint_as_float(h);
+    lo = x - hi;
+}
+
+// One k-step of C += A B with split operands, as three independent products:
+// the large one into ch, the two corrections into cl (summed at the end), so
+// consecutive MMAs of a contraction do not wait on each other
+__device__ __forceinline__ void mma3(float ch[4], float cl[4], const float4 &ahi, const float4 &alo, float b0,
+                                     float b1)
+{
+    float h0, l0, h1, l1;
+    tf32_split(b0, h0, l0);
+    tf32_split(b1, h1, l1);
+    mma_tf32(ch, ahi, h0, h1);
+    mma_tf32(cl, alo, h0, h1);
+    mma_tf32(cl, ahi, l0, l1);
+}
+
+// C fragment -> the four fields of this lane's node (see the header comment)
+__device__ __forceinline__ void frag_to_node(const float c[4], float v[4], int lane)
+{
+    const bool odd = lane & 1;
+    const float x = odd ? c[0] : c[2], y = odd ? c[1] : c[3];
+    const float rx = __shfl_xor_sync(0xffffffffu, x, 1), ry = __shfl_xor_sync(0xffffffffu, y, 1);
+    v[0] = odd ? rx : c[0];
+    v[1] = odd ? ry : c[1];
+    v[2] = odd ? c[2] : rx;
+    v[3] = odd ? c[3] : ry;
+}
+
+// Broken gradient of one 8-column tile: ur = Dr B, us = Ds B for B given as
+// this lane's four B values (k = t, t + 4, t + 8, t + 12), returned as the
+// four fields of this lane's node.  Four independent accumulator pairs.
+__device__ __forceinline__ void grad_mma(const float4 ah[2][2], const float4 al[2][2], const float b[4], int lane,
+                                         float ur[4], float us[4])
+{
+    float r0[4] = {0.f, 0.f, 0.f, 0.f}, r1[4] = {0.f, 0.f, 0.f, 0.f};
+    float r2[4] = {0.f, 0.f, 0.f, 0.f}, r3[4] = {0.f, 0.f, 0.f, 0.f};
+    float s0[4] = {0.f, 0.f, 0.f, 0.f}, s1[4] = {0.f, 0.f, 0.f, 0.f};
+    float s2[4] = {0.f, 0.f, 0.f, 0.f}, s3[4] = {0.f, 0.f, 0.f, 0.f};
+    mma3(r0, r1, ah[0][0], al[0][0], b[0], b[1]);
+    mma3(s0, s1, ah[1][0], al[1][0], b[0], b[1]);
+    mma3(r2, r3, ah[0][1], al[0][1], b[2], b[3]);
+    mma3(s2, s3, ah[1][1], al[1][1], b[2], b[3]);
+    float cr[4], cs[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        cr[c] = (r0[c] + r2[c]) + (r1[c] + r3[c]);
+        cs[c] = (s0[c] + s2[c]) + (s1[c] + s3[c]);
+    }
+    frag_to_node(cr, ur, lane);
+    frag_to_node(cs, us, lane);
+}
+
+template <int P, bool BATCH = false, bool FUSE = false>
+__global__ void __launch_bounds__(128, 4)
+stage_tc_kernel(StageParams sp, Phys<float> ph)
+{
+    using S = ShapeTC<P>;
+    using L = TcLayout<P>;
+    constexpr int Np = S::Np, Nfp = S::Nfp, NF = S::NF, WE = S::WE, NpP = S::NpP;
+    constexpr int US = S::US, FS = S::FS, HS = S::HS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const float4 *sFrag = reinterpret_cast<const float4 *>(smem_raw + L::hFrag);
+    int *sPos = reinterpret_cast<int *>(smem_raw + L::hPos);
+    int *sFm = reinterpret_cast<int *>(smem_raw + L::hFm);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    {
+        // operator fragments (built on the host in fragment order), face node tables
+        const float4 *tab = static_cast<const float4 *>(sp.ops);
+        float4 *dst = reinterpret_cast<float4 *>(smem_raw + L::hFrag);
+        for (int i = tid; i < TC_FRAG_FLOAT4; i += S::NT) dst[i] = tab[i];
+        for (int i = tid; i < NF; i += S::NT) sFm[i] = sp.fmask[i];
+        for (int i = tid; i < 48; i += S::NT) sPos[i] = -1;
+    }
+    __syncthreads();
+    for (int i = tid; i < NF; i += S::NT) sPos[(i / Nfp) * 16 + sFm[i]] = i % Nfp;
+    __syncthreads();
+
+    unsigned char *wb = smem_raw + L::header + wid * L::warp;
+    const unsigned wsh = static_cast<unsigned>(__cvta_generic_to_shared(wb));
+    int4 *sConn = reinterpret_cast<int4 *>(wb + L::oConn);
+    const float *sGeo = reinterpret_cast<const float *>(wb + L::oGeo);
+    const float *sNGeo = reinterpret_cast<const float *>(wb + L::oNGeo);
+    const float4 *sU = reinterpret_cast<const float4 *>(wb + L::oU);
+    const float4 *sN = reinterpret_cast<const float4 *>(wb + L::oN);
+    const float *sPo = reinterpret_cast<const float *>(wb + L::oPo);
+    const float *sPn = reinterpret_cast<const float *>(wb + L::oPn);
+    const double *sRaw = reinterpret_cast<const double *>(wb + L::oRaw);
+    const double *sK1 = reinterpret_cast<const double *>(wb + L::oK1);
+    float *sF = reinterpret_cast<float *>(wb + L::oF);
+    float *sG = reinterpret_cast<float *>(wb + L::oG);
+    float *sNorm = reinterpret_cast<float *>(wb + L::oNorm);
+    float *sDH = reinterpret_cast<float *>(wb + L::oDH);
+
+    const float *geo = static_cast<const float *>(sp.geo);
+    const long long K = sp.K;
+    const long long nwt = BATCH ? sp.ntiles : (K + WE - 1) / WE;
+    const double gm1d = sp.gm1;
+    const float cinv_fac = 0.5f * float(P + 1) * float(P + 2);
+    const float sig_fac = static_cast<float>(sp.sig_fac);
+    float dtr = static_cast<float>(sp.dt);
+    const bool update = sp.mode == STAGE_UPDATE;
+    bool need_k1 = update && !sp.first_stage;
+    const int g = lane >> 2, t = lane & 3;
+    const int jn = g + 8 * (lane & 1);       // node held after frag_to_node
+    const int ep = (lane >> 1) & 1;          // element of the pair held after frag_to_node
+    const int be = g >> 2, bc = g & 3;       // B column of this lane: element of the pair, field
+
+    for (int stg = 0; stg < (FUSE ? 5 : 1); ++stg) {
+    if constexpr (FUSE) {
+        if (stg > 0 && !grid_sync(sp.bar, sp.bar_err, gridDim.x, sp.bar_limit)) return;
+        fused_stage(sp, stg);
+        need_k1 = update && stg > 0;
+    }
+    for (long long wt = static_cast<long long>(blockIdx.x) * S::NW + wid; wt < nwt;
+         wt += static_cast<long long>(gridDim.x) * S::NW) {
+        long long k0 = wt * WE;
+        int ne = static_cast<int>((K - k0) < WE ? (K - k0) : WE);
+        if constexpr (BATCH) {
+            // warp tiles never straddle two cases: the case's viscosity, mesh
+            // velocity and time step
+            const int4 td = sp.tiles[wt];
+            k0 = td.x;
+            ne = td.y;
+            const BatchCase &cs = sp.cases[td.z];
+            ph.mu = static_cast<float>(cs.mu);
+            ph.vw2 = static_cast<float>(cs.vb);
+            dtr = static_cast<float>(cs.dt);
+        }
+        if (lane < ne) sConn[lane] = sp.conn[k0 + lane];
+        __syncwarp();
+        // ---- group A: FP32 state, pressure and geometry of the tile and of the
+        // three face neighbours of every element (a boundary face names its own
+        // element, so its slot holds the element itself)
+        for (int c = lane; c < ne * Np; c += 32) {
+            const int e = c / Np, j = c - (c / Np) * Np;
+            cp_async16(wsh + L::oU + 16u * (e * US + j), sp.Sin + (k0 + e) * Np + j);
+        }
+        for (int c = lane; c < ne * (NpP / 4); c += 32)
+            cp_async16(wsh + L::oPo + 16u * c, sp.Pin + k0 * NpP + 4 * c);
+        for (int c = lane; c < ne * 4; c += 32) cp_async16(wsh + L::oGeo + 16u * c, geo + k0 * 16 + 4 * c);
+        for (int c = lane; c < ne * 3 * Np; c += 32) {
+            const int sl = c / Np, j = c - (c / Np) * Np;
+            const int4 cn = sConn[sl / 3];
+            const int f = sl - 3 * (sl / 3);
+            const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
+            cp_async16(wsh + L::oN + 16u * (sl * US + j), sp.Sin + nb * Np + j);
+        }
+        for (int c = lane; c < ne * 3 * (NpP / 4); c += 32) {
+            const int sl = c / (NpP / 4), qq = c - (c / (NpP / 4)) * (NpP / 4);
+            const int4 cn = sConn[sl / 3];
+            const int f = sl - 3 * (sl / 3);
+            const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
+            cp_async16(wsh + L::oPn + 16u * c, sp.Pin + nb * NpP + 4 * qq);
+        }
+        for (int c = lane; c < ne * 3 * 4; c += 32) {
+            const int sl = c >> 2, qq = c & 3;
+            const int4 cn = sConn[sl / 3];
+            const int f = sl - 3 * (sl / 3);
+            const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
+            cp_async16(wsh + L::oNGeo + 16u * c, geo + nb * 16 + 4 * qq);
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+        // ---- group B: the FP64 registers, needed only by the update
+        for (int c = lane; c < ne * 2 * Np; c += 32) cp_async16(wsh + L::oRaw + 16u * c, sp.K0in + k0 * 4 * Np + 2 * c);
+        if (need_k1)
+            for (int c = lane; c < ne * 2 * Np; c += 32) cp_async16(wsh + L::oK1 + 16u * c, sp.K1 + k0 * 4 * Np + 2 * c);
+        asm volatile("cp.async.commit_group;\n" ::);
+        asm volatile("cp.async.wait_group 1;\n" ::);
+        __syncwarp();
+
+        // Dr, Ds fragments [matrix][k-step]
+        float4 ah[2][2], al[2][2];
+#pragma unroll
+        for (int m = 0; m < 2; ++m)
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                ah[m][ks] = sFrag[((m * 2 + ks) * 2 + 0) * 32 + lane];
+                al[m][ks] = sFrag[((m * 2 + ks) * 2 + 1) * 32 + lane];
+            }
+
+        // ---- V: broken gradient (MMA) and total flux of every volume node
+#pragma unroll
+        for (int nt = 0; nt < WE / 2; ++nt) {
+            const float *ub = reinterpret_cast<const float *>(sU + (2 * nt + be) * US);
+            const float ref = ub[bc];
+            float b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = t + 4 * q;
+                b[q] = (k < Np) ? ub[4 * k + bc] - ref : 0.f;
+            }
+            float ur[4], us[4];
+            grad_mma(ah, al, b, lane, ur, us);
+            const int e = 2 * nt + ep;
+            if (e < ne && jn < Np) {
+                const float *gg = sGeo + e * 16;
+                const float rx = gg[G_RX], ry = gg[G_RY], sx = gg[G_SX], sy = gg[G_SY];
+                float u[4], gx[4], gy[4];
+                f4_to(sU[e * US + jn], u);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    gx[c] = rx * ur[c] + sx * us[c];
+                    gy[c] = ry * ur[c] + sy * us[c];
+                }
+                const float p = sPo[e * NpP + jn];
+                float cx[4], cy[4], vx[4], vy[4], fr[4], fs[4];
+                adv_flux(u, p, ph, cx, cy);
+                visc_flux(u, gx, gy, ph, vx, vy);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float Fx = cx[c] - vx[c], Fy = cy[c] - vy[c];
+                    fr[c] = rx * Fx + ry * Fy;
+                    fs[c] = sx * Fx + sy * Fy;
+                }
+                float4 *fo = reinterpret_cast<float4 *>(sF + e * FS + jn * 8);
+                fo[0] = to_f4(fr);
+                fo[1] = to_f4(fs);
+            }
+        }
+
+        // ---- N: penalty norms of both traces at every face node
+        for (int q = lane; q < ne * NF; q += 32) {
+            const int e = q / NF, r = q - (q / NF) * NF, f = r / Nfp, i = r - (r / Nfp) * Nfp;
+            const int4 cn = sConn[e];
+            const int f2 = (cn.w >> (2 * f)) & 3, bt = (cn.w >> (8 + 2 * f)) & 3;
+            const float *gg = sGeo + e * 16;
+            const float n1 = gg[G_NX + f], n2 = gg[G_NY + f];
+            const int vm = sFm[f * Nfp + i], vp = sFm[f2 * Nfp + (Nfp - 1 - i)];
+            float u[4];
+            f4_to(sU[e * US + vm], u);
+            const float ir = 1.0f / u[0];
+            const float na = penalty_norm(u[0], u[1] * ir, u[2] * ir, u[3] * ir, n1, n2, ph);
+            float nb;
+            if (bt == BCT_INTERIOR) {
+                float w[4];
+                f4_to(sN[(e * 3 + f) * US + vp], w);
+                const float iw = 1.0f / w[0];
+                nb = penalty_norm(w[0], w[1] * iw, w[2] * iw, w[3] * iw, n1, n2, ph);
+            } else if (bt == BCT_FARFIELD) {
+                const float iw = 1.0f / ph.Uinf[0];
+                nb = penalty_norm(ph.Uinf[0], ph.Uinf[1] * iw, ph.Uinf[2] * iw, ph.Uinf[3] * iw, n1, n2, ph);
+            } else {
+                const float pw = sPo[e * NpP + vm];
+                const float eb = (pw / ph.gm1 + 0.5f * u[0] * (ph.vw1 * ph.vw1 + ph.vw2 * ph.vw2)) * ir;
+                nb = penalty_norm(u[0], ph.vw1, ph.vw2, eb, n1, n2, ph);
+            }
+            sNorm[e * NF + r] = fmaxf(na, nb);
+        }
+
+        // ---- S: gradients of the face slots (neighbour, or the element itself
+        // on a wall) at all their nodes; keep the ones on the shared face
+#pragma unroll 2
+        for (int st = 0; st < 3 * WE / 2; ++st) {
+            const float *nbp = reinterpret_cast<const float *>(sN + (2 * st + be) * US);
+            const float ref = nbp[bc];
+            float b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = t + 4 * q;
+                b[q] = (k < Np) ? nbp[4 * k + bc] - ref : 0.f;
+            }
+            float ur[4], us[4];
+            grad_mma(ah, al, b, lane, ur, us);
+            const int sl = 2 * st + ep, e = sl / 3, f = sl - 3 * (sl / 3);
+            if (e < ne && jn < Np) {
+                const int4 cn = sConn[e];
+                const int f2 = (cn.w >> (2 * f)) & 3, bt = (cn.w >> (8 + 2 * f)) & 3;
+                const int pos = sPos[f2 * 16 + jn];
+                if (bt != BCT_FARFIELD && pos >= 0) {
+                    const int i = (bt == BCT_INTERIOR) ? Nfp - 1 - pos : pos;
+                    const float *ng = sNGeo + sl * 16;
+                    float gx[4], gy[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        gx[c] = ng[G_RX] * ur[c] + ng[G_SX] * us[c];
+                        gy[c] = ng[G_RY] * ur[c] + ng[G_SY] * us[c];
+                    }
+                    float4 *go = reinterpret_cast<float4 *>(sG + (e * NF + f * Nfp + i) * 8);
+                    go[0] = to_f4(gx);
+                    go[1] = to_f4(gy);
+                }
+            }
+        }
+        __syncwarp();
+
+        // ---- F: numerical flux minus the own flux at every face node
+        for (int q = lane; q < ne * NF; q += 32) {
+            const int e = q / NF, r = q - (q / NF) * NF, f = r / Nfp, i = r - (r / Nfp) * Nfp;
+            const int4 cn = sConn[e];
+            const int f2 = (cn.w >> (2 * f)) & 3, bt = (cn.w >> (8 + 2 * f)) & 3;
+            const float *gg = sGeo + e * 16;
+            const float n1 = gg[G_NX + f], n2 = gg[G_NY + f], fsc = gg[G_FS + f];
+            float gbar = 0.f;
+#pragma unroll
+            for (int l = 0; l < Nfp; ++l) gbar = fmaxf(gbar, sNorm[e * NF + f * Nfp + l]);
+            float cinv = cinv_fac * fsc;
+            const float *ng = sNGeo + (e * 3 + f) * 16;
+            if (bt == BCT_INTERIOR) cinv = fmaxf(cinv, cinv_fac * ng[G_FS + f2]);
+            const float sigma = sig_fac * gbar * cinv;
+            const int vm = sFm[f * Nfp + i], vp = sFm[f2 * Nfp + (Nfp - 1 - i)];
+            float up[4], dH[4], Ftp[4];
+            f4_to(sU[e * US + vm], up);
+            const float pp = sPo[e * NpP + vm];
+            {
+                // F+ . n from the contravariant fluxes: (Fx, Fy) = M^-1 (Fr, Fs)
+                // with M = [[rx, ry], [sx, sy]]
+                const float rx = gg[G_RX], ry = gg[G_RY], sx = gg[G_SX], sy = gg[G_SY];
+                const float idet = 1.0f / (rx * sy - ry * sx);
+                const float a = (n1 * sy - n2 * sx) * idet, b = (n2 * rx - n1 * ry) * idet;
+                const float4 fr = *reinterpret_cast<const float4 *>(sF + e * FS + vm * 8);
+                const float4 fs = *reinterpret_cast<const float4 *>(sF + e * FS + vm * 8 + 4);
+                Ftp[0] = a * fr.x + b * fs.x;
+                Ftp[1] = a * fr.y + b * fs.y;
+                Ftp[2] = a * fr.z + b * fs.z;
+                Ftp[3] = a * fr.w + b * fs.w;
+            }
+            if (bt == BCT_INTERIOR) {
+                float um[4], gxm[4], gym[4];
+                f4_to(sN[(e * 3 + f) * US + vp], um);
+                const float4 *gq = reinterpret_cast<const float4 *>(sG + (e * NF + r) * 8);
+                f4_to(gq[0], gxm);
+                f4_to(gq[1], gym);
+                const float pm = sPn[(e * 3 + f) * NpP + vp];
+                float Fnm[4], vxm[4], vym[4], D[4];
+                flux_n(um, pm, n1, n2, ph, Fnm);
+                visc_flux(um, gxm, gym, ph, vxm, vym);
+                roe_dissipation(up, pp, um, pm, n1, n2, ph, D);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float Ftm = Fnm[c] - (vxm[c] * n1 + vym[c] * n2);
+                    dH[c] = 0.5f * (Ftp[c] - Ftm) - 0.5f * D[c] - sigma * (up[c] - um[c]);
+                }
+            } else if (bt == BCT_FARFIELD) {
+                const float ub[4] = {ph.Uinf[0], ph.Uinf[1], ph.Uinf[2], ph.Uinf[3]};
+                float Fnp[4], Fnb[4], D[4];
+                flux_n(up, pp, n1, n2, ph, Fnp);
+                flux_n(ub, ph.pinf, n1, n2, ph, Fnb);
+                roe_dissipation(up, pp, ub, ph.pinf, n1, n2, ph, D);
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    dH[c] = 0.5f * (Fnp[c] - Fnb[c]) - 0.5f * D[c] - sigma * (up[c] - ub[c]);
+            } else {
+                float gxp[4], gyp[4];
+                const float4 *gq = reinterpret_cast<const float4 *>(sG + (e * NF + r) * 8);
+                f4_to(gq[0], gxp);
+                f4_to(gq[1], gyp);
+                const float rb = up[0];
+                const float kw = 0.5f * rb * (ph.vw1 * ph.vw1 + ph.vw2 * ph.vw2);
+                const float ub[4] = {rb, rb * ph.vw1, rb * ph.vw2, pp / ph.gm1 + kw};
+                float Fnb[4], vxb[4], vyb[4], qx, qy;
+                flux_n(ub, pp, n1, n2, ph, Fnb);
+                visc_flux_prim(rb, ph.vw1, ph.vw2, ub[3] / rb, gxp, gyp, ph, vxb, vyb, &qx, &qy);
+                float vnb[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) vnb[c] = vxb[c] * n1 + vyb[c] * n2;
+                if (ph.adiabatic) vnb[3] -= qx * n1 + qy * n2;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) dH[c] = Ftp[c] - (Fnb[c] - vnb[c] + sigma * (up[c] - ub[c]));
+            }
+            *reinterpret_cast<float4 *>(sDH + e * HS + r * 4) =
+                make_float4(fsc * dH[0], fsc * dH[1], fsc * dH[2], fsc * dH[3]);
+        }
+        asm volatile("cp.async.wait_group 0;\n" ::);
+        __syncwarp();
+
+        // ---- U: R = -(Dr Fr + Ds Fs) + LIFT (Fscale dH) (MMA), then the stage
+        // update and the FP32 copy of the new state, one node per lane
+        {
+            float4 lh[2], ll[2];
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                lh[ks] = sFrag[((2 * 2 + ks) * 2 + 0) * 32 + lane];
+                ll[ks] = sFrag[((2 * 2 + ks) * 2 + 1) * 32 + lane];
+            }
+#pragma unroll
+            for (int nt = 0; nt < WE / 2; ++nt) {
+                const float *fb = sF + (2 * nt + be) * FS;
+                const float r0 = fb[bc], s0 = fb[4 + bc];
+                float br[4], bs[4], bh[4];
+                const float *hb = sDH + (2 * nt + be) * HS;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int k = t + 4 * q;
+                    br[q] = (k < Np) ? fb[8 * k + bc] - r0 : 0.f;
+                    bs[q] = (k < Np) ? fb[8 * k + 4 + bc] - s0 : 0.f;
+                    bh[q] = (k < NF) ? hb[4 * k + bc] : 0.f;
+                }
+                // four independent accumulators: divergence (Dr / Ds halves)
+                // and lift (two k-steps), each with its corrections
+                float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+                float d2[4] = {0.f, 0.f, 0.f, 0.f}, d3[4] = {0.f, 0.f, 0.f, 0.f};
+                float l0[4] = {0.f, 0.f, 0.f, 0.f}, l1[4] = {0.f, 0.f, 0.f, 0.f};
+                mma3(d0, d1, ah[0][0], al[0][0], br[0], br[1]);
+                mma3(d2, d3, ah[1][0], al[1][0], bs[0], bs[1]);
+                mma3(l0, l1, lh[0], ll[0], bh[0], bh[1]);
+                mma3(d0, d1, ah[0][1], al[0][1], br[2], br[3]);
+                mma3(d2, d3, ah[1][1], al[1][1], bs[2], bs[3]);
+                mma3(l0, l1, lh[1], ll[1], bh[2], bh[3]);
+                float cd[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) cd[c] = (l0[c] + l1[c]) - ((d0[c] + d2[c]) + (d1[c] + d3[c]));
+                float R[4];
+                frag_to_node(cd, R, lane);
+                const int e = 2 * nt + ep;
+                if (e < ne && jn < Np) {
+                    const long long base = (k0 + e) * 4 * Np + jn;
+                    if (sp.src) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) R[c] += cvt_d2f(sp.src[base + c * Np]);
+                    }
+                    if (!update) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) sp.Rout[base + c * Np] = cvt_f2d(R[c]);
+                    } else {
+                        double knew[4];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const double inc = cvt_f2d(dtr * R[c]);
+                            const double k1 = sp.first_stage ? inc : fma(sp.A, sK1[(e * 4 + c) * Np + jn], inc);
+                            sp.K1[base + c * Np] = k1;
+                            knew[c] = fma(sp.B, k1, sRaw[(e * 4 + c) * Np + jn]);
+                            sp.K0out[base + c * Np] = knew[c];
+                        }
+                        const float un[4] = {cvt_d2f_trunc(knew[0]), cvt_d2f_trunc(knew[1]),
+                                             cvt_d2f_trunc(knew[2]), cvt_d2f_trunc(knew[3])};
+                        sp.Sout[(k0 + e) * Np + jn] = to_f4(un);
+                        sp.Pout[(k0 + e) * NpP + jn] = pressure<float>(un, knew[3], gm1d);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+    }  // stages
+}
+
+}  // namespace dg

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "dg_device.cuh"
 
 namespace dg {
@@ -12,7 +14,8 @@ struct BatchCase;
 
 struct LaunchShape {
     bool theta = false;      // kernel variant with the theta terms of the IP flux
-    int variant = 1;         // mixed IIP kernel: 1 node per thread (1) or 2 nodes per thread (2)
+    int variant = 1;         // mixed IIP kernel: 1 node per thread (1), 2 nodes per thread (2),
+                             // tensor-core warp tiles (3)
     bool overint = false;    // FP64 kernel: volume flux integrated with a cubature rule
     int grid = 0;
     int threads = 0;
@@ -52,6 +55,18 @@ cudaError_t launch_stage_mixed_fused(int p, bool batch, const LaunchShape &ls, c
                                      const Phys<float> &ph, cudaStream_t st);
 // elements per tile of the mixed kernel for degree p
 int stage_tile_elems(int p);
+// the tensor-core mixed IIP kernel (p = 1..4): warp tiles of 4 elements;
+// its `ops` is the fragment table of build_tc_fragments
+bool stage_tc_supported(int p);
+// units = K elements (single mesh) or the tile count of a batch tile table;
+// fused: five stages per cooperative launch with grid barriers
+cudaError_t stage_shape_tc(int p, long long units, bool batch, bool fused, LaunchShape &out);
+cudaError_t launch_stage_tc(int p, bool batch, bool fused, const LaunchShape &ls, const StageParams &sp,
+                            const Phys<float> &ph, cudaStream_t st);
+// Dr, Ds [Np][Np] and LIFT [Np][NF] (FP64, row-major) -> the kernel's
+// fragment table (TF32 hi / lo pairs, 3 * 2 * 2 * 32 float4)
+void build_tc_fragments(int Np, int NF, const double *Dr, const double *Ds, const double *LIFT,
+                        std::vector<float> &out);
 // FP32 copy [K][Np] float4 and FP64-recovered pressure [K][NpP] of a state
 cudaError_t launch_make_shadow(int p, const double *K0, long long K, double gm1, float4 *S,
                                float *Pr, cudaStream_t st);

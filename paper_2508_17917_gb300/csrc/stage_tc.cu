@@ -1,0 +1,150 @@
+// stage_tc.cu -- the tensor-core stage kernel (mixed precision, IIP,
+// p = 1..4): launch shape, launch, and the operator fragment table.
+#include <cstring>
+
+#include "dg_stage_tc.cuh"
+#include "launch.h"
+
+namespace dg {
+namespace {
+
+// persistent grid: SMs x resident blocks, capped by the warp tiles (units =
+// K elements, or the tile count of a batch tile table); the fused variant
+// must fit the grid on the GPU at once (cooperative launch)
+template <int P, bool BATCH, bool FUSE>
+cudaError_t shape_tc_p(long long units, LaunchShape &ls)
+{
+    using S = ShapeTC<P>;
+    using L = TcLayout<P>;
+    auto kern = stage_tc_kernel<P, BATCH, FUSE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(L::bytes));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::NT, L::bytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) {
+        if (FUSE) return cudaErrorInvalidConfiguration;
+        per_sm = 1;
+    }
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long nwt = BATCH ? units : (units + S::WE - 1) / S::WE;
+    const long long nblocks = (nwt + S::NW - 1) / S::NW;
+    const long long grid = static_cast<long long>(sms) * per_sm;
+    ls.grid = static_cast<int>(nblocks < grid ? nblocks : grid);
+    if (ls.grid < 1) ls.grid = 1;
+    ls.threads = S::NT;
+    ls.smem = L::bytes;
+    ls.elems_per_tile = S::WE;
+    ls.theta = false;
+    ls.variant = 3;
+    return cudaSuccess;
+}
+
+template <int P, bool BATCH, bool FUSE>
+cudaError_t launch_tc_p(const LaunchShape &ls, const StageParams &sp, const Phys<float> &ph, cudaStream_t st)
+{
+    if (!FUSE) {
+        stage_tc_kernel<P, BATCH, false><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ls.grid);
+    cfg.blockDim = dim3(ls.threads);
+    cfg.dynamicSmemBytes = ls.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, stage_tc_kernel<P, BATCH, true>, sp, ph);
+}
+
+template <int P>
+cudaError_t shape_tc_any(long long units, bool batch, bool fused, LaunchShape &ls)
+{
+    if (batch) return fused ? shape_tc_p<P, true, true>(units, ls) : shape_tc_p<P, true, false>(units, ls);
+    return fused ? shape_tc_p<P, false, true>(units, ls) : shape_tc_p<P, false, false>(units, ls);
+}
+
+template <int P>
+cudaError_t launch_tc_any(bool batch, bool fused, const LaunchShape &ls, const StageParams &sp,
+                          const Phys<float> &ph, cudaStream_t st)
+{
+    if (batch) return fused ? launch_tc_p<P, true, true>(ls, sp, ph, st) : launch_tc_p<P, true, false>(ls, sp, ph, st);
+    return fused ? launch_tc_p<P, false, true>(ls, sp, ph, st) : launch_tc_p<P, false, false>(ls, sp, ph, st);
+}
+
+// x rounded to TF32 (10 explicit mantissa bits), ties away from zero; the
+// operators are finite and far from the FP32 overflow threshold
+float tf32_round(float x)
+{
+    unsigned u;
+    std::memcpy(&u, &x, 4);
+    u = (u + 0x1000u) & 0xffffe000u;
+    std::memcpy(&x, &u, 4);
+    return x;
+}
+
+}  // namespace
+
+bool stage_tc_supported(int p) { return p >= 1 && p <= 4; }
+
+cudaError_t stage_shape_tc(int p, long long units, bool batch, bool fused, LaunchShape &out)
+{
+    switch (p) {
+    case 1: return shape_tc_any<1>(units, batch, fused, out);
+    case 2: return shape_tc_any<2>(units, batch, fused, out);
+    case 3: return shape_tc_any<3>(units, batch, fused, out);
+    case 4: return shape_tc_any<4>(units, batch, fused, out);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_stage_tc(int p, bool batch, bool fused, const LaunchShape &ls, const StageParams &sp,
+                            const Phys<float> &ph, cudaStream_t st)
+{
+    switch (p) {
+    case 1: return launch_tc_any<1>(batch, fused, ls, sp, ph, st);
+    case 2: return launch_tc_any<2>(batch, fused, ls, sp, ph, st);
+    case 3: return launch_tc_any<3>(batch, fused, ls, sp, ph, st);
+    case 4: return launch_tc_any<4>(batch, fused, ls, sp, ph, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// A operands of the three operators, zero-padded to 16 x 16, in the order the
+// kernel reads them: [matrix][k-step][hi, lo][lane][a0..a3] with lane = 4 g + t,
+// a0 = A[g][8 ks + t], a1 = A[g + 8][8 ks + t], a2 = A[g][8 ks + t + 4],
+// a3 = A[g + 8][8 ks + t + 4].  hi is the FP64 entry rounded to FP32 and
+// then to TF32; lo is the remainder rounded the same way.
+void build_tc_fragments(int Np, int NF, const double *Dr, const double *Ds, const double *LIFT,
+                        std::vector<float> &out)
+{
+    out.assign(static_cast<size_t>(TC_FRAG_FLOAT4) * 4, 0.0f);
+    auto entry = [&](int m, int row, int col) -> double {
+        if (row >= Np) return 0.0;
+        if (m < 2) return (col < Np) ? (m == 0 ? Dr : Ds)[row * Np + col] : 0.0;
+        return (col < NF) ? LIFT[row * NF + col] : 0.0;
+    };
+    for (int m = 0; m < 3; ++m)
+        for (int ks = 0; ks < 2; ++ks)
+            for (int lane = 0; lane < 32; ++lane) {
+                const int g = lane >> 2, t = lane & 3;
+                const int rows[4] = {g, g + 8, g, g + 8};
+                const int cols[4] = {8 * ks + t, 8 * ks + t, 8 * ks + t + 4, 8 * ks + t + 4};
+                for (int a = 0; a < 4; ++a) {
+                    const double x = entry(m, rows[a], cols[a]);
+                    const float hi = tf32_round(static_cast<float>(x));
+                    const float lo = tf32_round(static_cast<float>(x - static_cast<double>(hi)));
+                    out[((((m * 2 + ks) * 2 + 0) * 32 + lane) * 4) + a] = hi;
+                    out[((((m * 2 + ks) * 2 + 1) * 32 + lane) * 4) + a] = lo;
+                }
+            }
+}
+
+}  // namespace dg

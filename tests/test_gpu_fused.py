@@ -1,7 +1,7 @@
 """Fused steps: the five stages of Algorithm 1 in one cooperative launch with
 grid barriers between stages (dg_set_fused_steps).
 
-* The same result as five stage launches, for both tile shapes, on the
+* The same result as five stage launches, for every tile shape, on the
   periodic vortex and on the O-grid with wall and far-field faces: equal to
   within 1e-9 of the largest state value (the fused kernels are separate
   instantiations, so the compiler may contract a multiply-add differently;
@@ -59,7 +59,7 @@ def start(s, kw):
     return dg_inputs.perturb(U, seed=2, amp=1e-3)
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("case", [vortex_case, ogrid_case])
 def test_fused_steps_match_five_launches(dg, case, variant):
     mesh, p, kw, vw = case()

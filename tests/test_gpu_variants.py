@@ -86,7 +86,7 @@ def test_vortex_steps_variant(dg, variant):
     J, M = P.geo["J"], P.ops["M"]
     err = np.sqrt(np.einsum("k,kcn,nm,kcm->c", J, d, M, d) / np.einsum("k,kcn,nm,kcm->c", J, ref, M, ref))
     assert np.all(err <= 2e-5), err
-    assert s.variant in (1, 2)
+    assert s.variant in (1, 2, 3)
 
 
 def test_variant_two_rejected_on_fp64(dg):
