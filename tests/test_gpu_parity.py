@@ -146,19 +146,32 @@ def test_vortex_p2_100_steps(dg, precision, seed):
     assert s.check_finite()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_vortex_p4_full_size_short(dg, precision):
+_FULL = {}
+
+
+def _full_size_reference():
+    """Oracle run of the benchmark workload (shared by the cases below)."""
+    if not _FULL:
+        mesh = dg_inputs.periodic_square(128)
+        P = oracle.Problem(mesh, 4, mu=1e-3)
+        U0 = vortex_state(P, 0)
+        dt, _ = P.dt(U0, 0.3)
+        _FULL.update(mesh=mesh, P=P, U0=U0, dt=dt, ref=P.run(U0, 0.0, dt, 5))
+    return _FULL
+
+
+@pytest.mark.parametrize("precision,variant", [("fp64", 0), ("mixed", 0), ("mixed", 3)])
+def test_vortex_p4_full_size_short(dg, precision, variant):
     """p = 4, 128 x 128 split quads (K = 32,768): 5 steps at full size in the
-    benchmark's launch configuration, whole state compared."""
-    mesh = dg_inputs.periodic_square(128)
-    P = oracle.Problem(mesh, 4, mu=1e-3)
-    U0 = vortex_state(P, 0)
-    dt, _ = P.dt(U0, 0.3)
-    ref = P.run(U0, 0.0, dt, 5)
-    s = dg.Solver(mesh, 4, precision, stream=stream(), mu=1e-3)
-    s.set_state(U0)
-    s.steps(0.0, dt, 5)
-    err = rel_l2(P, s.get_state(), ref)
+    benchmark's launch configuration (tile shape from the tuner), whole state
+    compared; also with the tensor-core shape forced."""
+    f = _full_size_reference()
+    s = dg.Solver(f["mesh"], 4, precision, stream=stream(), mu=1e-3)
+    if variant:
+        s.set_variant(variant)
+    s.set_state(f["U0"])
+    s.steps(0.0, f["dt"], 5)
+    err = rel_l2(f["P"], s.get_state(), f["ref"])
     assert np.all(err <= PREC_TOL[precision]), err
 
 
