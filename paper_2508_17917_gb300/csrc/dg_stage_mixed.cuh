@@ -54,6 +54,17 @@ __device__ __forceinline__ void cp_async16(unsigned dst, const void *src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
 }
 
+// Programmatic dependent launch: wait until the previous kernel of the
+// stream has completed and its writes are visible (a no-op after an ordinary
+// launch), then allow the next kernel's blocks to be scheduled as this
+// kernel's blocks exit.  Called after the prologue that reads only constant
+// operator tables, before the first read or write of the state.
+__device__ __forceinline__ void pdl_wait_then_release()
+{
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // Grid-wide barrier for the fused (cooperative) launch.  Thread 0 of every
 // block makes the block's writes visible, counts the block in and waits for
 // the generation to advance; the last block in resets the count and advances
@@ -198,6 +209,7 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
     const bool update = sp.mode == STAGE_UPDATE;
     bool need_k1 = update && !sp.first_stage;
     __syncthreads();
+    pdl_wait_then_release();
 
     const int ve = tid / Np, vi = tid - (tid / Np) * Np;
     const int fe = tid / NF, fm = tid - (tid / NF) * NF;

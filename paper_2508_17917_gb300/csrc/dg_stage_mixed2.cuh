@@ -71,6 +71,7 @@ stage_mixed2_kernel(StageParams sp, Phys<float> ph)
     const bool update = sp.mode == STAGE_UPDATE;
     bool need_k1 = update && !sp.first_stage;
     __syncthreads();
+    pdl_wait_then_release();
 
     const int el = tid / W, q = tid - (tid / W) * W;
     // volume slot: nodes i0, i1 (i1 = i0 when q + H is past the last node)

@@ -173,6 +173,7 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
     __syncthreads();
     for (int i = tid; i < NF; i += S::NT) sPos[(i / Nfp) * 16 + sFm[i]] = i % Nfp;
     __syncthreads();
+    pdl_wait_then_release();
 
     unsigned char *wb = smem_raw + L::header + wid * L::warp;
     const unsigned wsh = static_cast<unsigned>(__cvta_generic_to_shared(wb));

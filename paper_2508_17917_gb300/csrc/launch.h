@@ -23,6 +23,26 @@ struct LaunchShape {
     int elems_per_tile = 0;
 };
 
+// Launch `kern` with programmatic stream serialization: its blocks may be
+// scheduled while the previous kernel of the stream drains; the kernel waits
+// for that kernel (pdl_wait_then_release) before touching the state.
+template <typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(Args...), const LaunchShape &ls, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ls.grid);
+    cfg.blockDim = dim3(ls.threads);
+    cfg.dynamicSmemBytes = ls.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+
 // Launch configuration of the fused stage kernel for degree p and K elements
 // on the current device (persistent grid: SMs x resident CTAs, capped by tiles).
 cudaError_t stage_shape_fp64(int p, long long K, bool theta, LaunchShape &out, bool overint = false);

@@ -5,6 +5,7 @@
 #include "launch.h"
 
 namespace dg {
+
 namespace {
 
 template <int P, bool TH>
@@ -36,11 +37,8 @@ cudaError_t shape_p(long long K, LaunchShape &ls)
 template <int P>
 cudaError_t launch_p(const LaunchShape &ls, const StageParams &sp, const Phys<float> &ph, cudaStream_t st)
 {
-    if (ls.theta)
-        stage_mixed_kernel<P, true><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
-    else
-        stage_mixed_kernel<P, false><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
-    return cudaGetLastError();
+    if (ls.theta) return launch_pdl(stage_mixed_kernel<P, true, false, false>, ls, st, sp, ph);
+    return launch_pdl(stage_mixed_kernel<P, false, false, false>, ls, st, sp, ph);
 }
 
 template <int P>
@@ -71,8 +69,7 @@ cudaError_t shape_batch_p(long long ntiles, LaunchShape &ls)
 template <int P>
 cudaError_t launch_batch_p(const LaunchShape &ls, const StageParams &sp, const Phys<float> &ph, cudaStream_t st)
 {
-    stage_mixed_kernel<P, false, true><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
-    return cudaGetLastError();
+    return launch_pdl(stage_mixed_kernel<P, false, true, false>, ls, st, sp, ph);
 }
 
 // two nodes per thread (IIP): shape for `ntiles` tiles (batch) or for K elements
@@ -107,8 +104,7 @@ cudaError_t shape2_p(long long units, LaunchShape &ls)
 template <int P, bool BATCH>
 cudaError_t launch2_p(const LaunchShape &ls, const StageParams &sp, const Phys<float> &ph, cudaStream_t st)
 {
-    stage_mixed2_kernel<P, BATCH><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
-    return cudaGetLastError();
+    return launch_pdl(stage_mixed2_kernel<P, BATCH, false>, ls, st, sp, ph);
 }
 
 // fused variant: five stages per cooperative launch; the grid is the number
