@@ -238,6 +238,10 @@ def run_ours(args):
     solvers = {}
     for prec in ("mixed", "fp64"):
         s = dg.Solver(mesh, P, prec, stream=sh, mu=1e-3)
+        if prec == "mixed" and args.variant:
+            # a forced tile shape (profiling runs: timing under a profiler
+            # would mislead the first-step tuner)
+            s.set_variant(args.variant)
         x, y = s.node_coords()
         U0 = dg_inputs.perturb(to_kcn(dg_inputs.isentropic_vortex(x, y)), seed=0)
         s.set_state(U0)
@@ -598,6 +602,8 @@ def main():
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="tile shape of the headline's mixed kernel (0: first-step tuner)")
     ap.add_argument("--profile", choices=["mixed512", "mixed128", "fp64_128", "sip128", "tc512"], default=None)
     args = ap.parse_args()
     if args.profile:

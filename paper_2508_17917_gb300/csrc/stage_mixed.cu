@@ -69,7 +69,10 @@ cudaError_t shape_batch_p(long long ntiles, LaunchShape &ls)
 template <int P>
 cudaError_t launch_batch_p(const LaunchShape &ls, const StageParams &sp, const Phys<float> &ph, cudaStream_t st)
 {
-    return launch_pdl(stage_mixed_kernel<P, false, true, false>, ls, st, sp, ph);
+    // batch stage launches are graph-captured next to the batch's other
+    // kernels: ordinary launches (overlapping launches measured slower there)
+    stage_mixed_kernel<P, false, true><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
+    return cudaGetLastError();
 }
 
 // two nodes per thread (IIP): shape for `ntiles` tiles (batch) or for K elements
@@ -104,7 +107,11 @@ cudaError_t shape2_p(long long units, LaunchShape &ls)
 template <int P, bool BATCH>
 cudaError_t launch2_p(const LaunchShape &ls, const StageParams &sp, const Phys<float> &ph, cudaStream_t st)
 {
-    return launch_pdl(stage_mixed2_kernel<P, BATCH, false>, ls, st, sp, ph);
+    if (BATCH) {
+        stage_mixed2_kernel<P, true><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
+        return cudaGetLastError();
+    }
+    return launch_pdl(stage_mixed2_kernel<P, false, false>, ls, st, sp, ph);
 }
 
 // fused variant: five stages per cooperative launch; the grid is the number

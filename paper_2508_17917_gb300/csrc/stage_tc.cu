@@ -47,7 +47,11 @@ cudaError_t shape_tc_p(long long units, LaunchShape &ls)
 template <int P, bool BATCH, bool FUSE>
 cudaError_t launch_tc_p(const LaunchShape &ls, const StageParams &sp, const Phys<float> &ph, cudaStream_t st)
 {
-    if (!FUSE) return launch_pdl(stage_tc_kernel<P, BATCH, false>, ls, st, sp, ph);
+    if (!FUSE && !BATCH) return launch_pdl(stage_tc_kernel<P, false, false>, ls, st, sp, ph);
+    if (!FUSE) {
+        stage_tc_kernel<P, true, false><<<ls.grid, ls.threads, ls.smem, st>>>(sp, ph);
+        return cudaGetLastError();
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ls.grid);
     cfg.blockDim = dim3(ls.threads);
