@@ -20,9 +20,11 @@
 //   arithmetic, and it keeps large means (the energy at low Mach) out of the
 //   split.
 // * The face-node gradients of the neighbours (Eq. ip_flux needs
-//   {{G grad U}} on both sides) come from the same MMA applied to the
-//   neighbour's staged state; a boundary face names its own element, so a
-//   wall face gets the own gradient the same way.
+//   {{G grad U}} on both sides) are the rows of [Dr; Ds] at the shared node
+//   applied to the neighbour's staged state (FP32 FMAs: 5 of 16 rows are
+//   needed, which costs fewer instructions than an MMA of all 16); a
+//   boundary face names its own element, so a wall face gets the own
+//   gradient the same way.
 //
 // MMA fragment layout (m16n8k8, row.col, TF32; lane = 4 g + t):
 //   A (16 x 8): a0 = A[g][t], a1 = A[g+8][t], a2 = A[g][t+4], a3 = A[g+8][t+4]
@@ -49,7 +51,9 @@ struct ShapeTC {
     static constexpr int HS = 80;                 // floats per element of the dH table
 };
 
-// operator fragment table: [matrix: Dr, Ds, LIFT][k-step][hi, lo][lane] float4
+// operator table: the MMA fragments [matrix: Dr, Ds, LIFT][k-step][hi, lo][lane]
+// (float4), then (Dr, Ds) in FP32 as float2 [Np][Np] for the face-node
+// gradients of the neighbours
 constexpr int TC_FRAG_FLOAT4 = 3 * 2 * 2 * 32;
 
 template <int P>
@@ -59,9 +63,9 @@ struct TcLayout {
     static constexpr size_t al(size_t b) { return (b + 15) & ~size_t(15); }
     // block header
     static constexpr size_t hFrag = 0;                                      // float4 [TC_FRAG_FLOAT4]
-    static constexpr size_t hPos = hFrag + sizeof(float4) * TC_FRAG_FLOAT4; // int [3][16]: place of node j on face f, or -1
-    static constexpr size_t hFm = hPos + al(sizeof(int) * 3 * 16);          // int [NF]
-    static constexpr size_t header = hFm + al(sizeof(int) * NF);
+    static constexpr size_t hFm = hFrag + sizeof(float4) * TC_FRAG_FLOAT4;  // int [NF]
+    static constexpr size_t hD = hFm + al(sizeof(int) * NF);                // float2 [Np][Np]: (Dr, Ds)
+    static constexpr size_t header = hD + al(sizeof(float2) * Np * Np);
     // one region per warp
     static constexpr size_t oConn = 0;                                      // int4 [WE]
     static constexpr size_t oGeo = oConn + al(16 * WE);                     // float [WE][16]
@@ -73,8 +77,7 @@ struct TcLayout {
     static constexpr size_t oRaw = oPn + al(4 * 3 * WE * NpP);              // double [WE][4][Np]
     static constexpr size_t oK1 = oRaw + al(8 * WE * 4 * Np);               // double [WE][4][Np]
     static constexpr size_t oF = oK1 + al(8 * WE * 4 * Np);                 // float [WE][FS]: node j: Fr[4], Fs[4]
-    static constexpr size_t oG = oF + al(4 * WE * S::FS);                   // float [WE][NF][8]: gx[4], gy[4] of the other side
-    static constexpr size_t oNorm = oG + al(4 * WE * NF * 8);               // float [WE][NF]
+    static constexpr size_t oNorm = oF + al(4 * WE * S::FS);                // float [WE][NF]
     static constexpr size_t oDH = oNorm + al(4 * WE * NF);                  // float [WE][HS]: slot r: Fscale dH[4]
     static constexpr size_t warp = oDH + al(4 * WE * S::HS);
     static constexpr size_t bytes = header + S::NW * warp;
@@ -159,19 +162,19 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
     constexpr int US = S::US, FS = S::FS, HS = S::HS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const float4 *sFrag = reinterpret_cast<const float4 *>(smem_raw + L::hFrag);
-    int *sPos = reinterpret_cast<int *>(smem_raw + L::hPos);
     int *sFm = reinterpret_cast<int *>(smem_raw + L::hFm);
+    const float2 *sD = reinterpret_cast<const float2 *>(smem_raw + L::hD);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     {
         // operator fragments (built on the host in fragment order), face node tables
         const float4 *tab = static_cast<const float4 *>(sp.ops);
         float4 *dst = reinterpret_cast<float4 *>(smem_raw + L::hFrag);
         for (int i = tid; i < TC_FRAG_FLOAT4; i += S::NT) dst[i] = tab[i];
+        const float2 *dtab = reinterpret_cast<const float2 *>(tab + TC_FRAG_FLOAT4);
+        float2 *dD = reinterpret_cast<float2 *>(smem_raw + L::hD);
+        for (int i = tid; i < Np * Np; i += S::NT) dD[i] = dtab[i];
         for (int i = tid; i < NF; i += S::NT) sFm[i] = sp.fmask[i];
-        for (int i = tid; i < 48; i += S::NT) sPos[i] = -1;
     }
-    __syncthreads();
-    for (int i = tid; i < NF; i += S::NT) sPos[(i / Nfp) * 16 + sFm[i]] = i % Nfp;
     __syncthreads();
     pdl_wait_then_release();
 
@@ -187,7 +190,6 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
     const double *sRaw = reinterpret_cast<const double *>(wb + L::oRaw);
     const double *sK1 = reinterpret_cast<const double *>(wb + L::oK1);
     float *sF = reinterpret_cast<float *>(wb + L::oF);
-    float *sG = reinterpret_cast<float *>(wb + L::oG);
     float *sNorm = reinterpret_cast<float *>(wb + L::oNorm);
     float *sDH = reinterpret_cast<float *>(wb + L::oDH);
 
@@ -347,40 +349,6 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
             sNorm[e * NF + r] = fmaxf(na, nb);
         }
 
-        // ---- S: gradients of the face slots (neighbour, or the element itself
-        // on a wall) at all their nodes; keep the ones on the shared face
-#pragma unroll 2
-        for (int st = 0; st < 3 * WE / 2; ++st) {
-            const float *nbp = reinterpret_cast<const float *>(sN + (2 * st + be) * US);
-            const float ref = nbp[bc];
-            float b[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int k = t + 4 * q;
-                b[q] = (k < Np) ? nbp[4 * k + bc] - ref : 0.f;
-            }
-            float ur[4], us[4];
-            grad_mma(ah, al, b, lane, ur, us);
-            const int sl = 2 * st + ep, e = sl / 3, f = sl - 3 * (sl / 3);
-            if (e < ne && jn < Np) {
-                const int4 cn = sConn[e];
-                const int f2 = (cn.w >> (2 * f)) & 3, bt = (cn.w >> (8 + 2 * f)) & 3;
-                const int pos = sPos[f2 * 16 + jn];
-                if (bt != BCT_FARFIELD && pos >= 0) {
-                    const int i = (bt == BCT_INTERIOR) ? Nfp - 1 - pos : pos;
-                    const float *ng = sNGeo + sl * 16;
-                    float gx[4], gy[4];
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        gx[c] = ng[G_RX] * ur[c] + ng[G_SX] * us[c];
-                        gy[c] = ng[G_RY] * ur[c] + ng[G_SY] * us[c];
-                    }
-                    float4 *go = reinterpret_cast<float4 *>(sG + (e * NF + f * Nfp + i) * 8);
-                    go[0] = to_f4(gx);
-                    go[1] = to_f4(gy);
-                }
-            }
-        }
         __syncwarp();
 
         // ---- F: numerical flux minus the own flux at every face node
@@ -414,12 +382,26 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
                 Ftp[2] = a * fr.z + b * fs.z;
                 Ftp[3] = a * fr.w + b * fs.w;
             }
+            // broken gradient of the other side at this face node: the
+            // neighbour's at vp, or (wall) the element's own at vm; a boundary
+            // face's slot holds the element itself
+            float go_x[4] = {0.f, 0.f, 0.f, 0.f}, go_y[4] = {0.f, 0.f, 0.f, 0.f};
+            if (bt != BCT_FARFIELD) {
+                const float4 *src = sN + (e * 3 + f) * US;
+                const int row = (bt == BCT_INTERIOR) ? vp : vm;
+                float wr[4] = {0.f, 0.f, 0.f, 0.f}, ws[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int j = 0; j < Np; ++j) acc_rs(wr, ws, sD[row * Np + j], src[j]);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    go_x[c] = ng[G_RX] * wr[c] + ng[G_SX] * ws[c];
+                    go_y[c] = ng[G_RY] * wr[c] + ng[G_SY] * ws[c];
+                }
+            }
             if (bt == BCT_INTERIOR) {
-                float um[4], gxm[4], gym[4];
+                float um[4];
+                const float *gxm = go_x, *gym = go_y;
                 f4_to(sN[(e * 3 + f) * US + vp], um);
-                const float4 *gq = reinterpret_cast<const float4 *>(sG + (e * NF + r) * 8);
-                f4_to(gq[0], gxm);
-                f4_to(gq[1], gym);
                 const float pm = sPn[(e * 3 + f) * NpP + vp];
                 float Fnm[4], vxm[4], vym[4], D[4];
                 flux_n(um, pm, n1, n2, ph, Fnm);
@@ -440,10 +422,7 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
                 for (int c = 0; c < 4; ++c)
                     dH[c] = 0.5f * (Fnp[c] - Fnb[c]) - 0.5f * D[c] - sigma * (up[c] - ub[c]);
             } else {
-                float gxp[4], gyp[4];
-                const float4 *gq = reinterpret_cast<const float4 *>(sG + (e * NF + r) * 8);
-                f4_to(gq[0], gxp);
-                f4_to(gq[1], gyp);
+                const float *gxp = go_x, *gyp = go_y;
                 const float rb = up[0];
                 const float kw = 0.5f * rb * (ph.vw1 * ph.vw1 + ph.vw2 * ph.vw2);
                 const float ub[4] = {rb, rb * ph.vw1, rb * ph.vw2, pp / ph.gm1 + kw};

@@ -84,7 +84,8 @@ cudaError_t stage_shape_tc(int p, long long units, bool batch, bool fused, Launc
 cudaError_t launch_stage_tc(int p, bool batch, bool fused, const LaunchShape &ls, const StageParams &sp,
                             const Phys<float> &ph, cudaStream_t st);
 // Dr, Ds [Np][Np] and LIFT [Np][NF] (FP64, row-major) -> the kernel's
-// fragment table (TF32 hi / lo pairs, 3 * 2 * 2 * 32 float4)
+// operator table (TF32 hi / lo fragments, 3 * 2 * 2 * 32 float4, then
+// (Dr, Ds) as FP32 pairs [Np][Np])
 void build_tc_fragments(int Np, int NF, const double *Dr, const double *Ds, const double *LIFT,
                         std::vector<float> &out);
 // FP32 copy [K][Np] float4 and FP64-recovered pressure [K][NpP] of a state

@@ -122,11 +122,12 @@ cudaError_t launch_stage_tc(int p, bool batch, bool fused, const LaunchShape &ls
 // kernel reads them: [matrix][k-step][hi, lo][lane][a0..a3] with lane = 4 g + t,
 // a0 = A[g][8 ks + t], a1 = A[g + 8][8 ks + t], a2 = A[g][8 ks + t + 4],
 // a3 = A[g + 8][8 ks + t + 4].  hi is the FP64 entry rounded to FP32 and
-// then to TF32; lo is the remainder rounded the same way.
+// then to TF32; lo is the remainder rounded the same way.  Followed by
+// (Dr, Ds) in FP32 as interleaved pairs, row-major (the face-node rows).
 void build_tc_fragments(int Np, int NF, const double *Dr, const double *Ds, const double *LIFT,
                         std::vector<float> &out)
 {
-    out.assign(static_cast<size_t>(TC_FRAG_FLOAT4) * 4, 0.0f);
+    out.assign(static_cast<size_t>(TC_FRAG_FLOAT4) * 4 + 2 * static_cast<size_t>(Np) * Np, 0.0f);
     auto entry = [&](int m, int row, int col) -> double {
         if (row >= Np) return 0.0;
         if (m < 2) return (col < Np) ? (m == 0 ? Dr : Ds)[row * Np + col] : 0.0;
@@ -146,6 +147,12 @@ void build_tc_fragments(int Np, int NF, const double *Dr, const double *Ds, cons
                     out[((((m * 2 + ks) * 2 + 1) * 32 + lane) * 4) + a] = lo;
                 }
             }
+    // then (Dr, Ds) pairs in FP32, row-major
+    float *d = out.data() + static_cast<size_t>(TC_FRAG_FLOAT4) * 4;
+    for (int i = 0; i < Np * Np; ++i) {
+        d[2 * i] = static_cast<float>(Dr[i]);
+        d[2 * i + 1] = static_cast<float>(Ds[i]);
+    }
 }
 
 }  // namespace dg
