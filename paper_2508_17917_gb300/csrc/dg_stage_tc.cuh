@@ -130,23 +130,22 @@ __device__ __forceinline__ void frag_to_node(const float c[4], float v[4], int l
 
 // Broken gradient of one 8-column tile: ur = Dr B, us = Ds B for B given as
 // this lane's four B values (k = t, t + 4, t + 8, t + 12), returned as the
-// four fields of this lane's node.  Four independent accumulator pairs.
+// four fields of this lane's node.  Separate accumulators for the large
+// products and the corrections of each operator.
 __device__ __forceinline__ void grad_mma(const float4 ah[2][2], const float4 al[2][2], const float b[4], int lane,
                                          float ur[4], float us[4])
 {
     float r0[4] = {0.f, 0.f, 0.f, 0.f}, r1[4] = {0.f, 0.f, 0.f, 0.f};
-    float r2[4] = {0.f, 0.f, 0.f, 0.f}, r3[4] = {0.f, 0.f, 0.f, 0.f};
     float s0[4] = {0.f, 0.f, 0.f, 0.f}, s1[4] = {0.f, 0.f, 0.f, 0.f};
-    float s2[4] = {0.f, 0.f, 0.f, 0.f}, s3[4] = {0.f, 0.f, 0.f, 0.f};
     mma3(r0, r1, ah[0][0], al[0][0], b[0], b[1]);
     mma3(s0, s1, ah[1][0], al[1][0], b[0], b[1]);
-    mma3(r2, r3, ah[0][1], al[0][1], b[2], b[3]);
-    mma3(s2, s3, ah[1][1], al[1][1], b[2], b[3]);
+    mma3(r0, r1, ah[0][1], al[0][1], b[2], b[3]);
+    mma3(s0, s1, ah[1][1], al[1][1], b[2], b[3]);
     float cr[4], cs[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        cr[c] = (r0[c] + r2[c]) + (r1[c] + r3[c]);
-        cs[c] = (s0[c] + s2[c]) + (s1[c] + s3[c]);
+        cr[c] = r0[c] + r1[c];
+        cs[c] = s0[c] + s1[c];
     }
     frag_to_node(cr, ur, lane);
     frag_to_node(cs, us, lane);
@@ -464,20 +463,19 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
                     bs[q] = (k < Np) ? fb[8 * k + 4 + bc] - s0 : 0.f;
                     bh[q] = (k < NF) ? hb[4 * k + bc] : 0.f;
                 }
-                // four independent accumulators: divergence (Dr / Ds halves)
-                // and lift (two k-steps), each with its corrections
+                // divergence and lift, each with separate accumulators for
+                // the large products and the corrections
                 float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
-                float d2[4] = {0.f, 0.f, 0.f, 0.f}, d3[4] = {0.f, 0.f, 0.f, 0.f};
                 float l0[4] = {0.f, 0.f, 0.f, 0.f}, l1[4] = {0.f, 0.f, 0.f, 0.f};
                 mma3(d0, d1, ah[0][0], al[0][0], br[0], br[1]);
-                mma3(d2, d3, ah[1][0], al[1][0], bs[0], bs[1]);
                 mma3(l0, l1, lh[0], ll[0], bh[0], bh[1]);
-                mma3(d0, d1, ah[0][1], al[0][1], br[2], br[3]);
-                mma3(d2, d3, ah[1][1], al[1][1], bs[2], bs[3]);
+                mma3(d0, d1, ah[1][0], al[1][0], bs[0], bs[1]);
                 mma3(l0, l1, lh[1], ll[1], bh[2], bh[3]);
+                mma3(d0, d1, ah[0][1], al[0][1], br[2], br[3]);
+                mma3(d0, d1, ah[1][1], al[1][1], bs[2], bs[3]);
                 float cd[4];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) cd[c] = (l0[c] + l1[c]) - ((d0[c] + d2[c]) + (d1[c] + d3[c]));
+                for (int c = 0; c < 4; ++c) cd[c] = (l0[c] + l1[c]) - (d0[c] + d1[c]);
                 float R[4];
                 frag_to_node(cd, R, lane);
                 const int e = 2 * nt + ep;
