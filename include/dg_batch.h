@@ -77,9 +77,10 @@ const char *dg_batch_last_error(const dg_batch *b);
 int64_t dg_batch_kernel_launches(const dg_batch *b);
 
 /* Tile shape of the stage kernel per degree group (see dg_set_stage_variant):
- * 0 = time both shapes per group at the next dg_batch_run (the default),
- * 1 or 2 = forced for every group.  Drops captured graphs.
- * Errors: DG_EINVAL. */
+ * 0 = time every available shape per group at the next dg_batch_run (the
+ * default), 1 or 2 = forced for every group, 3 = the tensor-core shape for
+ * the groups of p <= 4 and the two-node shape for the others.  Drops
+ * captured graphs.  Errors: DG_EINVAL. */
 dg_status dg_batch_set_stage_variant(dg_batch *b, int variant);
 
 /* Fused steps for the batch: on != 0 replaces the five stage launches of
@@ -89,7 +90,7 @@ dg_status dg_batch_set_stage_variant(dg_batch *b, int variant);
  * graphs.  Errors: DG_EINVAL, DG_ECUDA. */
 dg_status dg_batch_set_fused_steps(dg_batch *b, int on);
 
-/* The tile shape the group of case i uses (1 or 2); 0 for a bad argument. */
+/* The tile shape the group of case i uses (1, 2 or 3); 0 for a bad argument. */
 int dg_batch_stage_variant(const dg_batch *b, int i);
 
 /* The cudaStream_t the batch runs on (for events a caller records around

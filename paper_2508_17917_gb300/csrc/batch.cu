@@ -36,8 +36,10 @@ struct Group {
     long long lam_base = 0;          // first entry in the batch's Lambda_K array
     int wall_base = 0;               // first entry in the batch's wall partials
     int nwall = 0;
-    long long ntiles = 0, ntiles2 = 0;
+    long long ntiles = 0, ntiles2 = 0, ntiles3 = 0;
     dg::LaunchShape shape, shape2;   // one / two nodes per thread
+    dg::LaunchShape shape3;          // tensor-core warp tiles (p <= 4)
+    bool has_tc = false;
     int variant = 1;
     dg::LaunchShape fshape;          // fused steps: cooperative launch of the chosen shape
     int fshape_variant = 0;
@@ -45,7 +47,8 @@ struct Group {
     DevBuf<double> K0a, K0b, K1, geo64, Dr64, Ds64, wface, fxy;
     DevBuf<float> geo32, ops32, P0a, P0b;
     DevBuf<float4> S0a, S0b;
-    DevBuf<int4> conn, tiles, tiles2;
+    DevBuf<int4> conn, tiles, tiles2, tiles3;
+    DevBuf<float> tcfrag;            // operator table of the tensor-core shape
     DevBuf<int> fmask, elem_case;
     DevBuf<int2> walls;
 };
@@ -219,10 +222,14 @@ dg_status enqueue_step(dg_batch *b, double cfl, double *hist, int rows)
             sp.cases = b->dcases.ptr;
             if (b->fused) {
                 // the five stages in one cooperative launch (grid barriers between stages)
-                sp.tiles = (g.variant == 2) ? g.tiles2.ptr : g.tiles.ptr;
-                sp.ntiles = (g.variant == 2) ? g.ntiles2 : g.ntiles;
+                sp.tiles = (g.variant == 3) ? g.tiles3.ptr : (g.variant == 2) ? g.tiles2.ptr : g.tiles.ptr;
+                sp.ntiles = (g.variant == 3) ? g.ntiles3 : (g.variant == 2) ? g.ntiles2 : g.ntiles;
+                if (g.variant == 3) sp.ops = g.tcfrag.ptr;
                 if (g.fshape_variant != g.variant) {
-                    B_CUDA(b, dg::stage_shape_mixed_fused(g.p, g.variant, true, sp.ntiles, g.fshape));
+                    if (g.variant == 3)
+                        B_CUDA(b, dg::stage_shape_tc(g.p, sp.ntiles, true, true, g.fshape));
+                    else
+                        B_CUDA(b, dg::stage_shape_mixed_fused(g.p, g.variant, true, sp.ntiles, g.fshape));
                     g.fshape_variant = g.variant;
                 }
                 for (int i = 0; i < 5; ++i) {
@@ -233,7 +240,15 @@ dg_status enqueue_step(dg_batch *b, double cfl, double *hist, int rows)
                 sp.bar_err = b->bar_err.ptr;
                 sp.bar_limit = b->bar_limit;
                 B_CUDA(b, cudaMemsetAsync(g.bar.ptr, 0, 2 * sizeof(unsigned), b->stream));
-                B_CUDA(b, dg::launch_stage_mixed_fused(g.p, true, g.fshape, sp, ph32, b->stream));
+                if (g.variant == 3)
+                    B_CUDA(b, dg::launch_stage_tc(g.p, true, true, g.fshape, sp, ph32, b->stream));
+                else
+                    B_CUDA(b, dg::launch_stage_mixed_fused(g.p, true, g.fshape, sp, ph32, b->stream));
+            } else if (g.variant == 3) {
+                sp.tiles = g.tiles3.ptr;
+                sp.ntiles = g.ntiles3;
+                sp.ops = g.tcfrag.ptr;
+                B_CUDA(b, dg::launch_stage_tc(g.p, true, false, g.shape3, sp, ph32, b->stream));
             } else if (g.variant == 2) {
                 sp.tiles = g.tiles2.ptr;
                 sp.ntiles = g.ntiles2;
@@ -256,8 +271,9 @@ dg_status enqueue_step(dg_batch *b, double cfl, double *hist, int rows)
     return DG_OK;
 }
 
-// First run: per degree group, time both stage-kernel shapes on the current
-// states in residual-only launches (into a scratch array) and keep the faster.
+// First run: per degree group, time every available stage-kernel shape on
+// the current states in residual-only launches (into a scratch array) and
+// keep the fastest.
 dg_status tune_groups(dg_batch *b)
 {
     if (b->tuned) return DG_OK;
@@ -267,13 +283,15 @@ dg_status tune_groups(dg_batch *b)
     B_CUDA(b, cudaEventCreate(&e1));
     for (auto &g : b->groups) {
         if (b->variant_req != 0) {
-            g.variant = b->variant_req;
+            // the tensor-core shape covers p <= 4; other groups take the two-node shape
+            g.variant = (b->variant_req == 3 && !g.has_tc) ? 2 : b->variant_req;
             continue;
         }
         DevBuf<double> scratch;
         B_CUDA(b, scratch.alloc(static_cast<size_t>(g.K) * 4 * g.ops.Np));
         float best = 0.f;
-        for (int v = 1; v <= 2; ++v) {
+        for (int v = 1; v <= 3; ++v) {
+            if (v == 3 && !g.has_tc) continue;
             dg::StageParams sp{};
             const bool a = b->cur_is_a;
             sp.K0in = a ? g.K0a.ptr : g.K0b.ptr;
@@ -294,7 +312,12 @@ dg_status tune_groups(dg_batch *b)
             float ms = 0.f;
             for (int rep = 0; rep < 5; ++rep) {
                 if (rep == 2) B_CUDA(b, cudaEventRecord(e0, b->stream));
-                if (v == 2) {
+                if (v == 3) {
+                    sp.tiles = g.tiles3.ptr;
+                    sp.ntiles = g.ntiles3;
+                    sp.ops = g.tcfrag.ptr;
+                    B_CUDA(b, dg::launch_stage_tc(g.p, true, false, g.shape3, sp, ph32, b->stream));
+                } else if (v == 2) {
                     sp.tiles = g.tiles2.ptr;
                     sp.ntiles = g.ntiles2;
                     B_CUDA(b, dg::launch_stage_mixed2(g.p, true, g.shape2, sp, ph32, b->stream));
@@ -379,12 +402,12 @@ dg_status dg_batch_create(const dg_params *common, int ncases, const dg_case *ca
         g.p = degrees[gi];
         if (!dg::build_reference_operators(g.p, g.ops)) return bail(DG_EINVAL);
         const int Np = g.ops.Np, Nfp = g.ops.Nfp, NF = 3 * Nfp;
-        const int E = dg::stage_tile_elems(g.p), E2 = dg::stage_tile_elems2(g.p);
+        const int E = dg::stage_tile_elems(g.p), E2 = dg::stage_tile_elems2(g.p), E3 = dg::stage_tile_elems_tc();
         std::vector<double> geo;
         std::vector<int4> conn;
         std::vector<int2> walls;
         std::vector<double> wxy;
-        std::vector<int4> tiles, tiles2;
+        std::vector<int4> tiles, tiles2, tiles3;
         std::vector<int> ecase;
         g.lam_base = lam_total;
         g.wall_base = wall_total;
@@ -425,6 +448,9 @@ dg_status dg_batch_create(const dg_params *common, int ncases, const dg_case *ca
             for (long long k0 = 0; k0 < c.K; k0 += E2)
                 tiles2.push_back(make_int4(static_cast<int>(off + k0),
                                            static_cast<int>(std::min<long long>(E2, c.K - k0)), i, 0));
+            for (long long k0 = 0; k0 < c.K; k0 += E3)
+                tiles3.push_back(make_int4(static_cast<int>(off + k0),
+                                           static_cast<int>(std::min<long long>(E3, c.K - k0)), i, 0));
             ecase.insert(ecase.end(), static_cast<size_t>(c.K), i);
             g.K += c.K;
             dg::BatchCase &bc = b->init[i];
@@ -440,6 +466,8 @@ dg_status dg_batch_create(const dg_params *common, int ncases, const dg_case *ca
         g.nwall = static_cast<int>(walls.size());
         g.ntiles = static_cast<long long>(tiles.size());
         g.ntiles2 = static_cast<long long>(tiles2.size());
+        g.ntiles3 = static_cast<long long>(tiles3.size());
+        g.has_tc = dg::stage_tc_supported(g.p);
         lam_total += g.K;
         wall_total += g.nwall;
         const size_t nd = static_cast<size_t>(g.K) * 4 * Np;
@@ -464,6 +492,12 @@ dg_status dg_batch_create(const dg_params *common, int ncases, const dg_case *ca
         chk(g.conn.alloc(conn.size()));
         chk(g.tiles.alloc(tiles.size()));
         chk(g.tiles2.alloc(tiles2.size()));
+        chk(g.tiles3.alloc(tiles3.size()));
+        std::vector<float> frag;
+        if (g.has_tc) {
+            dg::build_tc_fragments(Np, NF, g.ops.Dr.data(), g.ops.Ds.data(), g.ops.LIFT.data(), frag);
+            chk(g.tcfrag.alloc(frag.size()));
+        }
         chk(g.elem_case.alloc(ecase.size()));
         chk(g.ops32.alloc(o32.size()));
         chk(g.Dr64.alloc(static_cast<size_t>(Np) * Np));
@@ -480,6 +514,8 @@ dg_status dg_batch_create(const dg_params *common, int ncases, const dg_case *ca
         chk(cudaMemcpy(g.conn.ptr, conn.data(), conn.size() * sizeof(int4), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(g.tiles.ptr, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(g.tiles2.ptr, tiles2.data(), tiles2.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(g.tiles3.ptr, tiles3.data(), tiles3.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        if (g.has_tc) chk(cudaMemcpy(g.tcfrag.ptr, frag.data(), frag.size() * sizeof(float), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(g.elem_case.ptr, ecase.data(), ecase.size() * sizeof(int), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(g.ops32.ptr, o32.data(), o32.size() * sizeof(float), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(g.Dr64.ptr, g.ops.Dr.data(), g.ops.Dr.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -499,6 +535,7 @@ dg_status dg_batch_create(const dg_params *common, int ncases, const dg_case *ca
         chk(cudaMemset(g.P0b.ptr, 0, npp * sizeof(float)));
         chk(dg::stage_shape_mixed_batch(g.p, g.ntiles, g.shape));
         chk(dg::stage_shape_mixed2(g.p, g.ntiles2, true, g.shape2));
+        if (g.has_tc) chk(dg::stage_shape_tc(g.p, g.ntiles3, true, false, g.shape3));
         if (e != cudaSuccess) return bail(DG_ECUDA);
     }
     cudaError_t e = cudaSuccess;
@@ -534,7 +571,7 @@ dg_status dg_batch_set_stage_variant(dg_batch *b, int variant)
 {
     if (!b) return DG_EINVAL;
     b->err.clear();
-    if (variant < 0 || variant > 2) return bfail(b, DG_EINVAL, "variant must be 0, 1 or 2");
+    if (variant < 0 || variant > 3) return bfail(b, DG_EINVAL, "variant must be 0, 1, 2 or 3");
     b->variant_req = variant;
     b->tuned = false;
     b->drop_graphs();

@@ -6,7 +6,7 @@
 // state, pressure recovery and registers.  What changes is how the work is
 // laid out:
 //
-// * Every warp owns a tile of WE = 4 elements from load to store.  It stages
+// * Every warp owns a tile of WE = 2 elements from load to store.  It stages
 //   its own inputs with cp.async and synchronises with __syncwarp only, so the
 //   warps of a block run independently (no block barrier in the loop).
 // * The contractions -- broken gradient [Dr; Ds] U, divergence Dr Fr + Ds Fs

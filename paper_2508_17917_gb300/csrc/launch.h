@@ -78,6 +78,8 @@ int stage_tile_elems(int p);
 // the tensor-core mixed IIP kernel (p = 1..4): warp tiles of 4 elements;
 // its `ops` is the fragment table of build_tc_fragments
 bool stage_tc_supported(int p);
+// elements per warp tile of the tensor-core kernel (any p)
+int stage_tile_elems_tc();
 // units = K elements (single mesh) or the tile count of a batch tile table;
 // fused: five stages per cooperative launch with grid barriers
 cudaError_t stage_shape_tc(int p, long long units, bool batch, bool fused, LaunchShape &out);

@@ -95,6 +95,8 @@ float tf32_round(float x)
 
 bool stage_tc_supported(int p) { return p >= 1 && p <= 4; }
 
+int stage_tile_elems_tc() { return ShapeTC<1>::WE; }
+
 cudaError_t stage_shape_tc(int p, long long units, bool batch, bool fused, LaunchShape &out)
 {
     switch (p) {

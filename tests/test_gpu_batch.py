@@ -88,7 +88,8 @@ def rel_err(got, ref):
 
 # (launch mode, tile shape; 0 = tuned); "fused": one cooperative launch per
 # degree group and step, replayed from the graph
-RUNS = [("graph", 1), ("plain", 1), ("graph", 2), ("graph", 0), ("fused", 1), ("fused", 2)]
+RUNS = [("graph", 1), ("plain", 1), ("graph", 2), ("graph", 3), ("graph", 0), ("fused", 1), ("fused", 2),
+        ("fused", 3)]
 
 
 @pytest.fixture(scope="module")
@@ -125,12 +126,16 @@ def test_batch_graph_replay_is_bit_identical(small_run):
     assert np.array_equal(rg, rp)
 
 
-@pytest.mark.parametrize("run", [("graph", 1), ("graph", 2), ("graph", 0), ("fused", 2)])
+@pytest.mark.parametrize("run", [("graph", 1), ("graph", 2), ("graph", 3), ("graph", 0), ("fused", 2),
+                                 ("fused", 3)])
 @pytest.mark.parametrize("i", range(len(SMALL)))
 def test_batch_case_matches_oracle_loop(small_run, i, run):
     cases, states, nsteps, res = small_run
     hist, Us, rigid, _, variants = res[run]
-    assert variants[i] == (run[1] or variants[i]) and variants[i] in (1, 2)
+    # a forced tensor-core shape applies to the groups of p <= 4, the others
+    # take the two-node shape
+    want = run[1] if (run[1] != 3 or cases[i]["p"] <= 4) else 2
+    assert variants[i] == (want or variants[i]) and variants[i] in (1, 2, 3)
     ref, U_ref, P = oracle_loop(cases[i], states[i], nsteps)
     got = hist[:, i, :]
     # dt from the mixed-path state: FP32 bound of a state that differs at the 1e-6 level
@@ -147,7 +152,7 @@ def test_batch_case_matches_oracle_loop(small_run, i, run):
     assert rigid[i, 9] == 0
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_batch_fused_matches_five_launches(small_run, variant):
     """Same result as the five stage launches up to the last bit of a
     separately compiled kernel (1e-9 of the largest value)."""
@@ -165,11 +170,12 @@ def test_batch_launch_count(small_run):
     # set_state per case, initial forces (groups + 1), then per step: dt per group,
     # dt reduce, Newmark, 5 stages per group, forces per group, force sum, record;
     # the tuned run adds five residual-only launches per shape and group
+    # (three shapes at p <= 4, two beyond)
     for run in RUNS:
         stage = groups if run[0] == "fused" else 5 * groups
         per_step = groups + 2 + stage + groups + 1 + 1
         launches = res[run][3]
-        tune = 10 * groups if run[1] == 0 else 0
+        tune = sum(15 if p <= 4 else 10 for p in {c["p"] for c in cases}) if run[1] == 0 else 0
         assert launches == len(cases) + (groups + 1) + tune + nsteps * per_step, (run, launches)
 
 
