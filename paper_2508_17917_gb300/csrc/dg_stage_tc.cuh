@@ -77,8 +77,7 @@ struct TcLayout {
     static constexpr size_t oRaw = oPn + al(4 * 3 * WE * NpP);              // double [WE][4][Np]
     static constexpr size_t oK1 = oRaw + al(8 * WE * 4 * Np);               // double [WE][4][Np]
     static constexpr size_t oF = oK1 + al(8 * WE * 4 * Np);                 // float [WE][FS]: node j: Fr[4], Fs[4]
-    static constexpr size_t oNorm = oF + al(4 * WE * S::FS);                // float [WE][NF]
-    static constexpr size_t oDH = oNorm + al(4 * WE * NF);                  // float [WE][HS]: slot r: Fscale dH[4]
+    static constexpr size_t oDH = oF + al(4 * WE * S::FS);                  // float [WE][HS]: slot r: Fscale dH[4]
     static constexpr size_t warp = oDH + al(4 * WE * S::HS);
     static constexpr size_t bytes = header + S::NW * warp;
 };
@@ -189,7 +188,6 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
     const double *sRaw = reinterpret_cast<const double *>(wb + L::oRaw);
     const double *sK1 = reinterpret_cast<const double *>(wb + L::oK1);
     float *sF = reinterpret_cast<float *>(wb + L::oF);
-    float *sNorm = reinterpret_cast<float *>(wb + L::oNorm);
     float *sDH = reinterpret_cast<float *>(wb + L::oDH);
 
     const float *geo = static_cast<const float *>(sp.geo);
@@ -319,55 +317,50 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
             }
         }
 
-        // ---- N: penalty norms of both traces at every face node
-        for (int q = lane; q < ne * NF; q += 32) {
-            const int e = q / NF, r = q - (q / NF) * NF, f = r / Nfp, i = r - (r / Nfp) * Nfp;
-            const int4 cn = sConn[e];
-            const int f2 = (cn.w >> (2 * f)) & 3, bt = (cn.w >> (8 + 2 * f)) & 3;
-            const float *gg = sGeo + e * 16;
-            const float n1 = gg[G_NX + f], n2 = gg[G_NY + f];
-            const int vm = sFm[f * Nfp + i], vp = sFm[f2 * Nfp + (Nfp - 1 - i)];
-            float u[4];
-            f4_to(sU[e * US + vm], u);
-            const float ir = 1.0f / u[0];
-            const float na = penalty_norm(u[0], u[1] * ir, u[2] * ir, u[3] * ir, n1, n2, ph);
-            float nb;
-            if (bt == BCT_INTERIOR) {
-                float w[4];
-                f4_to(sN[(e * 3 + f) * US + vp], w);
-                const float iw = 1.0f / w[0];
-                nb = penalty_norm(w[0], w[1] * iw, w[2] * iw, w[3] * iw, n1, n2, ph);
-            } else if (bt == BCT_FARFIELD) {
-                const float iw = 1.0f / ph.Uinf[0];
-                nb = penalty_norm(ph.Uinf[0], ph.Uinf[1] * iw, ph.Uinf[2] * iw, ph.Uinf[3] * iw, n1, n2, ph);
-            } else {
-                const float pw = sPo[e * NpP + vm];
-                const float eb = (pw / ph.gm1 + 0.5f * u[0] * (ph.vw1 * ph.vw1 + ph.vw2 * ph.vw2)) * ir;
-                nb = penalty_norm(u[0], ph.vw1, ph.vw2, eb, n1, n2, ph);
-            }
-            sNorm[e * NF + r] = fmaxf(na, nb);
-        }
+        __syncwarp();   // the fluxes of V are read at the face nodes below
 
-        __syncwarp();
-
-        // ---- F: numerical flux minus the own flux at every face node
-        for (int q = lane; q < ne * NF; q += 32) {
+        // ---- F: at every face node (one per lane, the Nfp nodes of a face on
+        // consecutive lanes): penalty norms of both traces, their maximum over
+        // the face, and the numerical flux minus the own flux
+        static_assert(WE * NF <= 32, "one face node per lane");
+        {
+            const bool act = lane < ne * NF;
+            const int q = act ? lane : 0;
             const int e = q / NF, r = q - (q / NF) * NF, f = r / Nfp, i = r - (r / Nfp) * Nfp;
             const int4 cn = sConn[e];
             const int f2 = (cn.w >> (2 * f)) & 3, bt = (cn.w >> (8 + 2 * f)) & 3;
             const float *gg = sGeo + e * 16;
             const float n1 = gg[G_NX + f], n2 = gg[G_NY + f], fsc = gg[G_FS + f];
-            float gbar = 0.f;
-#pragma unroll
-            for (int l = 0; l < Nfp; ++l) gbar = fmaxf(gbar, sNorm[e * NF + f * Nfp + l]);
-            float cinv = cinv_fac * fsc;
-            const float *ng = sNGeo + (e * 3 + f) * 16;
-            if (bt == BCT_INTERIOR) cinv = fmaxf(cinv, cinv_fac * ng[G_FS + f2]);
-            const float sigma = sig_fac * gbar * cinv;
             const int vm = sFm[f * Nfp + i], vp = sFm[f2 * Nfp + (Nfp - 1 - i)];
             float up[4], dH[4], Ftp[4];
             f4_to(sU[e * US + vm], up);
             const float pp = sPo[e * NpP + vm];
+            float nrm;
+            {
+                const float ir = 1.0f / up[0];
+                const float na = penalty_norm(up[0], up[1] * ir, up[2] * ir, up[3] * ir, n1, n2, ph);
+                float nb;
+                if (bt == BCT_INTERIOR) {
+                    float w[4];
+                    f4_to(sN[(e * 3 + f) * US + vp], w);
+                    const float iw = 1.0f / w[0];
+                    nb = penalty_norm(w[0], w[1] * iw, w[2] * iw, w[3] * iw, n1, n2, ph);
+                } else if (bt == BCT_FARFIELD) {
+                    const float iw = 1.0f / ph.Uinf[0];
+                    nb = penalty_norm(ph.Uinf[0], ph.Uinf[1] * iw, ph.Uinf[2] * iw, ph.Uinf[3] * iw, n1, n2, ph);
+                } else {
+                    const float eb = (pp / ph.gm1 + 0.5f * up[0] * (ph.vw1 * ph.vw1 + ph.vw2 * ph.vw2)) * ir;
+                    nb = penalty_norm(up[0], ph.vw1, ph.vw2, eb, n1, n2, ph);
+                }
+                nrm = fmaxf(na, nb);
+            }
+            float gbar = 0.f;
+#pragma unroll
+            for (int l = 0; l < Nfp; ++l) gbar = fmaxf(gbar, __shfl_sync(0xffffffffu, nrm, lane - i + l));
+            float cinv = cinv_fac * fsc;
+            const float *ng = sNGeo + (e * 3 + f) * 16;
+            if (bt == BCT_INTERIOR) cinv = fmaxf(cinv, cinv_fac * ng[G_FS + f2]);
+            const float sigma = sig_fac * gbar * cinv;
             {
                 // F+ . n from the contravariant fluxes: (Fx, Fy) = M^-1 (Fr, Fs)
                 // with M = [[rx, ry], [sx, sy]]
@@ -435,8 +428,9 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) dH[c] = Ftp[c] - (Fnb[c] - vnb[c] + sigma * (up[c] - ub[c]));
             }
-            *reinterpret_cast<float4 *>(sDH + e * HS + r * 4) =
-                make_float4(fsc * dH[0], fsc * dH[1], fsc * dH[2], fsc * dH[3]);
+            if (act)
+                *reinterpret_cast<float4 *>(sDH + e * HS + r * 4) =
+                    make_float4(fsc * dH[0], fsc * dH[1], fsc * dH[2], fsc * dH[3]);
         }
         asm volatile("cp.async.wait_group 0;\n" ::);
         __syncwarp();
