@@ -237,26 +237,21 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
         for (int c = lane; c < ne * (NpP / 4); c += 32)
             cp_async16(wsh + L::oPo + 16u * c, sp.Pin + k0 * NpP + 4 * c);
         for (int c = lane; c < ne * 4; c += 32) cp_async16(wsh + L::oGeo + 16u * c, geo + k0 * 16 + 4 * c);
-        for (int c = lane; c < ne * 3 * Np; c += 32) {
-            const int sl = c / Np, j = c - (c / Np) * Np;
-            const int4 cn = sConn[sl / 3];
-            const int f = sl - 3 * (sl / 3);
-            const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
-            cp_async16(wsh + L::oN + 16u * (sl * US + j), sp.Sin + nb * Np + j);
-        }
-        for (int c = lane; c < ne * 3 * (NpP / 4); c += 32) {
-            const int sl = c / (NpP / 4), qq = c - (c / (NpP / 4)) * (NpP / 4);
-            const int4 cn = sConn[sl / 3];
-            const int f = sl - 3 * (sl / 3);
-            const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
-            cp_async16(wsh + L::oPn + 16u * c, sp.Pin + nb * NpP + 4 * qq);
-        }
-        for (int c = lane; c < ne * 3 * 4; c += 32) {
-            const int sl = c >> 2, qq = c & 3;
-            const int4 cn = sConn[sl / 3];
-            const int f = sl - 3 * (sl / 3);
-            const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
-            cp_async16(wsh + L::oNGeo + 16u * c, geo + nb * 16 + 4 * qq);
+        {
+            // LPS lanes per neighbour slot: one connectivity lookup per lane
+            constexpr int LPS = 32 / (3 * WE);
+            const int sl = lane / LPS, part = lane - (lane / LPS) * LPS;
+            if (sl < 3 * ne) {
+                const int4 cn = sConn[sl / 3];
+                const int f = sl - 3 * (sl / 3);
+                const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
+                for (int j = part; j < Np; j += LPS)
+                    cp_async16(wsh + L::oN + 16u * (sl * US + j), sp.Sin + nb * Np + j);
+                for (int qq = part; qq < NpP / 4; qq += LPS)
+                    cp_async16(wsh + L::oPn + 16u * (sl * (NpP / 4) + qq), sp.Pin + nb * NpP + 4 * qq);
+                for (int qq = part; qq < 4; qq += LPS)
+                    cp_async16(wsh + L::oNGeo + 16u * (sl * 4 + qq), geo + nb * 16 + 4 * qq);
+            }
         }
         asm volatile("cp.async.commit_group;\n" ::);
         // ---- group B: the FP64 registers, needed only by the update
