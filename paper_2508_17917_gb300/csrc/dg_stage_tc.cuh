@@ -46,7 +46,8 @@ struct ShapeTC {
     static constexpr int NW = 4;                  // warps per block
     static constexpr int NT = 32 * NW;
     static constexpr int NpP = (Np + 3) & ~3;     // padded pressure row
-    static constexpr int US = 20;                 // float4 records per staged element (bank spread)
+    static constexpr int US = 20;                 // float4 records per staged element (bank spread of B loads)
+    static constexpr int UN = 21;                 // float4 records per neighbour slot (bank spread of face reads)
     static constexpr int FS = 132;                // floats per element of the flux table
     static constexpr int HS = 80;                 // floats per element of the dH table
 };
@@ -71,8 +72,8 @@ struct TcLayout {
     static constexpr size_t oGeo = oConn + al(16 * WE);                     // float [WE][16]
     static constexpr size_t oNGeo = oGeo + al(64 * WE);                     // float [3 WE][16]
     static constexpr size_t oU = oNGeo + al(64 * 3 * WE);                   // float4 [WE][US]
-    static constexpr size_t oN = oU + al(16 * WE * S::US);                  // float4 [3 WE][US]
-    static constexpr size_t oPo = oN + al(16 * 3 * WE * S::US);             // float [WE][NpP]
+    static constexpr size_t oN = oU + al(16 * WE * S::US);                  // float4 [3 WE][UN]
+    static constexpr size_t oPo = oN + al(16 * 3 * WE * S::UN);             // float [WE][NpP]
     static constexpr size_t oPn = oPo + al(4 * WE * NpP);                   // float [3 WE][NpP]
     static constexpr size_t oRaw = oPn + al(4 * 3 * WE * NpP);              // double [WE][4][Np]
     static constexpr size_t oK1 = oRaw + al(8 * WE * 4 * Np);               // double [WE][4][Np]
@@ -157,7 +158,7 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
     using S = ShapeTC<P>;
     using L = TcLayout<P>;
     constexpr int Np = S::Np, Nfp = S::Nfp, NF = S::NF, WE = S::WE, NpP = S::NpP;
-    constexpr int US = S::US, FS = S::FS, HS = S::HS;
+    constexpr int US = S::US, UN = S::UN, FS = S::FS, HS = S::HS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const float4 *sFrag = reinterpret_cast<const float4 *>(smem_raw + L::hFrag);
     int *sFm = reinterpret_cast<int *>(smem_raw + L::hFm);
@@ -246,7 +247,7 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
                 const int f = sl - 3 * (sl / 3);
                 const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
                 for (int j = part; j < Np; j += LPS)
-                    cp_async16(wsh + L::oN + 16u * (sl * US + j), sp.Sin + nb * Np + j);
+                    cp_async16(wsh + L::oN + 16u * (sl * UN + j), sp.Sin + nb * Np + j);
                 for (int qq = part; qq < NpP / 4; qq += LPS)
                     cp_async16(wsh + L::oPn + 16u * (sl * (NpP / 4) + qq), sp.Pin + nb * NpP + 4 * qq);
                 for (int qq = part; qq < 4; qq += LPS)
@@ -337,7 +338,7 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
                 float nb;
                 if (bt == BCT_INTERIOR) {
                     float w[4];
-                    f4_to(sN[(e * 3 + f) * US + vp], w);
+                    f4_to(sN[(e * 3 + f) * UN + vp], w);
                     const float iw = 1.0f / w[0];
                     nb = penalty_norm(w[0], w[1] * iw, w[2] * iw, w[3] * iw, n1, n2, ph);
                 } else if (bt == BCT_FARFIELD) {
@@ -374,7 +375,7 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
             // face's slot holds the element itself
             float go_x[4] = {0.f, 0.f, 0.f, 0.f}, go_y[4] = {0.f, 0.f, 0.f, 0.f};
             if (bt != BCT_FARFIELD) {
-                const float4 *src = sN + (e * 3 + f) * US;
+                const float4 *src = sN + (e * 3 + f) * UN;
                 const int row = (bt == BCT_INTERIOR) ? vp : vm;
                 float wr[4] = {0.f, 0.f, 0.f, 0.f}, ws[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -388,7 +389,7 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
             if (bt == BCT_INTERIOR) {
                 float um[4];
                 const float *gxm = go_x, *gym = go_y;
-                f4_to(sN[(e * 3 + f) * US + vp], um);
+                f4_to(sN[(e * 3 + f) * UN + vp], um);
                 const float pm = sPn[(e * 3 + f) * NpP + vp];
                 float Fnm[4], vxm[4], vym[4], D[4];
                 flux_n(um, pm, n1, n2, ph, Fnm);
