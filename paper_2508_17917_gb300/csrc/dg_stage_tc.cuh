@@ -152,7 +152,7 @@ __device__ __forceinline__ void grad_mma(const float4 ah[2][2], const float4 al[
 }
 
 template <int P, bool BATCH = false, bool FUSE = false>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, FUSE ? 4 : 5)
 stage_tc_kernel(StageParams sp, Phys<float> ph)
 {
     using S = ShapeTC<P>;
