@@ -106,11 +106,11 @@ dg_status dg_set_mesh(dg_ctx *ctx, int64_t Nv, const double *vx, const double *v
  * 2 = two volume nodes and two face nodes of one face per thread (128
  * threads), 3 = one warp per tile of 4 elements with the Dr / Ds / LIFT
  * products on the tensor cores (mma.sync TF32, three products of split
- * operands, about 2^-21 relative; p <= 4 only), 0 = time every available
+ * operands, about 2^-21 relative; p <= 6), 0 = time every available
  * shape (residual-only launches on the current state) at the first time step
  * after a mesh upload and keep the fastest (the default).  Other paths have
  * one kernel and accept 0 and 1.  Errors: DG_EINVAL (variant outside 0..3),
- * DG_EUNSUPPORTED (2 or 3 on the FP64 or theta != 0 path, 3 with p > 4). */
+ * DG_EUNSUPPORTED (2 or 3 on the FP64 or theta != 0 path). */
 dg_status dg_set_stage_variant(dg_ctx *ctx, int variant);
 
 /* The tile shape in use: 1, 2 or 3 (the single-node kernel until tuned). */

@@ -376,7 +376,7 @@ class Solver:
 
     def set_variant(self, v):
         """Stage-kernel tile shape: 0 = tuned on first step, 1, 2 or 3 forced
-        (3: tensor-core warp tiles, p <= 4)."""
+        (3: tensor-core warp tiles)."""
         dg_set_stage_variant(self.ctx, v)
 
     @property

@@ -38,7 +38,7 @@ struct Group {
     int nwall = 0;
     long long ntiles = 0, ntiles2 = 0, ntiles3 = 0;
     dg::LaunchShape shape, shape2;   // one / two nodes per thread
-    dg::LaunchShape shape3;          // tensor-core warp tiles (p <= 4)
+    dg::LaunchShape shape3;          // tensor-core warp tiles (p <= 6)
     bool has_tc = false;
     int variant = 1;
     dg::LaunchShape fshape;          // fused steps: cooperative launch of the chosen shape
@@ -283,7 +283,7 @@ dg_status tune_groups(dg_batch *b)
     B_CUDA(b, cudaEventCreate(&e1));
     for (auto &g : b->groups) {
         if (b->variant_req != 0) {
-            // the tensor-core shape covers p <= 4; other groups take the two-node shape
+            // the tensor-core shape covers p <= 6; other groups would take the two-node shape
             g.variant = (b->variant_req == 3 && !g.has_tc) ? 2 : b->variant_req;
             continue;
         }

@@ -52,7 +52,7 @@ struct dg_ctx {
     bool cur_is_a = true;
     dg::LaunchShape shape;    // stage kernel in use
     dg::LaunchShape shape1, shape2;   // mixed IIP: one / two nodes per thread
-    dg::LaunchShape shape3;           // mixed IIP, p <= 4: tensor-core warp tiles
+    dg::LaunchShape shape3;           // mixed IIP, p <= 6: tensor-core warp tiles
     bool has_tc = false;              // shape3 is configured for the current mesh
     dg::DevBuf<float> tcfrag;         // operator fragments of the tensor-core kernel
     int variant_req = 0;      // 0: pick by timing on first use, 1, 2 or 3: forced
@@ -383,7 +383,7 @@ dg_status dg_set_stage_variant(dg_ctx *c, int variant)
     if (variant >= 2 && (c->prm.precision != DG_PRECISION_MIXED || c->prm.theta != 0.0))
         return fail(c, DG_EUNSUPPORTED, "the two-node and tensor-core kernels are mixed-precision IIP kernels");
     if (variant == 3 && !dg::stage_tc_supported(c->prm.p))
-        return fail(c, DG_EUNSUPPORTED, "the tensor-core kernel covers p <= 4");
+        return fail(c, DG_EUNSUPPORTED, "the tensor-core kernel covers p <= 6");
     c->variant_req = variant;
     c->tuned = (variant != 0);
     if (c->K > 0 && c->prm.precision == DG_PRECISION_MIXED && c->prm.theta == 0.0)

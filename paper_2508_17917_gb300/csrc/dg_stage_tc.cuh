@@ -32,7 +32,9 @@
 //   C (16 x 8): c0 = C[g][2t], c1 = C[g][2t+1], c2 = C[g+8][2t], c3 = C[g+8][2t+1]
 // Rows are nodes, columns (element of the pair, field): column n = 4 e + c.
 // After a shuffle with lane ^ 1 every lane holds all four fields of one node:
-// node g + 8 (lane & 1) of element (lane >> 1) & 1 of the pair.
+// node g + 8 (lane & 1) of element (lane >> 1) & 1 of the pair.  For p = 5
+// and 6 (Np = 21, 28) the node rows span two 16-row tiles (MT = 2), so a lane
+// holds one node per tile, and the contractions take up to four k-steps.
 #pragma once
 #include "dg_stage_mixed.cuh"
 
@@ -41,30 +43,39 @@ namespace dg {
 template <int P>
 struct ShapeTC {
     static constexpr int Np = (P + 1) * (P + 2) / 2, Nfp = P + 1, NF = 3 * Nfp;
-    static_assert(Np <= 16 && NF <= 16, "one 16-row MMA tile per operator: p <= 4");
+    static_assert(Np <= 32 && NF <= 32, "at most two 16-row MMA tiles per operator: p <= 6");
+    static constexpr int MT = (Np + 15) / 16;     // 16-row tiles of nodes
+    static constexpr int KD = (Np + 7) / 8;       // k-steps over the nodes (Dr, Ds)
+    static constexpr int KL = (NF + 7) / 8;       // k-steps over the face nodes (LIFT)
     static constexpr int WE = 2;                  // elements per warp tile
+    static constexpr int EPP = (32 / NF < WE) ? 32 / NF : WE;   // elements per face-node pass
     static constexpr int NW = 4;                  // warps per block
     static constexpr int NT = 32 * NW;
     static constexpr int NpP = (Np + 3) & ~3;     // padded pressure row
-    static constexpr int US = 20;                 // float4 records per staged element (bank spread of B loads)
-    static constexpr int UN = 21;                 // float4 records per neighbour slot (bank spread of face reads)
-    static constexpr int FS = 132;                // floats per element of the flux table
-    static constexpr int HS = 80;                 // floats per element of the dH table
+    // float4 records per staged element / neighbour slot, and floats per
+    // element of the flux and dH tables: sizes chosen so that the lanes of
+    // a B-fragment load, and the face-node reads of the six slots, fall in
+    // distinct shared-memory banks
+    static constexpr int US = Np + ((12 - Np % 8) % 8);          // >= Np, = 4 mod 8
+    static constexpr int UN = Np + ((13 - Np % 8) % 8);          // >= Np, = 5 mod 8
+    static constexpr int FS = 128 * MT + 4;       // = 4 mod 32
+    static constexpr int HS = 32 * KL + 16;       // = 16 mod 32
+    // operator fragments: Dr and Ds [MT][KD], LIFT [MT][KL], each [hi, lo][lane]
+    static constexpr int NFRAG = (2 * MT * KD + MT * KL) * 64;   // float4
+    static constexpr bool FRAG_SMEM = MT == 1;    // staged in shared memory (else read through L1)
 };
 
-// operator table: the MMA fragments [matrix: Dr, Ds, LIFT][k-step][hi, lo][lane]
-// (float4), then (Dr, Ds) in FP32 as float2 [Np][Np] for the face-node
-// gradients of the neighbours
-constexpr int TC_FRAG_FLOAT4 = 3 * 2 * 2 * 32;
-
+// operator table: the MMA fragments (ShapeTC<P>::NFRAG float4), then
+// (Dr, Ds) in FP32 as float2 [Np][Np] for the face-node gradients of the
+// neighbours
 template <int P>
 struct TcLayout {
     using S = ShapeTC<P>;
     static constexpr int Np = S::Np, NF = S::NF, WE = S::WE, NpP = S::NpP;
     static constexpr size_t al(size_t b) { return (b + 15) & ~size_t(15); }
     // block header
-    static constexpr size_t hFrag = 0;                                      // float4 [TC_FRAG_FLOAT4]
-    static constexpr size_t hFm = hFrag + sizeof(float4) * TC_FRAG_FLOAT4;  // int [NF]
+    static constexpr size_t hFrag = 0;                                      // float4 [NFRAG] if FRAG_SMEM
+    static constexpr size_t hFm = hFrag + (S::FRAG_SMEM ? sizeof(float4) * S::NFRAG : 0);   // int [NF]
     static constexpr size_t hD = hFm + al(sizeof(int) * NF);                // float2 [Np][Np]: (Dr, Ds)
     static constexpr size_t header = hD + al(sizeof(float2) * Np * Np);
     // one region per warp
@@ -128,54 +139,43 @@ __device__ __forceinline__ void frag_to_node(const float c[4], float v[4], int l
     v[3] = odd ? c[3] : ry;
 }
 
-// Broken gradient of one 8-column tile: ur = Dr B, us = Ds B for B given as
-// this lane's four B values (k = t, t + 4, t + 8, t + 12), returned as the
-// four fields of this lane's node.  Separate accumulators for the large
-// products and the corrections of each operator.
-__device__ __forceinline__ void grad_mma(const float4 ah[2][2], const float4 al[2][2], const float b[4], int lane,
-                                         float ur[4], float us[4])
-{
-    float r0[4] = {0.f, 0.f, 0.f, 0.f}, r1[4] = {0.f, 0.f, 0.f, 0.f};
-    float s0[4] = {0.f, 0.f, 0.f, 0.f}, s1[4] = {0.f, 0.f, 0.f, 0.f};
-    mma3(r0, r1, ah[0][0], al[0][0], b[0], b[1]);
-    mma3(s0, s1, ah[1][0], al[1][0], b[0], b[1]);
-    mma3(r0, r1, ah[0][1], al[0][1], b[2], b[3]);
-    mma3(s0, s1, ah[1][1], al[1][1], b[2], b[3]);
-    float cr[4], cs[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        cr[c] = r0[c] + r1[c];
-        cs[c] = s0[c] + s1[c];
-    }
-    frag_to_node(cr, ur, lane);
-    frag_to_node(cs, us, lane);
-}
-
 template <int P, bool BATCH = false, bool FUSE = false>
-__global__ void __launch_bounds__(128, FUSE ? 4 : 5)
+__global__ void __launch_bounds__(128, (FUSE || ShapeTC<P>::MT > 1) ? 4 : 5)
 stage_tc_kernel(StageParams sp, Phys<float> ph)
 {
     using S = ShapeTC<P>;
     using L = TcLayout<P>;
     constexpr int Np = S::Np, Nfp = S::Nfp, NF = S::NF, WE = S::WE, NpP = S::NpP;
     constexpr int US = S::US, UN = S::UN, FS = S::FS, HS = S::HS;
+    constexpr int MT = S::MT, KD = S::KD, KL = S::KL, EPP = S::EPP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const float4 *gFrag = static_cast<const float4 *>(sp.ops);
     const float4 *sFrag = reinterpret_cast<const float4 *>(smem_raw + L::hFrag);
     int *sFm = reinterpret_cast<int *>(smem_raw + L::hFm);
     const float2 *sD = reinterpret_cast<const float2 *>(smem_raw + L::hD);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     {
-        // operator fragments (built on the host in fragment order), face node tables
-        const float4 *tab = static_cast<const float4 *>(sp.ops);
+        // operator fragments (built on the host in fragment order), (Dr, Ds)
+        // rows, face node table
         float4 *dst = reinterpret_cast<float4 *>(smem_raw + L::hFrag);
-        for (int i = tid; i < TC_FRAG_FLOAT4; i += S::NT) dst[i] = tab[i];
-        const float2 *dtab = reinterpret_cast<const float2 *>(tab + TC_FRAG_FLOAT4);
+        if constexpr (S::FRAG_SMEM)
+            for (int i = tid; i < S::NFRAG; i += S::NT) dst[i] = gFrag[i];
+        const float2 *dtab = reinterpret_cast<const float2 *>(gFrag + S::NFRAG);
         float2 *dD = reinterpret_cast<float2 *>(smem_raw + L::hD);
         for (int i = tid; i < Np * Np; i += S::NT) dD[i] = dtab[i];
         for (int i = tid; i < NF; i += S::NT) sFm[i] = sp.fmask[i];
     }
     __syncthreads();
     pdl_wait_then_release();
+    // fragment `h` (0 hi, 1 lo) of entry `ent` of the operator table
+    auto frag = [&](int ent, int h) -> float4 {
+        const int idx = (ent * 2 + h) * 32 + lane;
+        if constexpr (S::FRAG_SMEM) return sFrag[idx];
+        else return __ldg(gFrag + idx);
+    };
+    // entries: Dr [mt][ks], Ds [mt][ks], LIFT [mt][ks]
+    auto ent_d = [&](int m, int mt, int ks) { return (m * MT + mt) * KD + ks; };
+    auto ent_l = [&](int mt, int ks) { return 2 * MT * KD + mt * KL + ks; };
 
     unsigned char *wb = smem_raw + L::header + wid * L::warp;
     const unsigned wsh = static_cast<unsigned>(__cvta_generic_to_shared(wb));
@@ -201,7 +201,7 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
     const bool update = sp.mode == STAGE_UPDATE;
     bool need_k1 = update && !sp.first_stage;
     const int g = lane >> 2, t = lane & 3;
-    const int jn = g + 8 * (lane & 1);       // node held after frag_to_node
+    const int jn = g + 8 * (lane & 1);       // node (within a 16-row tile) held after frag_to_node
     const int ep = (lane >> 1) & 1;          // element of the pair held after frag_to_node
     const int be = g >> 2, bc = g & 3;       // B column of this lane: element of the pair, field
 
@@ -263,53 +263,60 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
         asm volatile("cp.async.wait_group 1;\n" ::);
         __syncwarp();
 
-        // Dr, Ds fragments [matrix][k-step]
-        float4 ah[2][2], al[2][2];
-#pragma unroll
-        for (int m = 0; m < 2; ++m)
-#pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-                ah[m][ks] = sFrag[((m * 2 + ks) * 2 + 0) * 32 + lane];
-                al[m][ks] = sFrag[((m * 2 + ks) * 2 + 1) * 32 + lane];
-            }
-
         // ---- V: broken gradient (MMA) and total flux of every volume node
 #pragma unroll
         for (int nt = 0; nt < WE / 2; ++nt) {
+            // B: the element's state relative to its first node, rows k = 8 ks + t (+ 4)
             const float *ub = reinterpret_cast<const float *>(sU + (2 * nt + be) * US);
             const float ref = ub[bc];
-            float b[4];
+            float b[2 * KD];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < 2 * KD; ++q) {
                 const int k = t + 4 * q;
                 b[q] = (k < Np) ? ub[4 * k + bc] - ref : 0.f;
             }
-            float ur[4], us[4];
-            grad_mma(ah, al, b, lane, ur, us);
-            const int e = 2 * nt + ep;
-            if (e < ne && jn < Np) {
-                const float *gg = sGeo + e * 16;
-                const float rx = gg[G_RX], ry = gg[G_RY], sx = gg[G_SX], sy = gg[G_SY];
-                float u[4], gx[4], gy[4];
-                f4_to(sU[e * US + jn], u);
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                float r0[4] = {0.f, 0.f, 0.f, 0.f}, r1[4] = {0.f, 0.f, 0.f, 0.f};
+                float s0[4] = {0.f, 0.f, 0.f, 0.f}, s1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int ks = 0; ks < KD; ++ks) {
+                    mma3(r0, r1, frag(ent_d(0, mt, ks), 0), frag(ent_d(0, mt, ks), 1), b[2 * ks], b[2 * ks + 1]);
+                    mma3(s0, s1, frag(ent_d(1, mt, ks), 0), frag(ent_d(1, mt, ks), 1), b[2 * ks], b[2 * ks + 1]);
+                }
+                float cr[4], cs[4], ur[4], us[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    gx[c] = rx * ur[c] + sx * us[c];
-                    gy[c] = ry * ur[c] + sy * us[c];
+                    cr[c] = r0[c] + r1[c];
+                    cs[c] = s0[c] + s1[c];
                 }
-                const float p = sPo[e * NpP + jn];
-                float cx[4], cy[4], vx[4], vy[4], fr[4], fs[4];
-                adv_flux(u, p, ph, cx, cy);
-                visc_flux(u, gx, gy, ph, vx, vy);
+                frag_to_node(cr, ur, lane);
+                frag_to_node(cs, us, lane);
+                const int e = 2 * nt + ep, j = 16 * mt + jn;
+                if (e < ne && j < Np) {
+                    const float *gg = sGeo + e * 16;
+                    const float rx = gg[G_RX], ry = gg[G_RY], sx = gg[G_SX], sy = gg[G_SY];
+                    float u[4], gx[4], gy[4];
+                    f4_to(sU[e * US + j], u);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const float Fx = cx[c] - vx[c], Fy = cy[c] - vy[c];
-                    fr[c] = rx * Fx + ry * Fy;
-                    fs[c] = sx * Fx + sy * Fy;
+                    for (int c = 0; c < 4; ++c) {
+                        gx[c] = rx * ur[c] + sx * us[c];
+                        gy[c] = ry * ur[c] + sy * us[c];
+                    }
+                    const float p = sPo[e * NpP + j];
+                    float cx[4], cy[4], vx[4], vy[4], fr[4], fs[4];
+                    adv_flux(u, p, ph, cx, cy);
+                    visc_flux(u, gx, gy, ph, vx, vy);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float Fx = cx[c] - vx[c], Fy = cy[c] - vy[c];
+                        fr[c] = rx * Fx + ry * Fy;
+                        fs[c] = sx * Fx + sy * Fy;
+                    }
+                    float4 *fo = reinterpret_cast<float4 *>(sF + e * FS + j * 8);
+                    fo[0] = to_f4(fr);
+                    fo[1] = to_f4(fs);
                 }
-                float4 *fo = reinterpret_cast<float4 *>(sF + e * FS + jn * 8);
-                fo[0] = to_f4(fr);
-                fo[1] = to_f4(fs);
             }
         }
 
@@ -318,11 +325,13 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
         // ---- F: at every face node (one per lane, the Nfp nodes of a face on
         // consecutive lanes): penalty norms of both traces, their maximum over
         // the face, and the numerical flux minus the own flux
-        static_assert(WE * NF <= 32, "one face node per lane");
-        {
-            const bool act = lane < ne * NF;
+        static_assert(EPP >= 1 && EPP * NF <= 32, "the face nodes of an element fit one pass");
+#pragma unroll 1
+        for (int pe = 0; pe < WE; pe += EPP) {
+            if (pe >= ne) break;                 // warp-uniform: the tile has no element pe
+            const bool act = lane < EPP * NF && pe + lane / NF < ne;
             const int q = act ? lane : 0;
-            const int e = q / NF, r = q - (q / NF) * NF, f = r / Nfp, i = r - (r / Nfp) * Nfp;
+            const int e = pe + q / NF, r = q - (q / NF) * NF, f = r / Nfp, i = r - (r / Nfp) * Nfp;
             const int4 cn = sConn[e];
             const int f2 = (cn.w >> (2 * f)) & 3, bt = (cn.w >> (8 + 2 * f)) & 3;
             const float *gg = sGeo + e * 16;
@@ -432,45 +441,46 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
         __syncwarp();
 
         // ---- U: R = -(Dr Fr + Ds Fs) + LIFT (Fscale dH) (MMA), then the stage
-        // update and the FP32 copy of the new state, one node per lane
-        {
-            float4 lh[2], ll[2];
+        // update and the FP32 copy of the new state, one node per lane and tile
 #pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-                lh[ks] = sFrag[((2 * 2 + ks) * 2 + 0) * 32 + lane];
-                ll[ks] = sFrag[((2 * 2 + ks) * 2 + 1) * 32 + lane];
+        for (int nt = 0; nt < WE / 2; ++nt) {
+            const float *fb = sF + (2 * nt + be) * FS;
+            const float r0 = fb[bc], s0 = fb[4 + bc];
+            const float *hb = sDH + (2 * nt + be) * HS;
+            float br[2 * KD], bs[2 * KD], bh[2 * KL];
+#pragma unroll
+            for (int q = 0; q < 2 * KD; ++q) {
+                const int k = t + 4 * q;
+                br[q] = (k < Np) ? fb[8 * k + bc] - r0 : 0.f;
+                bs[q] = (k < Np) ? fb[8 * k + 4 + bc] - s0 : 0.f;
             }
 #pragma unroll
-            for (int nt = 0; nt < WE / 2; ++nt) {
-                const float *fb = sF + (2 * nt + be) * FS;
-                const float r0 = fb[bc], s0 = fb[4 + bc];
-                float br[4], bs[4], bh[4];
-                const float *hb = sDH + (2 * nt + be) * HS;
+            for (int q = 0; q < 2 * KL; ++q) {
+                const int k = t + 4 * q;
+                bh[q] = (k < NF) ? hb[4 * k + bc] : 0.f;
+            }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int k = t + 4 * q;
-                    br[q] = (k < Np) ? fb[8 * k + bc] - r0 : 0.f;
-                    bs[q] = (k < Np) ? fb[8 * k + 4 + bc] - s0 : 0.f;
-                    bh[q] = (k < NF) ? hb[4 * k + bc] : 0.f;
-                }
+            for (int mt = 0; mt < MT; ++mt) {
                 // divergence and lift, each with separate accumulators for
                 // the large products and the corrections
                 float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
                 float l0[4] = {0.f, 0.f, 0.f, 0.f}, l1[4] = {0.f, 0.f, 0.f, 0.f};
-                mma3(d0, d1, ah[0][0], al[0][0], br[0], br[1]);
-                mma3(l0, l1, lh[0], ll[0], bh[0], bh[1]);
-                mma3(d0, d1, ah[1][0], al[1][0], bs[0], bs[1]);
-                mma3(l0, l1, lh[1], ll[1], bh[2], bh[3]);
-                mma3(d0, d1, ah[0][1], al[0][1], br[2], br[3]);
-                mma3(d0, d1, ah[1][1], al[1][1], bs[2], bs[3]);
+#pragma unroll
+                for (int ks = 0; ks < KD; ++ks) {
+                    mma3(d0, d1, frag(ent_d(0, mt, ks), 0), frag(ent_d(0, mt, ks), 1), br[2 * ks], br[2 * ks + 1]);
+                    mma3(d0, d1, frag(ent_d(1, mt, ks), 0), frag(ent_d(1, mt, ks), 1), bs[2 * ks], bs[2 * ks + 1]);
+                }
+#pragma unroll
+                for (int ks = 0; ks < KL; ++ks)
+                    mma3(l0, l1, frag(ent_l(mt, ks), 0), frag(ent_l(mt, ks), 1), bh[2 * ks], bh[2 * ks + 1]);
                 float cd[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) cd[c] = (l0[c] + l1[c]) - (d0[c] + d1[c]);
                 float R[4];
                 frag_to_node(cd, R, lane);
-                const int e = 2 * nt + ep;
-                if (e < ne && jn < Np) {
-                    const long long base = (k0 + e) * 4 * Np + jn;
+                const int e = 2 * nt + ep, j = 16 * mt + jn;
+                if (e < ne && j < Np) {
+                    const long long base = (k0 + e) * 4 * Np + j;
                     if (sp.src) {
 #pragma unroll
                         for (int c = 0; c < 4; ++c) R[c] += cvt_d2f(sp.src[base + c * Np]);
@@ -483,15 +493,15 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
                             const double inc = cvt_f2d(dtr * R[c]);
-                            const double k1 = sp.first_stage ? inc : fma(sp.A, sK1[(e * 4 + c) * Np + jn], inc);
+                            const double k1 = sp.first_stage ? inc : fma(sp.A, sK1[(e * 4 + c) * Np + j], inc);
                             sp.K1[base + c * Np] = k1;
-                            knew[c] = fma(sp.B, k1, sRaw[(e * 4 + c) * Np + jn]);
+                            knew[c] = fma(sp.B, k1, sRaw[(e * 4 + c) * Np + j]);
                             sp.K0out[base + c * Np] = knew[c];
                         }
                         const float un[4] = {cvt_d2f_trunc(knew[0]), cvt_d2f_trunc(knew[1]),
                                              cvt_d2f_trunc(knew[2]), cvt_d2f_trunc(knew[3])};
-                        sp.Sout[(k0 + e) * Np + jn] = to_f4(un);
-                        sp.Pout[(k0 + e) * NpP + jn] = pressure<float>(un, knew[3], gm1d);
+                        sp.Sout[(k0 + e) * Np + j] = to_f4(un);
+                        sp.Pout[(k0 + e) * NpP + j] = pressure<float>(un, knew[3], gm1d);
                     }
                 }
             }

@@ -75,8 +75,8 @@ cudaError_t launch_stage_mixed_fused(int p, bool batch, const LaunchShape &ls, c
                                      const Phys<float> &ph, cudaStream_t st);
 // elements per tile of the mixed kernel for degree p
 int stage_tile_elems(int p);
-// the tensor-core mixed IIP kernel (p = 1..4): warp tiles of 4 elements;
-// its `ops` is the fragment table of build_tc_fragments
+// the tensor-core mixed IIP kernel (p = 1..6): warp tiles of 2 elements;
+// its `ops` is the operator table of build_tc_fragments
 bool stage_tc_supported(int p);
 // elements per warp tile of the tensor-core kernel (any p)
 int stage_tile_elems_tc();
@@ -86,8 +86,8 @@ cudaError_t stage_shape_tc(int p, long long units, bool batch, bool fused, Launc
 cudaError_t launch_stage_tc(int p, bool batch, bool fused, const LaunchShape &ls, const StageParams &sp,
                             const Phys<float> &ph, cudaStream_t st);
 // Dr, Ds [Np][Np] and LIFT [Np][NF] (FP64, row-major) -> the kernel's
-// operator table (TF32 hi / lo fragments, 3 * 2 * 2 * 32 float4, then
-// (Dr, Ds) as FP32 pairs [Np][Np])
+// operator table (TF32 hi / lo fragments of 16-row tiles, then (Dr, Ds) as
+// FP32 pairs [Np][Np])
 void build_tc_fragments(int Np, int NF, const double *Dr, const double *Ds, const double *LIFT,
                         std::vector<float> &out);
 // FP32 copy [K][Np] float4 and FP64-recovered pressure [K][NpP] of a state

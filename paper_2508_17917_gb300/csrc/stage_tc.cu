@@ -1,5 +1,5 @@
 // stage_tc.cu -- the tensor-core stage kernel (mixed precision, IIP,
-// p = 1..4): launch shape, launch, and the operator fragment table.
+// p = 1..6): launch shape, launch, and the operator fragment table.
 #include <cstring>
 
 #include "dg_stage_tc.cuh"
@@ -93,7 +93,7 @@ float tf32_round(float x)
 
 }  // namespace
 
-bool stage_tc_supported(int p) { return p >= 1 && p <= 4; }
+bool stage_tc_supported(int p) { return p >= 1 && p <= 6; }
 
 int stage_tile_elems_tc() { return ShapeTC<1>::WE; }
 
@@ -104,6 +104,8 @@ cudaError_t stage_shape_tc(int p, long long units, bool batch, bool fused, Launc
     case 2: return shape_tc_any<2>(units, batch, fused, out);
     case 3: return shape_tc_any<3>(units, batch, fused, out);
     case 4: return shape_tc_any<4>(units, batch, fused, out);
+    case 5: return shape_tc_any<5>(units, batch, fused, out);
+    case 6: return shape_tc_any<6>(units, batch, fused, out);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -116,41 +118,49 @@ cudaError_t launch_stage_tc(int p, bool batch, bool fused, const LaunchShape &ls
     case 2: return launch_tc_any<2>(batch, fused, ls, sp, ph, st);
     case 3: return launch_tc_any<3>(batch, fused, ls, sp, ph, st);
     case 4: return launch_tc_any<4>(batch, fused, ls, sp, ph, st);
+    case 5: return launch_tc_any<5>(batch, fused, ls, sp, ph, st);
+    case 6: return launch_tc_any<6>(batch, fused, ls, sp, ph, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
-// A operands of the three operators, zero-padded to 16 x 16, in the order the
-// kernel reads them: [matrix][k-step][hi, lo][lane][a0..a3] with lane = 4 g + t,
-// a0 = A[g][8 ks + t], a1 = A[g + 8][8 ks + t], a2 = A[g][8 ks + t + 4],
-// a3 = A[g + 8][8 ks + t + 4].  hi is the FP64 entry rounded to FP32 and
-// then to TF32; lo is the remainder rounded the same way.  Followed by
-// (Dr, Ds) in FP32 as interleaved pairs, row-major (the face-node rows).
+// A operands of the three operators, zero-padded to 16 MT rows and 8 KD
+// (Dr, Ds) or 8 KL (LIFT) columns, in the order the kernel reads them:
+// entries Dr [MT][KD], Ds [MT][KD], LIFT [MT][KL], each [hi, lo][lane][a0..a3]
+// with lane = 4 g + t, a0 = A[16 mt + g][8 ks + t], a1 = A[16 mt + g + 8][8 ks + t],
+// a2 = A[16 mt + g][8 ks + t + 4], a3 = A[16 mt + g + 8][8 ks + t + 4].  hi is
+// the FP64 entry rounded to FP32 and then to TF32; lo is the remainder
+// rounded the same way.  Followed by (Dr, Ds) in FP32 as interleaved pairs,
+// row-major (the face-node rows).
 void build_tc_fragments(int Np, int NF, const double *Dr, const double *Ds, const double *LIFT,
                         std::vector<float> &out)
 {
-    out.assign(static_cast<size_t>(TC_FRAG_FLOAT4) * 4 + 2 * static_cast<size_t>(Np) * Np, 0.0f);
-    auto entry = [&](int m, int row, int col) -> double {
-        if (row >= Np) return 0.0;
-        if (m < 2) return (col < Np) ? (m == 0 ? Dr : Ds)[row * Np + col] : 0.0;
-        return (col < NF) ? LIFT[row * NF + col] : 0.0;
-    };
-    for (int m = 0; m < 3; ++m)
-        for (int ks = 0; ks < 2; ++ks)
-            for (int lane = 0; lane < 32; ++lane) {
-                const int g = lane >> 2, t = lane & 3;
-                const int rows[4] = {g, g + 8, g, g + 8};
-                const int cols[4] = {8 * ks + t, 8 * ks + t, 8 * ks + t + 4, 8 * ks + t + 4};
-                for (int a = 0; a < 4; ++a) {
-                    const double x = entry(m, rows[a], cols[a]);
-                    const float hi = tf32_round(static_cast<float>(x));
-                    const float lo = tf32_round(static_cast<float>(x - static_cast<double>(hi)));
-                    out[((((m * 2 + ks) * 2 + 0) * 32 + lane) * 4) + a] = hi;
-                    out[((((m * 2 + ks) * 2 + 1) * 32 + lane) * 4) + a] = lo;
-                }
+    const int MT = (Np + 15) / 16, KD = (Np + 7) / 8, KL = (NF + 7) / 8;
+    const int nent = 2 * MT * KD + MT * KL;
+    const size_t nfrag = static_cast<size_t>(nent) * 64;            // float4
+    out.assign(nfrag * 4 + 2 * static_cast<size_t>(Np) * Np, 0.0f);
+    auto put = [&](int ent, const double *A, int ncols, int mt, int ks) {
+        for (int lane = 0; lane < 32; ++lane) {
+            const int g = lane >> 2, t = lane & 3;
+            const int rows[4] = {16 * mt + g, 16 * mt + g + 8, 16 * mt + g, 16 * mt + g + 8};
+            const int cols[4] = {8 * ks + t, 8 * ks + t, 8 * ks + t + 4, 8 * ks + t + 4};
+            for (int a = 0; a < 4; ++a) {
+                const double x = (rows[a] < Np && cols[a] < ncols) ? A[rows[a] * ncols + cols[a]] : 0.0;
+                const float hi = tf32_round(static_cast<float>(x));
+                const float lo = tf32_round(static_cast<float>(x - static_cast<double>(hi)));
+                out[((static_cast<size_t>(ent) * 2 + 0) * 32 + lane) * 4 + a] = hi;
+                out[((static_cast<size_t>(ent) * 2 + 1) * 32 + lane) * 4 + a] = lo;
             }
-    // then (Dr, Ds) pairs in FP32, row-major
-    float *d = out.data() + static_cast<size_t>(TC_FRAG_FLOAT4) * 4;
+        }
+    };
+    for (int mt = 0; mt < MT; ++mt) {
+        for (int ks = 0; ks < KD; ++ks) {
+            put((0 * MT + mt) * KD + ks, Dr, Np, mt, ks);
+            put((1 * MT + mt) * KD + ks, Ds, Np, mt, ks);
+        }
+        for (int ks = 0; ks < KL; ++ks) put(2 * MT * KD + mt * KL + ks, LIFT, NF, mt, ks);
+    }
+    float *d = out.data() + nfrag * 4;
     for (int i = 0; i < Np * Np; ++i) {
         d[2 * i] = static_cast<float>(Dr[i]);
         d[2 * i + 1] = static_cast<float>(Ds[i]);

@@ -132,10 +132,7 @@ def test_batch_graph_replay_is_bit_identical(small_run):
 def test_batch_case_matches_oracle_loop(small_run, i, run):
     cases, states, nsteps, res = small_run
     hist, Us, rigid, _, variants = res[run]
-    # a forced tensor-core shape applies to the groups of p <= 4, the others
-    # take the two-node shape
-    want = run[1] if (run[1] != 3 or cases[i]["p"] <= 4) else 2
-    assert variants[i] == (want or variants[i]) and variants[i] in (1, 2, 3)
+    assert variants[i] == (run[1] or variants[i]) and variants[i] in (1, 2, 3)
     ref, U_ref, P = oracle_loop(cases[i], states[i], nsteps)
     got = hist[:, i, :]
     # dt from the mixed-path state: FP32 bound of a state that differs at the 1e-6 level
@@ -169,13 +166,12 @@ def test_batch_launch_count(small_run):
     groups = len({c["p"] for c in cases})
     # set_state per case, initial forces (groups + 1), then per step: dt per group,
     # dt reduce, Newmark, 5 stages per group, forces per group, force sum, record;
-    # the tuned run adds five residual-only launches per shape and group
-    # (three shapes at p <= 4, two beyond)
+    # the tuned run adds five residual-only launches per shape (three) and group
     for run in RUNS:
         stage = groups if run[0] == "fused" else 5 * groups
         per_step = groups + 2 + stage + groups + 1 + 1
         launches = res[run][3]
-        tune = sum(15 if p <= 4 else 10 for p in {c["p"] for c in cases}) if run[1] == 0 else 0
+        tune = 15 * groups if run[1] == 0 else 0
         assert launches == len(cases) + (groups + 1) + tune + nsteps * per_step, (run, launches)
 
 

@@ -3,7 +3,10 @@ four elements, Dr / Ds / LIFT products as mma.sync TF32 with three products
 of split operands) against the oracle.
 
 Tolerances are those of the mixed path: 2e-5 relative to the largest
-residual entry, 2e-5 relative L2 per field after 100 steps.  The split
+residual entry up to p = 4, growing as (p / 4)^2 beyond (the FP32 rounding of
+the state amplified by derivative rows whose absolute sums grow like p^2, as
+for the other mixed shapes), and 2e-5 relative L2 per field after 100
+steps.  The split
 products are good to about 2^-21 of sum |A||B| and the operands are taken
 relative to the element's first node, so the contraction error stays below
 the FP32 rounding of the state that bounds the other mixed kernels."""
@@ -33,12 +36,16 @@ def stream():
     return torch.cuda.current_stream().cuda_stream
 
 
+def rhs_tol(p):
+    return 2e-5 * max(1.0, (p / 4.0) ** 2)
+
+
 def rel_l2(P, d, ref):
     J, M = P.geo["J"], P.ops["M"]
     return np.sqrt(np.einsum("k,kcn,nm,kcm->c", J, d, M, d) / np.einsum("k,kcn,nm,kcm->c", J, ref, M, ref))
 
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("n", [5, 7])
 def test_rhs_periodic_tc(dg, p, n):
     # K = 50 and 98 elements: several warp tiles and a ragged last tile
@@ -52,11 +59,11 @@ def test_rhs_periodic_tc(dg, p, n):
     assert s.variant == 3
     s.set_state(U)
     got = s.rhs(0.0, vw)
-    assert np.abs(got - ref).max() / np.abs(ref).max() <= 2e-5
+    assert np.abs(got - ref).max() / np.abs(ref).max() <= rhs_tol(p)
 
 
 @pytest.mark.parametrize("adiabatic", [1, 0])
-@pytest.mark.parametrize("p", [2, 3, 4])
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6])
 def test_rhs_ogrid_wall_farfield_tc(dg, p, adiabatic):
     mesh = dg_inputs.ogrid_cylinder(24, 8, 0.5, 4.0, seed=3)
     kw = dict(mu=0.01, rho_inf=1.0, u_inf=1.0, v_inf=0.0, p_inf=17.857142857142858,
@@ -72,7 +79,7 @@ def test_rhs_ogrid_wall_farfield_tc(dg, p, adiabatic):
     s.set_variant(3)
     s.set_state(U)
     got = s.rhs(0.0, vw)
-    assert np.abs(got - ref).max() / np.abs(ref).max() <= 2e-5
+    assert np.abs(got - ref).max() / np.abs(ref).max() <= rhs_tol(p)
 
 
 def test_rhs_manufactured_source_tc(dg):
@@ -92,7 +99,7 @@ def test_rhs_manufactured_source_tc(dg):
     assert np.abs(got - ref).max() / scale <= 2e-4
 
 
-@pytest.mark.parametrize("p", [2, 4])
+@pytest.mark.parametrize("p", [2, 4, 6])
 def test_vortex_100_steps_tc(dg, p):
     mesh = dg_inputs.periodic_square(10)
     P = oracle.Problem(mesh, p, mu=1e-3)
@@ -133,8 +140,8 @@ def test_ogrid_steps_tc(dg, variant):
     assert np.all(err <= 2e-5), err
 
 
-def test_tc_rejected_beyond_p4_and_on_fp64(dg):
-    s = dg.Solver(dg_inputs.periodic_square(4), 5, "mixed", stream=stream())
+def test_tc_rejected_on_fp64_and_theta(dg):
+    s = dg.Solver(dg_inputs.periodic_square(4), 3, "mixed", stream=stream(), theta=1.0, C1=0.05)
     with pytest.raises(dg.DGError) as e:
         s.set_variant(3)
     assert e.value.status == -6
