@@ -72,7 +72,9 @@ dg_status dg_mlp_loss_grad(dg_mlp *m, const float *X, const float *T, int B, flo
 
 /* nsteps Adam steps of full-batch training on (X, T) with learning rate lr;
  * loss_hist (device [nsteps] FP32, or NULL) receives the loss before each
- * update.  Errors: DG_EINVAL, DG_ECUDA. */
+ * update.  From 8 steps on, one captured step is replayed from a CUDA graph
+ * (same kernels and arguments, kept for the next call with the same X, T,
+ * B, lr and loss_hist).  Errors: DG_EINVAL, DG_ECUDA. */
 dg_status dg_mlp_train(dg_mlp *m, const float *X, const float *T, int B, int nsteps, float lr, float *loss_hist);
 
 #ifdef __cplusplus

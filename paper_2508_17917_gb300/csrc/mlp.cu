@@ -235,6 +235,33 @@ __global__ void adam_kernel(float *p, const float *g, float *m, float *v, long l
     }
 }
 
+// Adam step with the bias corrections of step *cnt taken from bc (pairs
+// bc1, bc2 per step); used when the training step is replayed from a graph
+__global__ void adam_indexed_kernel(float *p, const float *g, float *m, float *v, long long n, float lr, float b1,
+                                    float b2, float eps, const float *bc, const int *cnt)
+{
+    const int k = *cnt;
+    const float bc1 = bc[2 * k], bc2 = bc[2 * k + 1];
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    }
+}
+
+// hist[*cnt] = *loss (if hist), then advance the step index
+__global__ void record_loss_kernel(const float *loss, float *hist, int *cnt)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if (hist) hist[*cnt] = *loss;
+        *cnt += 1;
+    }
+}
+
 // bfloat16 copies of the weight matrices (biases stay FP32)
 __global__ void weights_bf16_kernel(const float *p, const long long *woff, const long long *wlen, int nl, bf16 *wq,
                                     const long long *qoff)
@@ -265,12 +292,22 @@ struct dg_mlp {
     int64_t launches = 0;
     long long step = 0;
     dg::DevBuf<float> p, m, v, g, lossbuf, partial, ws;   // ws: split-K slices
+    // training replayed from a CUDA graph: one captured Adam step, the bias
+    // corrections of every step of the call, the step index, the output rows
+    dg::DevBuf<float> bc, yscr;
+    dg::DevBuf<int> cnt;
+    cudaGraphExec_t gexec = nullptr;
+    const void *gkey[3] = {nullptr, nullptr, nullptr};
+    int gkey_b = 0;
+    float gkey_lr = 0.0f;
+    int64_t glaunches = 0;                             // kernels in the captured step
     dg::DevBuf<bf16> wq;
     dg::DevBuf<long long> dwoff, dwlen, dqoff;
     std::vector<dg::DevBuf<float>> Z, DZ32;            // per hidden layer / per layer
     std::vector<dg::DevBuf<bf16>> H, DZ16;             // H[0] = input
     ~dg_mlp()
     {
+        if (gexec) cudaGraphExecDestroy(gexec);
         if (stream) cudaStreamDestroy(stream);
     }
 };
@@ -574,22 +611,80 @@ dg_status dg_mlp_train(dg_mlp *m, const float *X, const float *T, int B, int nst
     dg_status st = check_rows(m, X, T, B);
     if (st != DG_OK) return st;
     if (nsteps < 0 || !(lr > 0.0f)) return mfail(m, DG_EINVAL, "need nsteps >= 0 and lr > 0");
-    dg::DevBuf<float> y;
-    M_CUDA(m, y.alloc(static_cast<size_t>(B) * m->n_out));
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-    for (int n = 0; n < nsteps; ++n) {
-        st = loss_grad(m, X, T, B, m->g.ptr, loss_hist ? loss_hist + n : m->lossbuf.ptr, y.ptr);
-        if (st != DG_OK) return st;
-        m->step += 1;
-        const float bc1 = static_cast<float>(1.0 - std::pow(0.9, static_cast<double>(m->step)));
-        const float bc2 = static_cast<float>(1.0 - std::pow(0.999, static_cast<double>(m->step)));
-        adam_kernel<<<blocks_for(m->nparams), 256, 0, m->stream>>>(m->p.ptr, m->g.ptr, m->m.ptr, m->v.ptr, m->nparams,
-                                                                  lr, b1, b2, eps, bc1, bc2);
-        m->launches += 1;
-        M_CUDA(m, cudaGetLastError());
-        st = refresh_bf16(m);
-        if (st != DG_OK) return st;
+    if (!m->yscr.ptr) M_CUDA(m, m->yscr.alloc(static_cast<size_t>(m->max_batch) * m->n_out));
+    if (nsteps < 8) {
+        for (int n = 0; n < nsteps; ++n) {
+            st = loss_grad(m, X, T, B, m->g.ptr, loss_hist ? loss_hist + n : m->lossbuf.ptr, m->yscr.ptr);
+            if (st != DG_OK) return st;
+            m->step += 1;
+            const float bc1 = static_cast<float>(1.0 - std::pow(0.9, static_cast<double>(m->step)));
+            const float bc2 = static_cast<float>(1.0 - std::pow(0.999, static_cast<double>(m->step)));
+            adam_kernel<<<blocks_for(m->nparams), 256, 0, m->stream>>>(m->p.ptr, m->g.ptr, m->m.ptr, m->v.ptr,
+                                                                      m->nparams, lr, b1, b2, eps, bc1, bc2);
+            m->launches += 1;
+            M_CUDA(m, cudaGetLastError());
+            st = refresh_bf16(m);
+            if (st != DG_OK) return st;
+        }
+        M_CUDA(m, cudaStreamSynchronize(m->stream));
+        return DG_OK;
     }
+    // Longer runs replay one captured step: the same kernels with the same
+    // arguments as above, the bias corrections (computed here in double, as
+    // above) and the loss history indexed by a device step counter.
+    std::vector<float> bch(2 * static_cast<size_t>(nsteps));
+    for (int n = 0; n < nsteps; ++n) {
+        const double k = static_cast<double>(m->step + 1 + n);
+        bch[2 * n] = static_cast<float>(1.0 - std::pow(0.9, k));
+        bch[2 * n + 1] = static_cast<float>(1.0 - std::pow(0.999, k));
+    }
+    if (m->bc.n < bch.size()) {
+        if (m->gexec) {
+            cudaGraphExecDestroy(m->gexec);
+            m->gexec = nullptr;
+        }
+        M_CUDA(m, m->bc.alloc(bch.size()));
+    }
+    if (!m->cnt.ptr) M_CUDA(m, m->cnt.alloc(1));
+    M_CUDA(m, cudaMemcpyAsync(m->bc.ptr, bch.data(), bch.size() * sizeof(float), cudaMemcpyHostToDevice, m->stream));
+    M_CUDA(m, cudaMemsetAsync(m->cnt.ptr, 0, sizeof(int), m->stream));
+    const bool same = m->gexec && m->gkey[0] == X && m->gkey[1] == T && m->gkey[2] == loss_hist && m->gkey_b == B &&
+                      m->gkey_lr == lr;
+    if (!same) {
+        if (m->gexec) {
+            cudaGraphExecDestroy(m->gexec);
+            m->gexec = nullptr;
+        }
+        const int64_t l0 = m->launches;
+        M_CUDA(m, cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+        st = loss_grad(m, X, T, B, m->g.ptr, m->lossbuf.ptr, m->yscr.ptr);
+        adam_indexed_kernel<<<blocks_for(m->nparams), 256, 0, m->stream>>>(m->p.ptr, m->g.ptr, m->m.ptr, m->v.ptr,
+                                                                          m->nparams, lr, b1, b2, eps, m->bc.ptr,
+                                                                          m->cnt.ptr);
+        record_loss_kernel<<<1, 32, 0, m->stream>>>(m->lossbuf.ptr, loss_hist, m->cnt.ptr);
+        if (st == DG_OK) st = refresh_bf16(m);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(m->stream, &graph);
+        if (st != DG_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        M_CUDA(m, ec);
+        const cudaError_t ei = cudaGraphInstantiate(&m->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        M_CUDA(m, ei);
+        m->glaunches = m->launches - l0 + 2;
+        m->launches = l0;
+        m->gkey[0] = X;
+        m->gkey[1] = T;
+        m->gkey[2] = loss_hist;
+        m->gkey_b = B;
+        m->gkey_lr = lr;
+    }
+    for (int n = 0; n < nsteps; ++n) M_CUDA(m, cudaGraphLaunch(m->gexec, m->stream));
+    m->launches += m->glaunches * nsteps;
+    m->step += nsteps;
     M_CUDA(m, cudaStreamSynchronize(m->stream));
     return DG_OK;
 }
