@@ -101,16 +101,17 @@ dg_status dg_set_mesh(dg_ctx *ctx, int64_t Nv, const double *vx, const double *v
                       int64_t K, const int32_t *EToV, const int32_t *EToE,
                       const int32_t *EToF, const int32_t *bc);
 
-/* Tile shape of the mixed-precision IIP stage kernel (no counterpart in the
+/* Tile shape of the mixed-precision stage kernel (no counterpart in the
  * paper): 1 = one volume node and one face node per thread (256 threads),
  * 2 = two volume nodes and two face nodes of one face per thread (128
- * threads), 3 = one warp per tile of 4 elements with the Dr / Ds / LIFT
- * products on the tensor cores (mma.sync TF32, three products of split
- * operands, about 2^-21 relative; p <= 6), 0 = time every available
- * shape (residual-only launches on the current state) at the first time step
- * after a mesh upload and keep the fastest (the default).  Other paths have
- * one kernel and accept 0 and 1.  Errors: DG_EINVAL (variant outside 0..3),
- * DG_EUNSUPPORTED (2 or 3 on the FP64 or theta != 0 path). */
+ * threads; IIP only), 3 = one warp per tile of 2 elements with the Dr / Ds /
+ * LIFT (and, for theta != 0, Wr / Ws) products on the tensor cores
+ * (mma.sync TF32, three products of split operands, about 2^-21 relative;
+ * p <= 6), 0 = time every available shape (residual-only launches on the
+ * current state) at the first time step after a mesh upload and keep the
+ * fastest (the default).  The FP64 path has one kernel and accepts 0 and 1.
+ * Errors: DG_EINVAL (variant outside 0..3), DG_EUNSUPPORTED (2 or 3 on the
+ * FP64 path, 2 with theta != 0). */
 dg_status dg_set_stage_variant(dg_ctx *ctx, int variant);
 
 /* The tile shape in use: 1, 2 or 3 (the single-node kernel until tuned). */

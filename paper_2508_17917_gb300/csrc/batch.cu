@@ -495,7 +495,8 @@ dg_status dg_batch_create(const dg_params *common, int ncases, const dg_case *ca
         chk(g.tiles3.alloc(tiles3.size()));
         std::vector<float> frag;
         if (g.has_tc) {
-            dg::build_tc_fragments(Np, NF, g.ops.Dr.data(), g.ops.Ds.data(), g.ops.LIFT.data(), frag);
+            dg::build_tc_fragments(Np, NF, g.ops.Dr.data(), g.ops.Ds.data(), g.ops.LIFT.data(), g.ops.Wr.data(),
+                                   g.ops.Ws.data(), frag);
             chk(g.tcfrag.alloc(frag.size()));
         }
         chk(g.elem_case.alloc(ecase.size()));

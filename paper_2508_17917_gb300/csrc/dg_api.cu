@@ -290,7 +290,8 @@ dg_status dg_create(const dg_params *params, void *cuda_stream, dg_ctx **out)
     cudaMemcpy(c->ops32.ptr, o32.data(), o32.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (dg::stage_tc_supported(p.p)) {
         std::vector<float> frag;
-        dg::build_tc_fragments(Np, NF, c->ops.Dr.data(), c->ops.Ds.data(), c->ops.LIFT.data(), frag);
+        dg::build_tc_fragments(Np, NF, c->ops.Dr.data(), c->ops.Ds.data(), c->ops.LIFT.data(), c->ops.Wr.data(),
+                               c->ops.Ws.data(), frag);
         if (c->tcfrag.alloc(frag.size()) != cudaSuccess) {
             cudaGetLastError();
             delete c;
@@ -380,13 +381,15 @@ dg_status dg_set_stage_variant(dg_ctx *c, int variant)
     if (!c) return DG_EINVAL;
     c->err.clear();
     if (variant < 0 || variant > 3) return fail(c, DG_EINVAL, "variant must be 0, 1, 2 or 3");
-    if (variant >= 2 && (c->prm.precision != DG_PRECISION_MIXED || c->prm.theta != 0.0))
-        return fail(c, DG_EUNSUPPORTED, "the two-node and tensor-core kernels are mixed-precision IIP kernels");
+    if (variant >= 2 && c->prm.precision != DG_PRECISION_MIXED)
+        return fail(c, DG_EUNSUPPORTED, "the two-node and tensor-core kernels are mixed-precision kernels");
+    if (variant == 2 && c->prm.theta != 0.0)
+        return fail(c, DG_EUNSUPPORTED, "the two-node kernel is an IIP kernel");
     if (variant == 3 && !dg::stage_tc_supported(c->prm.p))
         return fail(c, DG_EUNSUPPORTED, "the tensor-core kernel covers p <= 6");
     c->variant_req = variant;
     c->tuned = (variant != 0);
-    if (c->K > 0 && c->prm.precision == DG_PRECISION_MIXED && c->prm.theta == 0.0)
+    if (c->K > 0 && c->prm.precision == DG_PRECISION_MIXED)
         c->shape = (variant == 3) ? c->shape3 : (variant == 2) ? c->shape2 : c->shape1;
     return DG_OK;
 }
@@ -455,13 +458,15 @@ dg_status dg_set_mesh(dg_ctx *c, int64_t Nv, const double *vx, const double *vy,
     if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel configuration");
     c->shape1 = c->shape;
     c->tuned = false;
-    if (c->prm.precision == DG_PRECISION_MIXED && !th) {
-        e = dg::stage_shape_mixed2(c->prm.p, K, false, c->shape2);
-        if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel configuration");
-        if (c->variant_req == 2) c->shape = c->shape2;
-        c->has_tc = false;
+    c->has_tc = false;
+    if (c->prm.precision == DG_PRECISION_MIXED) {
+        if (!th) {
+            e = dg::stage_shape_mixed2(c->prm.p, K, false, c->shape2);
+            if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel configuration");
+            if (c->variant_req == 2) c->shape = c->shape2;
+        }
         if (dg::stage_tc_supported(c->prm.p)) {
-            e = dg::stage_shape_tc(c->prm.p, K, false, false, c->shape3);
+            e = dg::stage_shape_tc(c->prm.p, K, false, false, c->shape3, th);
             if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel configuration");
             c->has_tc = true;
             if (c->variant_req == 3) c->shape = c->shape3;
@@ -545,11 +550,12 @@ dg_status dg_set_source(dg_ctx *c, int kind, const double *params)
     return DG_OK;
 }
 
-// Mixed IIP path, first use: time both stage kernels (one and two nodes per
-// thread) on the current state in residual-only mode and keep the faster.
+// Mixed path, first use: time every available stage-kernel shape (one and
+// two nodes per thread, tensor-core warp tiles; the two-node shape is IIP
+// only) on the current state in residual-only mode and keep the fastest.
 static dg_status tune_stage(dg_ctx *c, const double vw[2])
 {
-    if (c->tuned || c->prm.precision != DG_PRECISION_MIXED || c->prm.theta != 0.0 || c->variant_req != 0) {
+    if (c->tuned || c->prm.precision != DG_PRECISION_MIXED || c->variant_req != 0) {
         c->tuned = true;
         return DG_OK;
     }
@@ -561,6 +567,7 @@ static dg_status tune_stage(dg_ctx *c, const double vw[2])
     dg::LaunchShape pick = c->shape1;
     for (const dg::LaunchShape *cand : {&c->shape1, &c->shape2, &c->shape3}) {
         if (cand == &c->shape3 && !c->has_tc) continue;
+        if (cand == &c->shape2 && c->prm.theta != 0.0) continue;
         c->shape = *cand;
         float ms = 0.f;
         for (int rep = 0; rep < 5; ++rep) {

@@ -60,22 +60,26 @@ struct ShapeTC {
     static constexpr int UN = Np + ((13 - Np % 8) % 8);          // >= Np, = 5 mod 8
     static constexpr int FS = 128 * MT + 4;       // = 4 mod 32
     static constexpr int HS = 32 * KL + 16;       // = 16 mod 32
-    // operator fragments: Dr and Ds [MT][KD], LIFT [MT][KL], each [hi, lo][lane]
-    static constexpr int NFRAG = (2 * MT * KD + MT * KL) * 64;   // float4
+    // operator fragments: Dr and Ds [MT][KD], LIFT [MT][KL], then (theta
+    // variant) Wr and Ws [MT][KD], each [hi, lo][lane]
+    static constexpr int NENT = 2 * MT * KD + MT * KL;           // entries of the IIP kernel
+    static constexpr int NENT_ALL = NENT + 2 * MT * KD;          // with Wr, Ws
+    static constexpr int NFRAG_ALL = NENT_ALL * 64;              // float4 in the table
     static constexpr bool FRAG_SMEM = MT == 1;    // staged in shared memory (else read through L1)
 };
 
-// operator table: the MMA fragments (ShapeTC<P>::NFRAG float4), then
+// operator table: the MMA fragments (ShapeTC<P>::NFRAG_ALL float4), then
 // (Dr, Ds) in FP32 as float2 [Np][Np] for the face-node gradients of the
 // neighbours
-template <int P>
+template <int P, bool TH = false>
 struct TcLayout {
     using S = ShapeTC<P>;
+    static constexpr int NFRAG = (TH ? S::NENT_ALL : S::NENT) * 64;    // fragments the kernel reads
     static constexpr int Np = S::Np, NF = S::NF, WE = S::WE, NpP = S::NpP;
     static constexpr size_t al(size_t b) { return (b + 15) & ~size_t(15); }
     // block header
     static constexpr size_t hFrag = 0;                                      // float4 [NFRAG] if FRAG_SMEM
-    static constexpr size_t hFm = hFrag + (S::FRAG_SMEM ? sizeof(float4) * S::NFRAG : 0);   // int [NF]
+    static constexpr size_t hFm = hFrag + (S::FRAG_SMEM ? sizeof(float4) * NFRAG : 0);      // int [NF]
     static constexpr size_t hD = hFm + al(sizeof(int) * NF);                // float2 [Np][Np]: (Dr, Ds)
     static constexpr size_t header = hD + al(sizeof(float2) * Np * Np);
     // one region per warp
@@ -90,7 +94,8 @@ struct TcLayout {
     static constexpr size_t oK1 = oRaw + al(8 * WE * 4 * Np);               // double [WE][4][Np]
     static constexpr size_t oF = oK1 + al(8 * WE * 4 * Np);                 // float [WE][FS]: node j: Fr[4], Fs[4]
     static constexpr size_t oDH = oF + al(4 * WE * S::FS);                  // float [WE][HS]: slot r: Fscale dH[4]
-    static constexpr size_t warp = oDH + al(4 * WE * S::HS);
+    static constexpr size_t oTH = oDH + al(4 * WE * S::HS);                 // theta: float [2][WE][HS]: x, y vectors
+    static constexpr size_t warp = oTH + (TH ? al(4 * 2 * WE * S::HS) : 0);
     static constexpr size_t bytes = header + S::NW * warp;
 };
 
@@ -139,12 +144,12 @@ __device__ __forceinline__ void frag_to_node(const float c[4], float v[4], int l
     v[3] = odd ? c[3] : ry;
 }
 
-template <int P, bool BATCH = false, bool FUSE = false>
-__global__ void __launch_bounds__(128, (FUSE || ShapeTC<P>::MT > 1) ? 4 : 5)
+template <int P, bool BATCH = false, bool FUSE = false, bool TH = false>
+__global__ void __launch_bounds__(128, (FUSE || TH || ShapeTC<P>::MT > 1) ? 4 : 5)
 stage_tc_kernel(StageParams sp, Phys<float> ph)
 {
     using S = ShapeTC<P>;
-    using L = TcLayout<P>;
+    using L = TcLayout<P, TH>;
     constexpr int Np = S::Np, Nfp = S::Nfp, NF = S::NF, WE = S::WE, NpP = S::NpP;
     constexpr int US = S::US, UN = S::UN, FS = S::FS, HS = S::HS;
     constexpr int MT = S::MT, KD = S::KD, KL = S::KL, EPP = S::EPP;
@@ -159,8 +164,8 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
         // rows, face node table
         float4 *dst = reinterpret_cast<float4 *>(smem_raw + L::hFrag);
         if constexpr (S::FRAG_SMEM)
-            for (int i = tid; i < S::NFRAG; i += S::NT) dst[i] = gFrag[i];
-        const float2 *dtab = reinterpret_cast<const float2 *>(gFrag + S::NFRAG);
+            for (int i = tid; i < L::NFRAG; i += S::NT) dst[i] = gFrag[i];
+        const float2 *dtab = reinterpret_cast<const float2 *>(gFrag + S::NFRAG_ALL);
         float2 *dD = reinterpret_cast<float2 *>(smem_raw + L::hD);
         for (int i = tid; i < Np * Np; i += S::NT) dD[i] = dtab[i];
         for (int i = tid; i < NF; i += S::NT) sFm[i] = sp.fmask[i];
@@ -176,6 +181,7 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
     // entries: Dr [mt][ks], Ds [mt][ks], LIFT [mt][ks]
     auto ent_d = [&](int m, int mt, int ks) { return (m * MT + mt) * KD + ks; };
     auto ent_l = [&](int mt, int ks) { return 2 * MT * KD + mt * KL + ks; };
+    auto ent_w = [&](int m, int mt, int ks) { return S::NENT + (m * MT + mt) * KD + ks; };   // Wr, Ws
 
     unsigned char *wb = smem_raw + L::header + wid * L::warp;
     const unsigned wsh = static_cast<unsigned>(__cvta_generic_to_shared(wb));
@@ -190,6 +196,9 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
     const double *sK1 = reinterpret_cast<const double *>(wb + L::oK1);
     float *sF = reinterpret_cast<float *>(wb + L::oF);
     float *sDH = reinterpret_cast<float *>(wb + L::oDH);
+    float *sTHx = reinterpret_cast<float *>(wb + L::oTH);        // theta variant only
+    float *sTHy = sTHx + WE * HS;
+    const float theta = static_cast<float>(sp.theta);
 
     const float *geo = static_cast<const float *>(sp.geo);
     const long long K = sp.K;
@@ -260,7 +269,10 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
         if (need_k1)
             for (int c = lane; c < ne * 2 * Np; c += 32) cp_async16(wsh + L::oK1 + 16u * c, sp.K1 + k0 * 4 * Np + 2 * c);
         asm volatile("cp.async.commit_group;\n" ::);
-        asm volatile("cp.async.wait_group 1;\n" ::);
+        if constexpr (TH)
+            asm volatile("cp.async.wait_group 0;\n" ::);   // the face pass forms FP64 jumps
+        else
+            asm volatile("cp.async.wait_group 1;\n" ::);
         __syncwarp();
 
         // ---- V: broken gradient (MMA) and total flux of every volume node
@@ -395,11 +407,29 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
                     go_y[c] = ng[G_RY] * wr[c] + ng[G_SY] * ws[c];
                 }
             }
+            // the jump U+ - U- of the penalty (and theta) terms: a small
+            // difference of large values, formed in FP64 in the theta variant;
+            // the state G is evaluated at, and the theta weight (1/2 on an
+            // interior face, where both sides add their share)
+            float jmp[4], gs[4], wth = 1.0f;
+            {
+                const float ir = 1.0f / up[0];
+                gs[0] = up[0]; gs[1] = up[1] * ir; gs[2] = up[2] * ir; gs[3] = up[3] * ir;
+            }
             if (bt == BCT_INTERIOR) {
                 float um[4];
                 const float *gxm = go_x, *gym = go_y;
                 f4_to(sN[(e * 3 + f) * UN + vp], um);
                 const float pm = sPn[(e * 3 + f) * NpP + vp];
+                if constexpr (TH) {
+                    const long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        jmp[c] = cvt_d2f(sRaw[(e * 4 + c) * Np + vm] - sp.K0in[(nb * 4 + c) * Np + vp]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) jmp[c] = up[c] - um[c];
+                }
                 float Fnm[4], vxm[4], vym[4], D[4];
                 flux_n(um, pm, n1, n2, ph, Fnm);
                 visc_flux(um, gxm, gym, ph, vxm, vym);
@@ -407,8 +437,9 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const float Ftm = Fnm[c] - (vxm[c] * n1 + vym[c] * n2);
-                    dH[c] = 0.5f * (Ftp[c] - Ftm) - 0.5f * D[c] - sigma * (up[c] - um[c]);
+                    dH[c] = 0.5f * (Ftp[c] - Ftm) - 0.5f * D[c] - sigma * jmp[c];
                 }
+                wth = 0.5f;
             } else if (bt == BCT_FARFIELD) {
                 const float ub[4] = {ph.Uinf[0], ph.Uinf[1], ph.Uinf[2], ph.Uinf[3]};
                 float Fnp[4], Fnb[4], D[4];
@@ -417,7 +448,10 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
                 roe_dissipation(up, pp, ub, ph.pinf, n1, n2, ph, D);
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
-                    dH[c] = 0.5f * (Fnp[c] - Fnb[c]) - 0.5f * D[c] - sigma * (up[c] - ub[c]);
+                    jmp[c] = TH ? cvt_d2f(sRaw[(e * 4 + c) * Np + vm] - sp.uinf[c]) : up[c] - ub[c];
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    dH[c] = 0.5f * (Fnp[c] - Fnb[c]) - 0.5f * D[c] - sigma * jmp[c];
             } else {
                 const float *gxp = go_x, *gyp = go_y;
                 const float rb = up[0];
@@ -431,11 +465,27 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
                 for (int c = 0; c < 4; ++c) vnb[c] = vxb[c] * n1 + vyb[c] * n2;
                 if (ph.adiabatic) vnb[3] -= qx * n1 + qy * n2;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) dH[c] = Ftp[c] - (Fnb[c] - vnb[c] + sigma * (up[c] - ub[c]));
+                for (int c = 0; c < 4; ++c) jmp[c] = up[c] - ub[c];
+                // E+ - E^b = (|m+|^2 / rho - rho |v_w|^2) / 2 without the cancellation
+                if constexpr (TH) jmp[3] = 0.5f * (up[1] * up[1] + up[2] * up[2]) / rb - kw;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) dH[c] = Ftp[c] - (Fnb[c] - vnb[c] + sigma * jmp[c]);
+                gs[0] = rb; gs[1] = ph.vw1; gs[2] = ph.vw2; gs[3] = ub[3] / rb;
             }
             if (act)
                 *reinterpret_cast<float4 *>(sDH + e * HS + r * 4) =
                     make_float4(fsc * dH[0], fsc * dH[1], fsc * dH[2], fsc * dH[3]);
+            if constexpr (TH) {
+                float tx[4], ty[4];
+                theta_vec(gs[0], gs[1], gs[2], gs[3], jmp, n1, n2, ph, tx, ty);
+                const float sc = theta * wth * fsc;
+                if (act) {
+                    *reinterpret_cast<float4 *>(sTHx + e * HS + r * 4) =
+                        make_float4(sc * tx[0], sc * tx[1], sc * tx[2], sc * tx[3]);
+                    *reinterpret_cast<float4 *>(sTHy + e * HS + r * 4) =
+                        make_float4(sc * ty[0], sc * ty[1], sc * ty[2], sc * ty[3]);
+                }
+            }
         }
         asm volatile("cp.async.wait_group 0;\n" ::);
         __syncwarp();
@@ -459,6 +509,7 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
                 const int k = t + 4 * q;
                 bh[q] = (k < NF) ? hb[4 * k + bc] : 0.f;
             }
+            float cR[MT][4];
 #pragma unroll
             for (int mt = 0; mt < MT; ++mt) {
                 // divergence and lift, each with separate accumulators for
@@ -473,11 +524,77 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
 #pragma unroll
                 for (int ks = 0; ks < KL; ++ks)
                     mma3(l0, l1, frag(ent_l(mt, ks), 0), frag(ent_l(mt, ks), 1), bh[2 * ks], bh[2 * ks + 1]);
-                float cd[4];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) cd[c] = (l0[c] + l1[c]) - (d0[c] + d1[c]);
+                for (int c = 0; c < 4; ++c) cR[mt][c] = (l0[c] + l1[c]) - (d0[c] + d1[c]);
+            }
+            if constexpr (TH) {
+                // theta terms: lift the face vectors (x and y), map them to
+                // (r, s) at every node, then apply Wr, Ws (weak-form
+                // derivatives; Wr 1 != 0, so no reference is taken out)
+                float bx[2 * KL], by[2 * KL];
+                const float *xb = sTHx + (2 * nt + be) * HS, *yb = sTHy + (2 * nt + be) * HS;
+#pragma unroll
+                for (int q = 0; q < 2 * KL; ++q) {
+                    const int k = t + 4 * q;
+                    bx[q] = (k < NF) ? xb[4 * k + bc] : 0.f;
+                    by[q] = (k < NF) ? yb[4 * k + bc] : 0.f;
+                }
+                __syncwarp();   // every lane holds its flux B values: sF is overwritten below
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    float x0[4] = {0.f, 0.f, 0.f, 0.f}, x1[4] = {0.f, 0.f, 0.f, 0.f};
+                    float y0[4] = {0.f, 0.f, 0.f, 0.f}, y1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int ks = 0; ks < KL; ++ks) {
+                        mma3(x0, x1, frag(ent_l(mt, ks), 0), frag(ent_l(mt, ks), 1), bx[2 * ks], bx[2 * ks + 1]);
+                        mma3(y0, y1, frag(ent_l(mt, ks), 0), frag(ent_l(mt, ks), 1), by[2 * ks], by[2 * ks + 1]);
+                    }
+                    float cx[4], cy[4], Lx[4], Ly[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        cx[c] = x0[c] + x1[c];
+                        cy[c] = y0[c] + y1[c];
+                    }
+                    frag_to_node(cx, Lx, lane);
+                    frag_to_node(cy, Ly, lane);
+                    const int e = 2 * nt + ep, j = 16 * mt + jn;
+                    if (e < ne && j < Np) {
+                        const float *gg = sGeo + e * 16;
+                        float ar[4], as[4];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            ar[c] = gg[G_RX] * Lx[c] + gg[G_RY] * Ly[c];
+                            as[c] = gg[G_SX] * Lx[c] + gg[G_SY] * Ly[c];
+                        }
+                        float4 *fo = reinterpret_cast<float4 *>(sF + e * FS + j * 8);
+                        fo[0] = to_f4(ar);
+                        fo[1] = to_f4(as);
+                    }
+                }
+                __syncwarp();
+                float war[2 * KD], was[2 * KD];
+#pragma unroll
+                for (int q = 0; q < 2 * KD; ++q) {
+                    const int k = t + 4 * q;
+                    war[q] = (k < Np) ? fb[8 * k + bc] : 0.f;
+                    was[q] = (k < Np) ? fb[8 * k + 4 + bc] : 0.f;
+                }
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    float w0[4] = {0.f, 0.f, 0.f, 0.f}, w1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int ks = 0; ks < KD; ++ks) {
+                        mma3(w0, w1, frag(ent_w(0, mt, ks), 0), frag(ent_w(0, mt, ks), 1), war[2 * ks], war[2 * ks + 1]);
+                        mma3(w0, w1, frag(ent_w(1, mt, ks), 0), frag(ent_w(1, mt, ks), 1), was[2 * ks], was[2 * ks + 1]);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) cR[mt][c] += w0[c] + w1[c];
+                }
+            }
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
                 float R[4];
-                frag_to_node(cd, R, lane);
+                frag_to_node(cR[mt], R, lane);
                 const int e = 2 * nt + ep, j = 16 * mt + jn;
                 if (e < ne && j < Np) {
                     const long long base = (k0 + e) * 4 * Np + j;

@@ -82,14 +82,15 @@ bool stage_tc_supported(int p);
 int stage_tile_elems_tc();
 // units = K elements (single mesh) or the tile count of a batch tile table;
 // fused: five stages per cooperative launch with grid barriers
-cudaError_t stage_shape_tc(int p, long long units, bool batch, bool fused, LaunchShape &out);
+// theta: the SIP / NIPG variant (single mesh, stage-wise launches only)
+cudaError_t stage_shape_tc(int p, long long units, bool batch, bool fused, LaunchShape &out, bool theta = false);
 cudaError_t launch_stage_tc(int p, bool batch, bool fused, const LaunchShape &ls, const StageParams &sp,
                             const Phys<float> &ph, cudaStream_t st);
-// Dr, Ds [Np][Np] and LIFT [Np][NF] (FP64, row-major) -> the kernel's
+// Dr, Ds [Np][Np], LIFT [Np][NF], Wr, Ws [Np][Np] (FP64, row-major) -> the kernel's
 // operator table (TF32 hi / lo fragments of 16-row tiles, then (Dr, Ds) as
 // FP32 pairs [Np][Np])
 void build_tc_fragments(int Np, int NF, const double *Dr, const double *Ds, const double *LIFT,
-                        std::vector<float> &out);
+                        const double *Wr, const double *Ws, std::vector<float> &out);
 // FP32 copy [K][Np] float4 and FP64-recovered pressure [K][NpP] of a state
 cudaError_t launch_make_shadow(int p, const double *K0, long long K, double gm1, float4 *S,
                                float *Pr, cudaStream_t st);

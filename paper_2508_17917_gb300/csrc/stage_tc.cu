@@ -11,12 +11,12 @@ namespace {
 // persistent grid: SMs x resident blocks, capped by the warp tiles (units =
 // K elements, or the tile count of a batch tile table); the fused variant
 // must fit the grid on the GPU at once (cooperative launch)
-template <int P, bool BATCH, bool FUSE>
+template <int P, bool BATCH, bool FUSE, bool TH = false>
 cudaError_t shape_tc_p(long long units, LaunchShape &ls)
 {
     using S = ShapeTC<P>;
-    using L = TcLayout<P>;
-    auto kern = stage_tc_kernel<P, BATCH, FUSE>;
+    using L = TcLayout<P, TH>;
+    auto kern = stage_tc_kernel<P, BATCH, FUSE, TH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(L::bytes));
     if (e != cudaSuccess) return e;
@@ -39,7 +39,7 @@ cudaError_t shape_tc_p(long long units, LaunchShape &ls)
     ls.threads = S::NT;
     ls.smem = L::bytes;
     ls.elems_per_tile = S::WE;
-    ls.theta = false;
+    ls.theta = TH;
     ls.variant = 3;
     return cudaSuccess;
 }
@@ -66,8 +66,13 @@ cudaError_t launch_tc_p(const LaunchShape &ls, const StageParams &sp, const Phys
 }
 
 template <int P>
-cudaError_t shape_tc_any(long long units, bool batch, bool fused, LaunchShape &ls)
+cudaError_t shape_tc_any(long long units, bool batch, bool fused, bool theta, LaunchShape &ls)
 {
+    if (theta) {
+        // the theta variant runs stage-wise on a single mesh
+        if (batch || fused) return cudaErrorInvalidValue;
+        return shape_tc_p<P, false, false, true>(units, ls);
+    }
     if (batch) return fused ? shape_tc_p<P, true, true>(units, ls) : shape_tc_p<P, true, false>(units, ls);
     return fused ? shape_tc_p<P, false, true>(units, ls) : shape_tc_p<P, false, false>(units, ls);
 }
@@ -76,6 +81,10 @@ template <int P>
 cudaError_t launch_tc_any(bool batch, bool fused, const LaunchShape &ls, const StageParams &sp,
                           const Phys<float> &ph, cudaStream_t st)
 {
+    if (ls.theta) {
+        if (batch || fused) return cudaErrorInvalidValue;
+        return launch_pdl(stage_tc_kernel<P, false, false, true>, ls, st, sp, ph);
+    }
     if (batch) return fused ? launch_tc_p<P, true, true>(ls, sp, ph, st) : launch_tc_p<P, true, false>(ls, sp, ph, st);
     return fused ? launch_tc_p<P, false, true>(ls, sp, ph, st) : launch_tc_p<P, false, false>(ls, sp, ph, st);
 }
@@ -97,15 +106,15 @@ bool stage_tc_supported(int p) { return p >= 1 && p <= 6; }
 
 int stage_tile_elems_tc() { return ShapeTC<1>::WE; }
 
-cudaError_t stage_shape_tc(int p, long long units, bool batch, bool fused, LaunchShape &out)
+cudaError_t stage_shape_tc(int p, long long units, bool batch, bool fused, LaunchShape &out, bool theta)
 {
     switch (p) {
-    case 1: return shape_tc_any<1>(units, batch, fused, out);
-    case 2: return shape_tc_any<2>(units, batch, fused, out);
-    case 3: return shape_tc_any<3>(units, batch, fused, out);
-    case 4: return shape_tc_any<4>(units, batch, fused, out);
-    case 5: return shape_tc_any<5>(units, batch, fused, out);
-    case 6: return shape_tc_any<6>(units, batch, fused, out);
+    case 1: return shape_tc_any<1>(units, batch, fused, theta, out);
+    case 2: return shape_tc_any<2>(units, batch, fused, theta, out);
+    case 3: return shape_tc_any<3>(units, batch, fused, theta, out);
+    case 4: return shape_tc_any<4>(units, batch, fused, theta, out);
+    case 5: return shape_tc_any<5>(units, batch, fused, theta, out);
+    case 6: return shape_tc_any<6>(units, batch, fused, theta, out);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -126,17 +135,18 @@ cudaError_t launch_stage_tc(int p, bool batch, bool fused, const LaunchShape &ls
 
 // A operands of the three operators, zero-padded to 16 MT rows and 8 KD
 // (Dr, Ds) or 8 KL (LIFT) columns, in the order the kernel reads them:
-// entries Dr [MT][KD], Ds [MT][KD], LIFT [MT][KL], each [hi, lo][lane][a0..a3]
+// entries Dr [MT][KD], Ds [MT][KD], LIFT [MT][KL], Wr [MT][KD], Ws [MT][KD]
+// (the weak-form derivatives of the theta terms), each [hi, lo][lane][a0..a3]
 // with lane = 4 g + t, a0 = A[16 mt + g][8 ks + t], a1 = A[16 mt + g + 8][8 ks + t],
 // a2 = A[16 mt + g][8 ks + t + 4], a3 = A[16 mt + g + 8][8 ks + t + 4].  hi is
 // the FP64 entry rounded to FP32 and then to TF32; lo is the remainder
 // rounded the same way.  Followed by (Dr, Ds) in FP32 as interleaved pairs,
 // row-major (the face-node rows).
 void build_tc_fragments(int Np, int NF, const double *Dr, const double *Ds, const double *LIFT,
-                        std::vector<float> &out)
+                        const double *Wr, const double *Ws, std::vector<float> &out)
 {
     const int MT = (Np + 15) / 16, KD = (Np + 7) / 8, KL = (NF + 7) / 8;
-    const int nent = 2 * MT * KD + MT * KL;
+    const int nent = 4 * MT * KD + MT * KL;
     const size_t nfrag = static_cast<size_t>(nent) * 64;            // float4
     out.assign(nfrag * 4 + 2 * static_cast<size_t>(Np) * Np, 0.0f);
     auto put = [&](int ent, const double *A, int ncols, int mt, int ks) {
@@ -159,6 +169,10 @@ void build_tc_fragments(int Np, int NF, const double *Dr, const double *Ds, cons
             put((1 * MT + mt) * KD + ks, Ds, Np, mt, ks);
         }
         for (int ks = 0; ks < KL; ++ks) put(2 * MT * KD + mt * KL + ks, LIFT, NF, mt, ks);
+        for (int ks = 0; ks < KD; ++ks) {
+            put(2 * MT * KD + MT * KL + (0 * MT + mt) * KD + ks, Wr, Np, mt, ks);
+            put(2 * MT * KD + MT * KL + (1 * MT + mt) * KD + ks, Ws, Np, mt, ks);
+        }
     }
     float *d = out.data() + nfrag * 4;
     for (int i = 0; i < Np * Np; ++i) {

@@ -140,12 +140,65 @@ def test_ogrid_steps_tc(dg, variant):
     assert np.all(err <= 2e-5), err
 
 
-def test_tc_rejected_on_fp64_and_theta(dg):
+def test_tc_rejected_on_fp64_two_node_on_theta(dg):
     s = dg.Solver(dg_inputs.periodic_square(4), 3, "mixed", stream=stream(), theta=1.0, C1=0.05)
     with pytest.raises(dg.DGError) as e:
-        s.set_variant(3)
+        s.set_variant(2)
     assert e.value.status == -6
     s = dg.Solver(dg_inputs.periodic_square(4), 3, "fp64", stream=stream())
     with pytest.raises(dg.DGError) as e:
         s.set_variant(3)
     assert e.value.status == -6
+
+
+@pytest.mark.parametrize("theta", [1.0, -1.0, 0.5])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6])
+def test_rhs_periodic_tc_theta(dg, p, theta):
+    """SIP / NIPG (theta terms of Eq. dg_on_K) in the tensor-core shape:
+    theta vectors lifted by MMA, the weak-form derivatives Wr, Ws by MMA,
+    FP64 jumps."""
+    mesh = dg_inputs.periodic_square(5)
+    P = oracle.Problem(mesh, p, mu=5e-3, theta=theta, C1=0.05)
+    U = dg_inputs.perturb(to_kcn(dg_inputs.isentropic_vortex(P.x, P.y)), seed=3, amp=1e-2)
+    vw = (0.05, 0.02)
+    ref = P.rhs(U, vw=vw)
+    s = dg.Solver(mesh, p, "mixed", stream=stream(), mu=5e-3, theta=theta, C1=0.05)
+    s.set_variant(3)
+    assert s.variant == 3
+    s.set_state(U)
+    got = s.rhs(0.0, vw)
+    assert np.abs(got - ref).max() / np.abs(ref).max() <= rhs_tol(p)
+
+
+@pytest.mark.parametrize("theta", [1.0, -1.0])
+@pytest.mark.parametrize("p", [2, 4, 6])
+def test_rhs_ogrid_tc_theta(dg, p, theta):
+    mesh = dg_inputs.ogrid_cylinder(24, 8, 0.5, 4.0, seed=3)
+    kw = dict(mu=0.01, rho_inf=1.0, u_inf=1.0, v_inf=0.0, p_inf=17.857142857142858, theta=theta, C1=0.05)
+    P = oracle.Problem(mesh, p, **kw)
+    r = np.hypot(P.x, P.y)
+    U = to_kcn(dg_inputs.free_stream(P.x.shape, rho=1.0, u=1.0, v=0.0, p=kw["p_inf"]))
+    U[:, 1] *= np.tanh(3 * (r - 0.5))
+    U = dg_inputs.perturb(U, seed=12, amp=1e-3)
+    vw = (0.0, 0.05)
+    ref = P.rhs(U, vw=vw)
+    s = dg.Solver(mesh, p, "mixed", stream=stream(), **kw)
+    s.set_variant(3)
+    s.set_state(U)
+    got = s.rhs(0.0, vw)
+    assert np.abs(got - ref).max() / np.abs(ref).max() <= rhs_tol(p)
+
+
+def test_sip_50_steps_tc(dg):
+    mesh = dg_inputs.periodic_square(8)
+    p = 3
+    P = oracle.Problem(mesh, p, mu=2e-3, theta=1.0, C1=0.1)
+    U0 = dg_inputs.perturb(to_kcn(dg_inputs.isentropic_vortex(P.x, P.y)), seed=5, amp=1e-3)
+    dt, _ = P.dt(U0, 0.3)
+    ref = P.run(U0, 0.0, dt, 50)
+    s = dg.Solver(mesh, p, "mixed", stream=stream(), mu=2e-3, theta=1.0, C1=0.1)
+    s.set_variant(3)
+    s.set_state(U0)
+    s.steps(0.0, dt, 50)
+    err = rel_l2(P, s.get_state() - ref, ref)
+    assert np.all(err <= 2e-5), err
