@@ -309,9 +309,10 @@ def run_ours(args):
     dts = ssip.dt(0.3)
     ts, _ = timed_steps(dg, torch, ssip, dts, max(5, args.steps // 10), 2, flush, stream)
     vs = dof * 5 * len(ts) / (sum(ts) * 1e-3)
+    sip_kernel = {1: "dg::stage_mixed_kernel<4, true>", 3: "dg::stage_tc_kernel<4, false, false, true>"}
     sip = {"workload": "same mesh and state, SIP (theta = 1, C1 = 0.05)", "value": vs, "unit": UNIT,
            "ms_per_step": sum(ts) / len(ts), "sip_over_iip": vs / (value / ws),
-           "kernel": "dg::stage_mixed_kernel<4, true>"}
+           "kernel": sip_kernel.get(ssip.variant, str(ssip.variant)), "tuned_variant": ssip.variant}
     del ssip
 
     # --- large variant (working set well above L2), mixed path
