@@ -78,7 +78,7 @@ def kernel_hash(variant=2):
 
 PROFILE_OF_VARIANT = {1: "stage_kernel_mixed_p4.md", 2: "stage_kernel_mixed2_p4.md", 3: "stage_kernel_tc_p4.md"}
 KERNEL_OF_VARIANT = {1: "dg::stage_mixed_kernel<4, false>", 2: "dg::stage_mixed2_kernel<4, false>",
-                     3: "dg::stage_tc_kernel<4, false, false>"}
+                     3: "dg::stage_tc_kernel<4, false, false, false>"}
 SHAPE_OF_VARIANT = {1: "one node per thread", 2: "two nodes per thread",
                     3: "one warp per two elements, tensor-core contractions"}
 
