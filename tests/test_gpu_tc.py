@@ -202,3 +202,42 @@ def test_sip_50_steps_tc(dg):
     s.steps(0.0, dt, 50)
     err = rel_l2(P, s.get_state() - ref, ref)
     assert np.all(err <= 2e-5), err
+
+
+def _drop_element(mesh, k_drop):
+    """The mesh without element k_drop: an odd element count, so the last
+    two-element warp tile holds one element; the faces the removal exposes
+    become far-field faces."""
+    from dg_inputs.meshes import BC_FARFIELD, BC_INTERIOR, Mesh, _connect
+    keep = np.array([k for k in range(mesh.K) if k != k_drop])
+    EToV = mesh.EToV[keep].copy()
+    EToE, EToF, owner = _connect(EToV, np.arange(mesh.Nv))
+    bc = np.full(EToV.shape, BC_INTERIOR, dtype=np.int32)
+    old_bc = mesh.bc[keep]
+    for (k, f) in owner.values():
+        bc[k, f] = old_bc[k, f] if old_bc[k, f] != BC_INTERIOR else BC_FARFIELD
+    return Mesh(mesh.vx, mesh.vy, EToV, EToE.astype(np.int32), EToF.astype(np.int32), bc, None, "dropped")
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("p", [2, 4, 6])
+def test_rhs_odd_element_count(dg, p, variant):
+    """A ragged last tile in every tile shape (383 elements: the last warp
+    tile of the tensor-core shape holds one element), walls and far field."""
+    if variant == 2 and p == 6:
+        pytest.skip("covered at p = 2, 4")
+    mesh = _drop_element(dg_inputs.ogrid_cylinder(24, 8, 0.5, 4.0, seed=3), 100)
+    assert mesh.K % 2 == 1
+    kw = dict(mu=0.01, rho_inf=1.0, u_inf=1.0, v_inf=0.2, p_inf=17.857142857142858)
+    P = oracle.Problem(mesh, p, **kw)
+    r = np.hypot(P.x, P.y)
+    U = to_kcn(dg_inputs.free_stream(P.x.shape, rho=1.0, u=1.0, v=0.2, p=kw["p_inf"]))
+    U[:, 1] *= np.tanh(3 * (r - 0.5))
+    U = dg_inputs.perturb(U, seed=13, amp=1e-3)
+    vw = (0.0, 0.03)
+    ref = P.rhs(U, vw=vw)
+    s = dg.Solver(mesh, p, "mixed", stream=stream(), **kw)
+    s.set_variant(variant)
+    s.set_state(U)
+    got = s.rhs(0.0, vw)
+    assert np.abs(got - ref).max() / np.abs(ref).max() <= rhs_tol(p)
