@@ -2,9 +2,9 @@
 // on the tensor cores.
 //
 // Same method as dg_stage_mixed.cuh: the strong-form residual of Eq. dg_on_K
-// (IIP, theta = 0) and one stage of Algorithm 1, FP32 arithmetic with FP64
-// state, pressure recovery and registers.  What changes is how the work is
-// laid out:
+// (IIP, and with the template flag TH the SIP / NIPG theta terms) and one
+// stage of Algorithm 1, FP32 arithmetic with FP64 state, pressure recovery
+// and registers.  What changes is how the work is laid out:
 //
 // * Every warp owns a tile of WE = 2 elements from load to store.  It stages
 //   its own inputs with cp.async and synchronises with __syncwarp only, so the
@@ -25,6 +25,10 @@
 //   needed, which costs fewer instructions than an MMA of all 16); a
 //   boundary face names its own element, so a wall face gets the own
 //   gradient the same way.
+// * Theta variant: the face pass also forms the jumps in FP64 and the theta
+//   vectors; the update pass lifts them (MMA), maps them to (r, s) per node
+//   and applies the weak-form derivatives Wr, Ws (MMA, no reference node:
+//   Wr 1 != 0).
 //
 // MMA fragment layout (m16n8k8, row.col, TF32; lane = 4 g + t):
 //   A (16 x 8): a0 = A[g][t], a1 = A[g+8][t], a2 = A[g][t+4], a3 = A[g+8][t+4]
