@@ -68,11 +68,19 @@ KERNEL_FILES = {
 }
 
 
+def code_only(text):
+    """C++ source without comments and blank space (a comment edit does not
+    change the kernel)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_hash(variant=2):
     h = hashlib.sha256()
     for f in KERNEL_FILES[variant]:
-        with open(os.path.join(ROOT, "paper_2508_17917_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2508_17917_gb300", "csrc", f)) as fh:
+            h.update(code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
