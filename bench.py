@@ -585,7 +585,7 @@ def run_profile(args):
     from dg_inputs.states import to_kcn
     prec, n, theta, var = {"mixed512": ("mixed", 512, 0.0, 0), "mixed128": ("mixed", 128, 0.0, 0),
                            "fp64_128": ("fp64", 128, 0.0, 0), "sip128": ("mixed", 128, 1.0, 0),
-                           "tc512": ("mixed", 512, 0.0, 3)}[args.profile]
+                           "tc512": ("mixed", 512, 0.0, 3), "tcsip512": ("mixed", 512, 1.0, 3)}[args.profile]
     torch.cuda.set_device(0)
     mesh = vortex_problem(n)
     s = dg.Solver(mesh, P, prec, stream=torch.cuda.current_stream().cuda_stream, mu=1e-3,
@@ -613,7 +613,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3],
                     help="tile shape of the headline's mixed kernel (0: first-step tuner)")
-    ap.add_argument("--profile", choices=["mixed512", "mixed128", "fp64_128", "sip128", "tc512"], default=None)
+    ap.add_argument("--profile", choices=["mixed512", "mixed128", "fp64_128", "sip128", "tc512", "tcsip512"], default=None)
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
