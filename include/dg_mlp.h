@@ -17,6 +17,17 @@
  * Training minimises the mean over batch and outputs of (y - t)^2 with Adam
  * (beta1 = 0.9, beta2 = 0.999, eps = 1e-8, bias-corrected).
  *
+ * Two implementations of the same arithmetic:
+ * - chunked (the default when the network fits: inputs and width <= 128,
+ *   outputs <= 16, at most 8 layers): one kernel carries chunks of 32 rows
+ *   through the forward pass, the loss and the backward pass in shared
+ *   memory and leaves per-block gradient sums; a second adds them in block
+ *   order and applies Adam (two launches per training step);
+ * - layer by layer: one tiled GEMM per product with fused epilogues, and
+ *   separate loss, bias-sum, Adam and weight-copy kernels.
+ * Both round to bfloat16 at the same points; their FP32 sums run in
+ * different orders.  Each is deterministic.
+ *
  * Parameters (FP32, this order): for each layer, W row-major [n_out][n_in]
  * then b [n_out].  The library keeps the FP32 master copy, the Adam moments
  * and the bfloat16 copy of the weights on the device.  All calls run on a
@@ -60,6 +71,14 @@ int64_t dg_mlp_kernel_launches(const dg_mlp *m);
  * Errors: DG_EINVAL, DG_ECUDA. */
 dg_status dg_mlp_set_params(dg_mlp *m, const float *params, int on_device);
 dg_status dg_mlp_get_params(dg_mlp *m, float *params, int on_device);
+
+/* Use the chunked implementation (on != 0) or the layer-by-layer one.
+ * Errors: DG_EINVAL, DG_EUNSUPPORTED (on, but the network does not fit the
+ * chunked path). */
+dg_status dg_mlp_set_fused(dg_mlp *m, int on);
+
+/* 1 if the chunked implementation is in use, else 0 (also for NULL). */
+int dg_mlp_is_fused(const dg_mlp *m);
 
 /* y = net(x) for B rows: X device [B][n_in] FP32, Y device [B][n_out] FP32.
  * Errors: DG_EINVAL (null, B < 1 or > max_batch), DG_ECUDA. */

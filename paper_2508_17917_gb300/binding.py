@@ -27,7 +27,7 @@ __all__ = ["DG_OK", "DG_PRECISION_FP64", "DG_PRECISION_MIXED", "DG_SOURCE_NONE",
            "dg_batch_rigid", "BatchSolver",
            "dg_mlp_create", "dg_mlp_destroy", "dg_mlp_last_error", "dg_mlp_param_count",
            "dg_mlp_kernel_launches", "dg_mlp_set_params", "dg_mlp_get_params", "dg_mlp_forward",
-           "dg_mlp_loss_grad", "dg_mlp_train", "Mlp"]
+           "dg_mlp_loss_grad", "dg_mlp_train", "dg_mlp_set_fused", "dg_mlp_is_fused", "Mlp"]
 
 DG_OK = 0
 DG_PRECISION_FP64, DG_PRECISION_MIXED = 0, 1
@@ -118,6 +118,8 @@ EXPORTED = {
     "dg_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "dg_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "dg_mlp_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_float, C.c_void_p]),
+    "dg_mlp_set_fused": (C.c_int, [C.c_void_p, C.c_int]),
+    "dg_mlp_is_fused": (C.c_int, [C.c_void_p]),
 }
 
 _lib = None
@@ -624,6 +626,14 @@ def dg_mlp_train(m, X, T, nsteps, lr, loss_hist=None):
     _mcheck(lib().dg_mlp_train(m, _f32_dev(X), _f32_dev(T), int(X.shape[0]), int(nsteps), float(lr), lh), m)
 
 
+def dg_mlp_set_fused(m, on):
+    _mcheck(lib().dg_mlp_set_fused(m, 1 if on else 0), m)
+
+
+def dg_mlp_is_fused(m):
+    return bool(lib().dg_mlp_is_fused(m))
+
+
 class Mlp:
     """The surrogate network: the dg_mlp_* calls as methods (torch CUDA
     float32 tensors in and out)."""
@@ -670,3 +680,12 @@ class Mlp:
     @property
     def launches(self):
         return dg_mlp_kernel_launches(self.m)
+
+    @property
+    def fused(self):
+        """True while the chunked implementation is in use."""
+        return dg_mlp_is_fused(self.m)
+
+    @fused.setter
+    def fused(self, on):
+        dg_mlp_set_fused(self.m, on)

@@ -14,6 +14,7 @@
 
 #include "../../include/dg_mlp.h"
 #include "devbuf.h"
+#include "mlp_fused.cuh"
 
 namespace {
 
@@ -305,6 +306,13 @@ struct dg_mlp {
     dg::DevBuf<long long> dwoff, dwlen, dqoff;
     std::vector<dg::DevBuf<float>> Z, DZ32;            // per hidden layer / per layer
     std::vector<dg::DevBuf<bf16>> H, DZ16;             // H[0] = input
+    // chunked path (mlp_fused.cuh): layout, whether the network fits it and
+    // is using it, the most blocks per launch, per-block gradient slices
+    mlpf::Net fnet{};
+    bool fused_ok = false, fused_on = false;
+    int fgrid = 0;
+    dg::DevBuf<float> fpart, flpart;
+    dg::DevBuf<bf16> wstaged;                          // W and W^T per layer in the staging layout
     ~dg_mlp()
     {
         if (gexec) cudaGraphExecDestroy(gexec);
@@ -353,9 +361,12 @@ cudaError_t gemm(dg_mlp *m, const bf16 *A, int lda, const bf16 *B, int ldb, int 
 
 int blocks_for(long long n) { return static_cast<int>(std::min<long long>((n + 255) / 256, 4096)); }
 
+dg_status fused_forward(dg_mlp *m, const float *X, int B, float *Y);
+
 // forward for B rows of X (FP32 device): fills H, Z and writes Y
 dg_status forward(dg_mlp *m, const float *X, int B, float *Y)
 {
+    if (m->fused_on) return fused_forward(m, X, B, Y);
     const long long nx = static_cast<long long>(B) * m->n_in;
     to_bf16_kernel<<<blocks_for(nx), 256, 0, m->stream>>>(X, nx, m->H[0].ptr);
     m->launches += 1;
@@ -418,10 +429,72 @@ dg_status loss_grad(dg_mlp *m, const float *X, const float *T, int B, float *gra
     return DG_OK;
 }
 
+// ---- chunked path: every block takes whole 32-row chunks of the batch
+
+int fused_blocks(const dg_mlp *m, int B) { return std::min((B + mlpf::R - 1) / mlpf::R, m->fgrid); }
+
+dg_status fused_forward(dg_mlp *m, const float *X, int B, float *Y)
+{
+    mlpf::mlp_chunk_kernel<false><<<fused_blocks(m, B), mlpf::NT, m->fnet.bytes, m->stream>>>(
+        m->fnet, m->p.ptr, m->wstaged.ptr, X, nullptr, B, Y, nullptr, nullptr);
+    m->launches += 1;
+    M_CUDA(m, cudaGetLastError());
+    return DG_OK;
+}
+
+// gradient slices and loss sums of every block for the rows of X, T
+dg_status fused_chunks(dg_mlp *m, const float *X, const float *T, int B)
+{
+    mlpf::mlp_chunk_kernel<true><<<fused_blocks(m, B), mlpf::NT, m->fnet.bytes, m->stream>>>(
+        m->fnet, m->p.ptr, m->wstaged.ptr, X, T, B, nullptr, m->fpart.ptr, m->flpart.ptr);
+    m->launches += 1;
+    M_CUDA(m, cudaGetLastError());
+    return DG_OK;
+}
+
+dg_status fused_loss_grad(dg_mlp *m, const float *X, const float *T, int B, float *grad, float *loss)
+{
+    dg_status st = fused_chunks(m, X, T, B);
+    if (st != DG_OK) return st;
+    mlpf::mlp_reduce_kernel<false><<<blocks_for(m->nparams), 256, 0, m->stream>>>(
+        m->fnet, fused_blocks(m, B), m->fpart.ptr, m->flpart.ptr, static_cast<long long>(B) * m->n_out, grad, loss,
+        nullptr, nullptr, nullptr, nullptr, nullptr, mlpf::Adam{});
+    m->launches += 1;
+    M_CUDA(m, cudaGetLastError());
+    return DG_OK;
+}
+
+// one Adam step: loss (before the update) to *loss; bias corrections bc1,
+// bc2, or those of step *cnt in bc when bc is set
+dg_status fused_step(dg_mlp *m, const float *X, const float *T, int B, float *loss, float lr, float bc1, float bc2,
+                     const float *bc, const int *cnt)
+{
+    dg_status st = fused_chunks(m, X, T, B);
+    if (st != DG_OK) return st;
+    const mlpf::Adam o{lr, 0.9f, 0.999f, 1e-8f, bc1, bc2, bc, cnt};
+    mlpf::mlp_reduce_kernel<true><<<blocks_for(m->nparams), 256, 0, m->stream>>>(
+        m->fnet, fused_blocks(m, B), m->fpart.ptr, m->flpart.ptr, static_cast<long long>(B) * m->n_out, nullptr,
+        loss, m->p.ptr, m->m.ptr, m->v.ptr, m->wstaged.ptr, m->wq.ptr, o);
+    m->launches += 1;
+    M_CUDA(m, cudaGetLastError());
+    return DG_OK;
+}
+
 dg_status refresh_bf16(dg_mlp *m)
 {
     weights_bf16_kernel<<<blocks_for(m->nq), 256, 0, m->stream>>>(m->p.ptr, m->dwoff.ptr, m->dwlen.ptr, m->nl,
                                                                  m->wq.ptr, m->dqoff.ptr);
+    m->launches += 1;
+    M_CUDA(m, cudaGetLastError());
+    return DG_OK;
+}
+
+// the chunked path's staged weight copies from the FP32 parameters
+dg_status refresh_staged(dg_mlp *m)
+{
+    if (!m->fused_ok) return DG_OK;
+    mlpf::mlp_stage_copies_kernel<<<blocks_for(m->nparams), 256, 0, m->stream>>>(m->fnet, m->p.ptr,
+                                                                                m->wstaged.ptr);
     m->launches += 1;
     M_CUDA(m, cudaGetLastError());
     return DG_OK;
@@ -529,7 +602,31 @@ dg_status dg_mlp_create(int n_in, int width, int depth, int n_out, int max_batch
         delete m;
         return DG_ECUDA;
     }
-    if (refresh_bf16(m) != DG_OK || cudaStreamSynchronize(m->stream) != cudaSuccess) {
+    {
+        // the chunked path, if the layers fit a block's shared memory
+        int dev = 0, smax = 0, sms = 0;
+        chk(cudaGetDevice(&dev));
+        chk(cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        chk(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (e == cudaSuccess && mlpf::plan(m->fnet, m->nl, m->din.data(), m->dout.data(), m->woff.data(),
+                                           m->boff.data(), m->qoff.data(), m->nparams, static_cast<size_t>(smax))) {
+            const int bytes = static_cast<int>(m->fnet.bytes);
+            chk(cudaFuncSetAttribute(mlpf::mlp_chunk_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+            chk(cudaFuncSetAttribute(mlpf::mlp_chunk_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+            m->fgrid = std::max(1, std::min(sms, (max_batch + mlpf::R - 1) / mlpf::R));
+            chk(m->fpart.alloc(static_cast<size_t>(m->fgrid) * static_cast<size_t>(m->nparams)));
+            chk(m->flpart.alloc(static_cast<size_t>(m->fgrid)));
+            chk(m->wstaged.alloc(static_cast<size_t>(m->fnet.nstaged)));
+            if (e == cudaSuccess) chk(cudaMemset(m->wstaged.ptr, 0, sizeof(bf16) * m->fnet.nstaged));
+            m->fused_ok = m->fused_on = (e == cudaSuccess);
+        }
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete m;
+        return DG_ECUDA;
+    }
+    if (refresh_bf16(m) != DG_OK || refresh_staged(m) != DG_OK || cudaStreamSynchronize(m->stream) != cudaSuccess) {
         cudaGetLastError();
         delete m;
         return DG_ECUDA;
@@ -561,6 +658,7 @@ dg_status dg_mlp_set_params(dg_mlp *m, const float *params, int on_device)
     M_CUDA(m, cudaMemsetAsync(m->v.ptr, 0, m->nparams * sizeof(float), m->stream));
     m->step = 0;
     dg_status st = refresh_bf16(m);
+    if (st == DG_OK) st = refresh_staged(m);
     if (st != DG_OK) return st;
     M_CUDA(m, cudaStreamSynchronize(m->stream));
     return DG_OK;
@@ -576,6 +674,28 @@ dg_status dg_mlp_get_params(dg_mlp *m, float *params, int on_device)
     M_CUDA(m, cudaStreamSynchronize(m->stream));
     return DG_OK;
 }
+
+dg_status dg_mlp_set_fused(dg_mlp *m, int on)
+{
+    if (!m) return DG_EINVAL;
+    m->err.clear();
+    if (on && !m->fused_ok) return mfail(m, DG_EUNSUPPORTED, "the layers do not fit the chunked path");
+    if ((on != 0) == m->fused_on) return DG_OK;
+    if (m->gexec) {
+        cudaGraphExecDestroy(m->gexec);
+        m->gexec = nullptr;
+    }
+    m->fused_on = on != 0;
+    if (m->fused_on) {
+        // the layer-by-layer kernels keep only the row-major bf16 copy current
+        dg_status st = refresh_staged(m);
+        if (st != DG_OK) return st;
+        M_CUDA(m, cudaStreamSynchronize(m->stream));
+    }
+    return DG_OK;
+}
+
+int dg_mlp_is_fused(const dg_mlp *m) { return (m && m->fused_on) ? 1 : 0; }
 
 dg_status dg_mlp_forward(dg_mlp *m, const float *X, int B, float *Y)
 {
@@ -596,9 +716,13 @@ dg_status dg_mlp_loss_grad(dg_mlp *m, const float *X, const float *T, int B, flo
     dg_status st = check_rows(m, X, T, B);
     if (st != DG_OK) return st;
     if (!grad || !loss) return mfail(m, DG_EINVAL, "null output");
-    dg::DevBuf<float> y;
-    M_CUDA(m, y.alloc(static_cast<size_t>(B) * m->n_out));
-    st = loss_grad(m, X, T, B, grad, loss, y.ptr);
+    if (m->fused_on) {
+        st = fused_loss_grad(m, X, T, B, grad, loss);
+    } else {
+        dg::DevBuf<float> y;
+        M_CUDA(m, y.alloc(static_cast<size_t>(B) * m->n_out));
+        st = loss_grad(m, X, T, B, grad, loss, y.ptr);
+    }
     if (st != DG_OK) return st;
     M_CUDA(m, cudaStreamSynchronize(m->stream));
     return DG_OK;
@@ -615,11 +739,18 @@ dg_status dg_mlp_train(dg_mlp *m, const float *X, const float *T, int B, int nst
     if (!m->yscr.ptr) M_CUDA(m, m->yscr.alloc(static_cast<size_t>(m->max_batch) * m->n_out));
     if (nsteps < 8) {
         for (int n = 0; n < nsteps; ++n) {
-            st = loss_grad(m, X, T, B, m->g.ptr, loss_hist ? loss_hist + n : m->lossbuf.ptr, m->yscr.ptr);
+            float *lo = loss_hist ? loss_hist + n : m->lossbuf.ptr;
+            const float bc1 = static_cast<float>(1.0 - std::pow(0.9, static_cast<double>(m->step + 1)));
+            const float bc2 = static_cast<float>(1.0 - std::pow(0.999, static_cast<double>(m->step + 1)));
+            if (m->fused_on) {
+                st = fused_step(m, X, T, B, lo, lr, bc1, bc2, nullptr, nullptr);
+                if (st != DG_OK) return st;
+                m->step += 1;
+                continue;
+            }
+            st = loss_grad(m, X, T, B, m->g.ptr, lo, m->yscr.ptr);
             if (st != DG_OK) return st;
             m->step += 1;
-            const float bc1 = static_cast<float>(1.0 - std::pow(0.9, static_cast<double>(m->step)));
-            const float bc2 = static_cast<float>(1.0 - std::pow(0.999, static_cast<double>(m->step)));
             adam_kernel<<<blocks_for(m->nparams), 256, 0, m->stream>>>(m->p.ptr, m->g.ptr, m->m.ptr, m->v.ptr,
                                                                       m->nparams, lr, b1, b2, eps, bc1, bc2);
             m->launches += 1;
@@ -658,12 +789,19 @@ dg_status dg_mlp_train(dg_mlp *m, const float *X, const float *T, int B, int nst
         }
         const int64_t l0 = m->launches;
         M_CUDA(m, cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
-        st = loss_grad(m, X, T, B, m->g.ptr, m->lossbuf.ptr, m->yscr.ptr);
-        adam_indexed_kernel<<<blocks_for(m->nparams), 256, 0, m->stream>>>(m->p.ptr, m->g.ptr, m->m.ptr, m->v.ptr,
-                                                                          m->nparams, lr, b1, b2, eps, m->bc.ptr,
-                                                                          m->cnt.ptr);
-        record_loss_kernel<<<1, 32, 0, m->stream>>>(m->lossbuf.ptr, loss_hist, m->cnt.ptr);
-        if (st == DG_OK) st = refresh_bf16(m);
+        if (m->fused_on) {
+            st = fused_step(m, X, T, B, m->lossbuf.ptr, lr, 1.0f, 1.0f, m->bc.ptr, m->cnt.ptr);
+            record_loss_kernel<<<1, 32, 0, m->stream>>>(m->lossbuf.ptr, loss_hist, m->cnt.ptr);
+            m->launches += 1;
+        } else {
+            st = loss_grad(m, X, T, B, m->g.ptr, m->lossbuf.ptr, m->yscr.ptr);
+            adam_indexed_kernel<<<blocks_for(m->nparams), 256, 0, m->stream>>>(m->p.ptr, m->g.ptr, m->m.ptr,
+                                                                              m->v.ptr, m->nparams, lr, b1, b2, eps,
+                                                                              m->bc.ptr, m->cnt.ptr);
+            record_loss_kernel<<<1, 32, 0, m->stream>>>(m->lossbuf.ptr, loss_hist, m->cnt.ptr);
+            m->launches += 2;
+            if (st == DG_OK) st = refresh_bf16(m);
+        }
         cudaGraph_t graph = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(m->stream, &graph);
         if (st != DG_OK) {
@@ -674,7 +812,7 @@ dg_status dg_mlp_train(dg_mlp *m, const float *X, const float *T, int B, int nst
         const cudaError_t ei = cudaGraphInstantiate(&m->gexec, graph, 0);
         cudaGraphDestroy(graph);
         M_CUDA(m, ei);
-        m->glaunches = m->launches - l0 + 2;
+        m->glaunches = m->launches - l0;
         m->launches = l0;
         m->gkey[0] = X;
         m->gkey[1] = T;

@@ -30,6 +30,18 @@ def dg():
     return dg
 
 
+IMPLS = ["chunked", "layers"]
+
+
+def make(dg, impl, *args, **kw):
+    """A network on the chunked implementation (the default where the
+    layers fit) or on the layer-by-layer one."""
+    net = dg.Mlp(*args, **kw)
+    net.fused = impl == "chunked"
+    assert net.fused == (impl == "chunked")
+    return net
+
+
 def sizes():
     return omlp.layer_sizes(N_IN, WIDTH, DEPTH, N_OUT)
 
@@ -38,10 +50,11 @@ def rel_l2(a, b):
     return np.linalg.norm(np.asarray(a, float) - b) / np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("B", [1, 77, 300, 4096])
-def test_forward_matches_oracle(dg, B):
+@pytest.mark.parametrize("impl", IMPLS)
+@pytest.mark.parametrize("B", [1, 77, 300, 4096, 8192])
+def test_forward_matches_oracle(dg, B, impl):
     import torch
-    net = dg.Mlp(N_IN, WIDTH, DEPTH, N_OUT, max_batch=4096, seed=3)
+    net = make(dg, impl, N_IN, WIDTH, DEPTH, N_OUT, max_batch=8192, seed=3)
     p = net.get_params().astype(np.float64)
     rng = np.random.default_rng(B)
     x = rng.normal(size=(B, N_IN)).astype(np.float32)
@@ -63,10 +76,11 @@ def test_init_is_seeded_uniform(dg):
     assert all(np.all(b == 0) for b in bs)
 
 
-@pytest.mark.parametrize("B", [5, 513])
-def test_loss_and_gradient_match_oracle(dg, B):
+@pytest.mark.parametrize("impl", IMPLS)
+@pytest.mark.parametrize("B", [5, 513, 6000])
+def test_loss_and_gradient_match_oracle(dg, B, impl):
     import torch
-    net = dg.Mlp(N_IN, WIDTH, DEPTH, N_OUT, max_batch=1024, seed=7)
+    net = make(dg, impl, N_IN, WIDTH, DEPTH, N_OUT, max_batch=8192, seed=7)
     rng = np.random.default_rng(11 + B)
     p = net.get_params().astype(np.float64)
     p += 0.05 * rng.normal(size=p.size)           # non-zero biases too
@@ -87,9 +101,10 @@ def test_loss_and_gradient_match_oracle(dg, B):
             o += n
 
 
-def test_adam_step_matches_oracle(dg):
+@pytest.mark.parametrize("impl", IMPLS)
+def test_adam_step_matches_oracle(dg, impl):
     import torch
-    net = dg.Mlp(N_IN, WIDTH, DEPTH, N_OUT, max_batch=1024, seed=9)
+    net = make(dg, impl, N_IN, WIDTH, DEPTH, N_OUT, max_batch=1024, seed=9)
     rng = np.random.default_rng(4)
     x = torch.from_numpy(rng.normal(size=(256, N_IN)).astype(np.float32)).cuda()
     t = torch.from_numpy(rng.normal(size=(256, N_OUT)).astype(np.float32)).cuda()
@@ -102,9 +117,10 @@ def test_adam_step_matches_oracle(dg):
     assert np.abs(p1 - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
 
 
-def test_training_fits_a_smooth_map(dg):
+@pytest.mark.parametrize("impl", IMPLS)
+def test_training_fits_a_smooth_map(dg, impl):
     import torch
-    net = dg.Mlp(8, 64, 2, 2, max_batch=2048, seed=1)
+    net = make(dg, impl, 8, 64, 2, 2, max_batch=2048, seed=1)
     rng = np.random.default_rng(0)
     x = rng.uniform(-1, 1, size=(2048, 8)).astype(np.float32)
     t = np.stack([np.sin(2 * x[:, 0] + x[:, 1]), x[:, 2] * x[:, 3]], axis=1).astype(np.float32)
@@ -114,7 +130,8 @@ def test_training_fits_a_smooth_map(dg):
     assert np.all(np.isfinite(hist))
 
 
-def test_graph_replayed_training_equals_stepwise(dg):
+@pytest.mark.parametrize("impl", IMPLS)
+def test_graph_replayed_training_equals_stepwise(dg, impl):
     """Runs of 8 steps and more replay one captured step from a CUDA graph (the
     step index and the loss history on the device); the result is the same,
     bit for bit, as the same steps taken one call at a time."""
@@ -122,8 +139,8 @@ def test_graph_replayed_training_equals_stepwise(dg):
     rng = np.random.default_rng(6)
     x = torch.from_numpy(rng.normal(size=(512, N_IN)).astype(np.float32)).cuda()
     t = torch.from_numpy(rng.normal(size=(512, N_OUT)).astype(np.float32)).cuda()
-    a = dg.Mlp(N_IN, WIDTH, DEPTH, N_OUT, max_batch=1024, seed=5)
-    b = dg.Mlp(N_IN, WIDTH, DEPTH, N_OUT, max_batch=1024, seed=5)
+    a = make(dg, impl, N_IN, WIDTH, DEPTH, N_OUT, max_batch=1024, seed=5)
+    b = make(dg, impl, N_IN, WIDTH, DEPTH, N_OUT, max_batch=1024, seed=5)
     ha = a.train(x, t, 12, 1e-3).cpu().numpy()
     hb = np.concatenate([b.train(x, t, 1, 1e-3).cpu().numpy() for _ in range(12)])
     assert np.array_equal(a.get_params(), b.get_params())
@@ -133,3 +150,75 @@ def test_graph_replayed_training_equals_stepwise(dg):
     hb2 = np.concatenate([b.train(x, t, 1, 1e-3).cpu().numpy() for _ in range(10)])
     assert np.array_equal(a.get_params(), b.get_params())
     assert np.array_equal(ha2, hb2)
+
+
+def test_chunked_and_layer_paths_agree(dg):
+    """The two implementations round at the same points: outputs, loss and
+    gradient agree to FP32 summation order (plus rare one-ulp bf16 flips),
+    and a few training steps stay together."""
+    import torch
+    rng = np.random.default_rng(21)
+    x = torch.from_numpy(rng.normal(size=(1000, N_IN)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.normal(size=(1000, N_OUT)).astype(np.float32)).cuda()
+    a = make(dg, "chunked", N_IN, WIDTH, DEPTH, N_OUT, max_batch=1024, seed=2)
+    b = make(dg, "layers", N_IN, WIDTH, DEPTH, N_OUT, max_batch=1024, seed=2)
+    ya, yb = a.forward(x).cpu().numpy(), b.forward(x).cpu().numpy()
+    assert rel_l2(ya, yb) <= 1e-3
+    la, ga = a.loss_grad(x, t)
+    lb, gb = b.loss_grad(x, t)
+    assert abs(la - lb) <= 1e-5 * lb
+    assert rel_l2(ga.cpu().numpy(), gb.cpu().numpy()) <= 2e-3
+    ha = a.train(x, t, 20, 1e-3).cpu().numpy()
+    hb = b.train(x, t, 20, 1e-3).cpu().numpy()
+    assert np.abs(ha - hb).max() <= 1e-3 * np.abs(hb).max()
+
+
+def test_chunked_path_selection_and_launches(dg):
+    """The chunked path is the default where the layers fit (two launches per
+    training step, three when a step is replayed from the graph: the loss
+    history entry is one more); a wider network keeps the layer-by-layer
+    kernels and refuses the chunked path."""
+    import torch
+    rng = np.random.default_rng(1)
+    x = torch.from_numpy(rng.normal(size=(256, N_IN)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.normal(size=(256, N_OUT)).astype(np.float32)).cuda()
+    net = dg.Mlp(N_IN, WIDTH, DEPTH, N_OUT, max_batch=1024, seed=0)
+    assert net.fused
+    n0 = net.launches
+    net.train(x, t, 3, 1e-3)
+    assert net.launches - n0 == 2 * 3
+    n0 = net.launches
+    net.train(x, t, 10, 1e-3)
+    assert net.launches - n0 == 3 * 10
+    wide = dg.Mlp(N_IN, 256, 2, N_OUT, max_batch=512, seed=0)
+    assert not wide.fused
+    with pytest.raises(dg.DGError):
+        wide.fused = True
+    y = wide.forward(x).cpu().numpy()
+    ref, _ = omlp.forward(wide.get_params().astype(np.float64), omlp.layer_sizes(N_IN, 256, 2, N_OUT),
+                          x.cpu().numpy(), bf16=True)
+    assert rel_l2(y, ref) <= 2e-3
+
+
+@pytest.mark.parametrize("n_in,width,depth,n_out", [(67, 128, 5, 2), (5, 10, 1, 16), (30, 40, 2, 3)])
+def test_chunked_path_other_shapes(dg, n_in, width, depth, n_out):
+    """Widths that are not multiples of the 16-wide MMA steps, 16 outputs, and
+    a network deep enough that only one weight staging buffer fits."""
+    import torch
+    net = make(dg, "chunked", n_in, width, depth, n_out, max_batch=2048, seed=4)
+    rng = np.random.default_rng(n_in + width)
+    p = net.get_params().astype(np.float64)
+    p += 0.05 * rng.normal(size=p.size)
+    net.set_params(p.astype(np.float32))
+    p = p.astype(np.float32).astype(np.float64)
+    B = 1111
+    x = rng.normal(size=(B, n_in)).astype(np.float32)
+    t = rng.normal(size=(B, n_out)).astype(np.float32)
+    sz = omlp.layer_sizes(n_in, width, depth, n_out)
+    y = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref_y, _ = omlp.forward(p, sz, x, bf16=True)
+    assert rel_l2(y, ref_y) <= 2e-3
+    loss, g = net.loss_grad(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    ref_loss, ref_g = omlp.loss_and_grad(p, sz, x, t, bf16=True)
+    assert abs(loss - ref_loss) <= 1e-3 * ref_loss
+    assert rel_l2(g.cpu().numpy(), ref_g) <= 2e-3
