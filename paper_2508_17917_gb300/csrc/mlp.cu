@@ -433,6 +433,8 @@ dg_status loss_grad(dg_mlp *m, const float *X, const float *T, int B, float *gra
 
 int fused_blocks(const dg_mlp *m, int B) { return std::min((B + mlpf::R - 1) / mlpf::R, m->fgrid); }
 
+int reduce_blocks(const dg_mlp *m) { return static_cast<int>((m->nparams + mlpf::RP - 1) / mlpf::RP); }
+
 dg_status fused_forward(dg_mlp *m, const float *X, int B, float *Y)
 {
     mlpf::mlp_chunk_kernel<false><<<fused_blocks(m, B), mlpf::NT, m->fnet.bytes, m->stream>>>(
@@ -456,7 +458,7 @@ dg_status fused_loss_grad(dg_mlp *m, const float *X, const float *T, int B, floa
 {
     dg_status st = fused_chunks(m, X, T, B);
     if (st != DG_OK) return st;
-    mlpf::mlp_reduce_kernel<false><<<blocks_for(m->nparams), 256, 0, m->stream>>>(
+    mlpf::mlp_reduce_kernel<false><<<reduce_blocks(m), mlpf::RP * mlpf::RQ, 0, m->stream>>>(
         m->fnet, fused_blocks(m, B), m->fpart.ptr, m->flpart.ptr, static_cast<long long>(B) * m->n_out, grad, loss,
         nullptr, nullptr, nullptr, nullptr, nullptr, mlpf::Adam{});
     m->launches += 1;
@@ -472,7 +474,7 @@ dg_status fused_step(dg_mlp *m, const float *X, const float *T, int B, float *lo
     dg_status st = fused_chunks(m, X, T, B);
     if (st != DG_OK) return st;
     const mlpf::Adam o{lr, 0.9f, 0.999f, 1e-8f, bc1, bc2, bc, cnt};
-    mlpf::mlp_reduce_kernel<true><<<blocks_for(m->nparams), 256, 0, m->stream>>>(
+    mlpf::mlp_reduce_kernel<true><<<reduce_blocks(m), mlpf::RP * mlpf::RQ, 0, m->stream>>>(
         m->fnet, fused_blocks(m, B), m->fpart.ptr, m->flpart.ptr, static_cast<long long>(B) * m->n_out, nullptr,
         loss, m->p.ptr, m->m.ptr, m->v.ptr, m->wstaged.ptr, m->wq.ptr, o);
     m->launches += 1;
