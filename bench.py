@@ -583,12 +583,13 @@ def run_profile(args):
     import dg_inputs
     import paper_2508_17917_gb300 as dg
     from dg_inputs.states import to_kcn
-    prec, n, theta, var = {"mixed512": ("mixed", 512, 0.0, 0), "mixed128": ("mixed", 128, 0.0, 0),
-                           "fp64_128": ("fp64", 128, 0.0, 0), "sip128": ("mixed", 128, 1.0, 0),
-                           "tc512": ("mixed", 512, 0.0, 3), "tcsip512": ("mixed", 512, 1.0, 3)}[args.profile]
+    prec, n, theta, var, p = {"mixed512": ("mixed", 512, 0.0, 0, P), "mixed128": ("mixed", 128, 0.0, 0, P),
+                              "fp64_128": ("fp64", 128, 0.0, 0, P), "sip128": ("mixed", 128, 1.0, 0, P),
+                              "tc512": ("mixed", 512, 0.0, 3, P), "tcsip512": ("mixed", 512, 1.0, 3, P),
+                              "tc6_375": ("mixed", 375, 0.0, 3, 6)}[args.profile]
     torch.cuda.set_device(0)
     mesh = vortex_problem(n)
-    s = dg.Solver(mesh, P, prec, stream=torch.cuda.current_stream().cuda_stream, mu=1e-3,
+    s = dg.Solver(mesh, p, prec, stream=torch.cuda.current_stream().cuda_stream, mu=1e-3,
                   theta=theta, C1=0.05 if theta else 0.01)
     if var:
         s.set_variant(var)
@@ -613,7 +614,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3],
                     help="tile shape of the headline's mixed kernel (0: first-step tuner)")
-    ap.add_argument("--profile", choices=["mixed512", "mixed128", "fp64_128", "sip128", "tc512", "tcsip512"], default=None)
+    ap.add_argument("--profile", choices=["mixed512", "mixed128", "fp64_128", "sip128", "tc512", "tcsip512", "tc6_375"], default=None)
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

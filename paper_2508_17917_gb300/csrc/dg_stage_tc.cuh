@@ -64,6 +64,9 @@ struct ShapeTC {
     static constexpr int UN = Np + ((13 - Np % 8) % 8);          // >= Np, = 5 mod 8
     static constexpr int FS = 128 * MT + 4;       // = 4 mod 32
     static constexpr int HS = 32 * KL + 16;       // = 16 mod 32
+    // row stride (float2) of the (Dr, Ds) rows the face pass reads, one row
+    // per lane: odd, so 16 consecutive rows start in distinct bank pairs
+    static constexpr int DS = Np | 1;
     // operator fragments: Dr and Ds [MT][KD], LIFT [MT][KL], then (theta
     // variant) Wr and Ws [MT][KD], each [hi, lo][lane]
     static constexpr int NENT = 2 * MT * KD + MT * KL;           // entries of the IIP kernel
@@ -84,8 +87,8 @@ struct TcLayout {
     // block header
     static constexpr size_t hFrag = 0;                                      // float4 [NFRAG] if FRAG_SMEM
     static constexpr size_t hFm = hFrag + (S::FRAG_SMEM ? sizeof(float4) * NFRAG : 0);      // int [NF]
-    static constexpr size_t hD = hFm + al(sizeof(int) * NF);                // float2 [Np][Np]: (Dr, Ds)
-    static constexpr size_t header = hD + al(sizeof(float2) * Np * Np);
+    static constexpr size_t hD = hFm + al(sizeof(int) * NF);                // float2 [Np][DS]: (Dr, Ds)
+    static constexpr size_t header = hD + al(sizeof(float2) * Np * S::DS);
     // one region per warp
     static constexpr size_t oConn = 0;                                      // int4 [WE]
     static constexpr size_t oGeo = oConn + al(16 * WE);                     // float [WE][16]
@@ -171,7 +174,7 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
             for (int i = tid; i < L::NFRAG; i += S::NT) dst[i] = gFrag[i];
         const float2 *dtab = reinterpret_cast<const float2 *>(gFrag + S::NFRAG_ALL);
         float2 *dD = reinterpret_cast<float2 *>(smem_raw + L::hD);
-        for (int i = tid; i < Np * Np; i += S::NT) dD[i] = dtab[i];
+        for (int i = tid; i < Np * Np; i += S::NT) dD[(i / Np) * S::DS + i % Np] = dtab[i];
         for (int i = tid; i < NF; i += S::NT) sFm[i] = sp.fmask[i];
     }
     __syncthreads();
@@ -404,7 +407,7 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
                 const int row = (bt == BCT_INTERIOR) ? vp : vm;
                 float wr[4] = {0.f, 0.f, 0.f, 0.f}, ws[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int j = 0; j < Np; ++j) acc_rs(wr, ws, sD[row * Np + j], src[j]);
+                for (int j = 0; j < Np; ++j) acc_rs(wr, ws, sD[row * S::DS + j], src[j]);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     go_x[c] = ng[G_RX] * wr[c] + ng[G_SX] * ws[c];
