@@ -222,3 +222,23 @@ def test_chunked_path_other_shapes(dg, n_in, width, depth, n_out):
     ref_loss, ref_g = omlp.loss_and_grad(p, sz, x, t, bf16=True)
     assert abs(loss - ref_loss) <= 1e-3 * ref_loss
     assert rel_l2(g.cpu().numpy(), ref_g) <= 2e-3
+
+
+def test_switching_implementations_keeps_the_weights(dg):
+    """Training on the layer-by-layer kernels updates the parameters and
+    their row-major bf16 copy only; switching back to the chunked path
+    refreshes its staged copy, so both paths then compute the same outputs."""
+    import torch
+    rng = np.random.default_rng(8)
+    x = torch.from_numpy(rng.normal(size=(300, N_IN)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.normal(size=(300, N_OUT)).astype(np.float32)).cuda()
+    net = make(dg, "chunked", N_IN, WIDTH, DEPTH, N_OUT, max_batch=512, seed=12)
+    net.train(x, t, 3, 1e-2)
+    net.fused = False
+    net.train(x, t, 3, 1e-2)
+    y_layers = net.forward(x).cpu().numpy()
+    net.fused = True
+    y_chunked = net.forward(x).cpu().numpy()
+    assert rel_l2(y_chunked, y_layers) <= 1e-3
+    ref, _ = omlp.forward(net.get_params().astype(np.float64), sizes(), x.cpu().numpy(), bf16=True)
+    assert rel_l2(y_chunked, ref) <= 2e-3
