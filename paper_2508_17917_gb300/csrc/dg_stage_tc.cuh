@@ -151,8 +151,10 @@ __device__ __forceinline__ void frag_to_node(const float c[4], float v[4], int l
     v[3] = odd ? c[3] : ry;
 }
 
+// Six blocks per SM (80 registers) for the stage-wise IIP kernel up to p = 4;
+// four (128 registers) for the fused, theta and two-tile (p = 5, 6) kernels.
 template <int P, bool BATCH = false, bool FUSE = false, bool TH = false>
-__global__ void __launch_bounds__(128, (FUSE || TH || ShapeTC<P>::MT > 1) ? 4 : 5)
+__global__ void __launch_bounds__(128, (FUSE || TH || ShapeTC<P>::MT > 1) ? 4 : 6)
 stage_tc_kernel(StageParams sp, Phys<float> ph)
 {
     using S = ShapeTC<P>;
