@@ -501,7 +501,9 @@ def run_mlp(dg, torch, np, B=4096, steps=200):
     rng = np.random.default_rng(0)
     X = torch.from_numpy(rng.normal(size=(B, 67)).astype(np.float32)).cuda()
     T = torch.from_numpy(rng.normal(size=(B, 2)).astype(np.float32)).cuda()
-    net.train(X, T, steps, 1e-3)        # warm-up: same call, so the timed one replays its captured graph
+    # warm-up with the same call: the timed call replays the captured step
+    # when its loss history lands at the same address (the graph's key)
+    net.train(X, T, steps, 1e-3)
     n0 = net.launches
     t0 = time.perf_counter()
     net.train(X, T, steps, 1e-3)
