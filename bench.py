@@ -597,6 +597,20 @@ def run_profile(args):
     import dg_inputs
     import paper_2508_17917_gb300 as dg
     from dg_inputs.states import to_kcn
+    if args.profile == "mlp4096":
+        # the surrogate network's training step, replayed from its graph
+        import numpy as np
+        torch.cuda.set_device(0)
+        B = 4096
+        rng = np.random.default_rng(0)
+        X = torch.from_numpy(rng.normal(size=(B, 67)).astype(np.float32)).cuda()
+        T = torch.from_numpy(rng.normal(size=(B, 2)).astype(np.float32)).cuda()
+        net = dg.Mlp(67, 128, 3, 2, max_batch=B, seed=0)
+        hist = net.train(X, T, 12, 1e-3)
+        torch.cuda.synchronize()
+        assert bool(torch.isfinite(hist).all())
+        print(json.dumps({"profile": args.profile, "B": B, "steps": 12, "launches": net.launches}))
+        return
     prec, n, theta, var, p = {"mixed512": ("mixed", 512, 0.0, 0, P), "mixed128": ("mixed", 128, 0.0, 0, P),
                               "fp64_128": ("fp64", 128, 0.0, 0, P), "sip128": ("mixed", 128, 1.0, 0, P),
                               "tc512": ("mixed", 512, 0.0, 3, P), "tcsip512": ("mixed", 512, 1.0, 3, P),
@@ -628,7 +642,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3],
                     help="tile shape of the headline's mixed kernel (0: first-step tuner)")
-    ap.add_argument("--profile", choices=["mixed512", "mixed128", "fp64_128", "sip128", "tc512", "tcsip512", "tc6_375"], default=None)
+    ap.add_argument("--profile", choices=["mixed512", "mixed128", "fp64_128", "sip128", "tc512", "tcsip512", "tc6_375", "mlp4096"], default=None)
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
