@@ -671,9 +671,14 @@ class Mlp:
         dg_mlp_loss_grad(self.m, X, T, g, loss)
         return float(loss.item()), g
 
-    def train(self, X, T, nsteps, lr):
+    def train(self, X, T, nsteps, lr, out=None):
+        """nsteps Adam steps; returns the loss before each step, in `out`
+        (a float32 CUDA tensor of at least nsteps values) if given.  Calls
+        with the same X, T, out and lr reuse the captured step graph."""
         import torch
-        hist = torch.empty(max(nsteps, 1), dtype=torch.float32, device=X.device)
+        hist = out if out is not None else torch.empty(max(nsteps, 1), dtype=torch.float32, device=X.device)
+        if hist.numel() < nsteps or hist.dtype != torch.float32 or not hist.is_contiguous():
+            raise ValueError("out must be a contiguous float32 tensor of at least nsteps values")
         dg_mlp_train(self.m, X, T, nsteps, lr, hist)
         return hist[:nsteps]
 
