@@ -438,17 +438,18 @@ int reduce_blocks(const dg_mlp *m) { return static_cast<int>((m->nparams + mlpf:
 dg_status fused_forward(dg_mlp *m, const float *X, int B, float *Y)
 {
     mlpf::mlp_chunk_kernel<false><<<fused_blocks(m, B), mlpf::NT, m->fnet.bytes, m->stream>>>(
-        m->fnet, m->p.ptr, m->wstaged.ptr, X, nullptr, B, Y, nullptr, nullptr);
+        m->fnet, m->p.ptr, m->wstaged.ptr, X, nullptr, B, Y, nullptr, nullptr, nullptr);
     m->launches += 1;
     M_CUDA(m, cudaGetLastError());
     return DG_OK;
 }
 
-// gradient slices and loss sums of every block for the rows of X, T
-dg_status fused_chunks(dg_mlp *m, const float *X, const float *T, int B)
+// gradient slices and loss sums of every block for the rows of X, T;
+// step (or null): the replayed step's index, advanced by the kernel
+dg_status fused_chunks(dg_mlp *m, const float *X, const float *T, int B, int *step = nullptr)
 {
     mlpf::mlp_chunk_kernel<true><<<fused_blocks(m, B), mlpf::NT, m->fnet.bytes, m->stream>>>(
-        m->fnet, m->p.ptr, m->wstaged.ptr, X, T, B, nullptr, m->fpart.ptr, m->flpart.ptr);
+        m->fnet, m->p.ptr, m->wstaged.ptr, X, T, B, nullptr, m->fpart.ptr, m->flpart.ptr, step);
     m->launches += 1;
     M_CUDA(m, cudaGetLastError());
     return DG_OK;
@@ -467,13 +468,14 @@ dg_status fused_loss_grad(dg_mlp *m, const float *X, const float *T, int B, floa
 }
 
 // one Adam step: loss (before the update) to *loss; bias corrections bc1,
-// bc2, or those of step *cnt in bc when bc is set
+// bc2 -- or, when bc is set (graph replay), those of step *cnt, which the
+// chunk kernel advances, with the loss also written to hist[*cnt] if hist
 dg_status fused_step(dg_mlp *m, const float *X, const float *T, int B, float *loss, float lr, float bc1, float bc2,
-                     const float *bc, const int *cnt)
+                     const float *bc, int *cnt, float *hist)
 {
-    dg_status st = fused_chunks(m, X, T, B);
+    dg_status st = fused_chunks(m, X, T, B, bc ? cnt : nullptr);
     if (st != DG_OK) return st;
-    const mlpf::Adam o{lr, 0.9f, 0.999f, 1e-8f, bc1, bc2, bc, cnt};
+    const mlpf::Adam o{lr, 0.9f, 0.999f, 1e-8f, bc1, bc2, bc, cnt, hist};
     mlpf::mlp_reduce_kernel<true><<<reduce_blocks(m), mlpf::RP * mlpf::RQ, 0, m->stream>>>(
         m->fnet, fused_blocks(m, B), m->fpart.ptr, m->flpart.ptr, static_cast<long long>(B) * m->n_out, nullptr,
         loss, m->p.ptr, m->m.ptr, m->v.ptr, m->wstaged.ptr, m->wq.ptr, o);
@@ -745,7 +747,7 @@ dg_status dg_mlp_train(dg_mlp *m, const float *X, const float *T, int B, int nst
             const float bc1 = static_cast<float>(1.0 - std::pow(0.9, static_cast<double>(m->step + 1)));
             const float bc2 = static_cast<float>(1.0 - std::pow(0.999, static_cast<double>(m->step + 1)));
             if (m->fused_on) {
-                st = fused_step(m, X, T, B, lo, lr, bc1, bc2, nullptr, nullptr);
+                st = fused_step(m, X, T, B, lo, lr, bc1, bc2, nullptr, nullptr, nullptr);
                 if (st != DG_OK) return st;
                 m->step += 1;
                 continue;
@@ -781,7 +783,9 @@ dg_status dg_mlp_train(dg_mlp *m, const float *X, const float *T, int B, int nst
     }
     if (!m->cnt.ptr) M_CUDA(m, m->cnt.alloc(1));
     M_CUDA(m, cudaMemcpyAsync(m->bc.ptr, bch.data(), bch.size() * sizeof(float), cudaMemcpyHostToDevice, m->stream));
-    M_CUDA(m, cudaMemsetAsync(m->cnt.ptr, 0, sizeof(int), m->stream));
+    // the step index: the chunked step advances it at its start (from -1),
+    // the layer-by-layer step after its update (from 0)
+    M_CUDA(m, cudaMemsetAsync(m->cnt.ptr, m->fused_on ? 0xff : 0, sizeof(int), m->stream));
     const bool same = m->gexec && m->gkey[0] == X && m->gkey[1] == T && m->gkey[2] == loss_hist && m->gkey_b == B &&
                       m->gkey_lr == lr;
     if (!same) {
@@ -792,9 +796,7 @@ dg_status dg_mlp_train(dg_mlp *m, const float *X, const float *T, int B, int nst
         const int64_t l0 = m->launches;
         M_CUDA(m, cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
         if (m->fused_on) {
-            st = fused_step(m, X, T, B, m->lossbuf.ptr, lr, 1.0f, 1.0f, m->bc.ptr, m->cnt.ptr);
-            record_loss_kernel<<<1, 32, 0, m->stream>>>(m->lossbuf.ptr, loss_hist, m->cnt.ptr);
-            m->launches += 1;
+            st = fused_step(m, X, T, B, m->lossbuf.ptr, lr, 1.0f, 1.0f, m->bc.ptr, m->cnt.ptr, loss_hist);
         } else {
             st = loss_grad(m, X, T, B, m->g.ptr, m->lossbuf.ptr, m->yscr.ptr);
             adam_indexed_kernel<<<blocks_for(m->nparams), 256, 0, m->stream>>>(m->p.ptr, m->g.ptr, m->m.ptr,

@@ -234,15 +234,18 @@ __device__ __forceinline__ void zero_cols(bf16 *D, int ls, int c0, int c1)
 
 // TRAIN = false: forward only, Y [B][n_out].  TRAIN = true: loss and
 // gradient; the block's slice of part [gridDim.x][nparams] and lpart
-// [gridDim.x] receive its sums over its chunks.
+// [gridDim.x] receive its sums over its chunks.  step (graph replay, or
+// null): the step index, advanced here by one (it starts a call at -1), so
+// that the reduction kernel of the same step reads it.
 template <bool TRAIN>
 __global__ void __launch_bounds__(NT) mlp_chunk_kernel(Net net, const float *__restrict__ P, const bf16 *__restrict__ WS,
                                                        const float *__restrict__ X, const float *__restrict__ T, int B,
                                                        float *__restrict__ Y, float *__restrict__ part,
-                                                       float *__restrict__ lpart)
+                                                       float *__restrict__ lpart, int *step)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (step && blockIdx.x == 0 && tid == 0) *step += 1;
     const int nl = net.nl, n_in = net.din[0], maxd = net.maxd, LDD = ldk(maxd), ZD = zld(maxd);
     float *D32 = reinterpret_cast<float *>(sm + net.oD32);
     const long long NP = net.nparams;
@@ -417,6 +420,7 @@ struct Adam {
     float lr, b1, b2, eps, bc1, bc2;
     const float *bc;       // if set: bias corrections (bc1, bc2) of step *cnt
     const int *cnt;
+    float *hist;           // if set (with bc): the loss also goes to hist[*cnt]
 };
 
 // weight i (a parameter index) rounded to bf16 into the staged copy WS
@@ -492,6 +496,7 @@ mlp_reduce_kernel(Net net, int G, const float *__restrict__ part, const float *_
         float s = 0.f;
         for (int c = 0; c < G; ++c) s += lpart[c];
         *loss = s / static_cast<float>(nsum);
+        if (ADAM && o.bc && o.hist) o.hist[*o.cnt] = s / static_cast<float>(nsum);
     }
 }
 

@@ -175,9 +175,9 @@ def test_chunked_and_layer_paths_agree(dg):
 
 def test_chunked_path_selection_and_launches(dg):
     """The chunked path is the default where the layers fit (two launches per
-    training step, three when a step is replayed from the graph: the loss
-    history entry is one more); a wider network keeps the layer-by-layer
-    kernels and refuses the chunked path."""
+    training step, also when a step is replayed from the graph: the step
+    index and the loss history are kept by the same two kernels); a wider
+    network keeps the layer-by-layer kernels and refuses the chunked path."""
     import torch
     rng = np.random.default_rng(1)
     x = torch.from_numpy(rng.normal(size=(256, N_IN)).astype(np.float32)).cuda()
@@ -189,7 +189,7 @@ def test_chunked_path_selection_and_launches(dg):
     assert net.launches - n0 == 2 * 3
     n0 = net.launches
     net.train(x, t, 10, 1e-3)
-    assert net.launches - n0 == 3 * 10
+    assert net.launches - n0 == 2 * 10
     wide = dg.Mlp(N_IN, 256, 2, N_OUT, max_batch=512, seed=0)
     assert not wide.fused
     with pytest.raises(dg.DGError):
