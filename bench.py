@@ -279,7 +279,9 @@ def run_ours(args):
     traffic = recorded_traffic(variant)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
-                "traffic": (traffic * dof * 5 / 5.0) if traffic is not None else None,
+                # the recorded figure is a stage-2 launch; stage 1 does not
+                # read K1 (8 B per DOF less): averaged over the step's launches
+                "traffic": ((traffic - 8.0 / 5.0) * dof) if traffic is not None else None,
                 "algorithmic_bytes_per_launch": bytes_step / 5.0,
                 "kernel": KERNEL_OF_VARIANT.get(variant, str(variant)),
                 "tile_shape": SHAPE_OF_VARIANT.get(variant, str(variant))}
