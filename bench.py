@@ -438,9 +438,10 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def run_batch(dg, torch, dg_inputs, to_kcn, np, peak, steps):
-    """The 64-case reduced-velocity sweep advanced as one batch; CUDA events
-    on the batch's stream around dg_batch_run (graph replays)."""
+def build_batch(dg, dg_inputs, to_kcn, np):
+    """The 64-case reduced-velocity sweep as one batch solver with its seeded
+    start states; returns the solver, the cases, the DOF count and the
+    algorithmic bytes of one step."""
     gamma, mach = 1.4, 0.2
     p_inf = 1.0 / (gamma * mach * mach)
     sweep = dg_inputs.viv_sweep()
@@ -463,6 +464,13 @@ def run_batch(dg, torch, dg_inputs, to_kcn, np, peak, steps):
         # five stage launches, plus the time-step bound's read of the FP32 state copy
         # and pressures (20 B per node) with geometry and connectivity
         bytes_step += 4 * K * Np * (24 + 4 * 32) + 5 * K * GEO_BYTES_MIXED + K * Np * 20 + K * GEO_BYTES_MIXED
+    return b, cases, dof, bytes_step
+
+
+def run_batch(dg, torch, dg_inputs, to_kcn, np, peak, steps):
+    """The 64-case reduced-velocity sweep advanced as one batch; CUDA events
+    on the batch's stream around dg_batch_run (graph replays)."""
+    b, cases, dof, bytes_step = build_batch(dg, dg_inputs, to_kcn, np)
     b.run(0.3, 3, use_graph=True)                        # warm-up, graphs captured
     ext = torch.cuda.ExternalStream(b.stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -600,6 +608,21 @@ def run_profile(args):
     import dg_inputs
     import paper_2508_17917_gb300 as dg
     from dg_inputs.states import to_kcn
+    if args.profile == "batch64":
+        # two steps of the 64-case sweep (the first one tunes the tile shape
+        # of every degree group and captures the step graphs)
+        import numpy as np
+        torch.cuda.set_device(0)
+        b, cases, dof, _ = build_batch(dg, dg_inputs, to_kcn, np)
+        b.run(0.3, args.steps, use_graph=True)
+        torch.cuda.synchronize()
+        assert not np.any(b.rigid()[:, 9])
+        shapes = {}
+        for i, c in enumerate(cases):
+            shapes.setdefault(f"p{c['p']}", b.variant(i))
+        print(json.dumps({"profile": args.profile, "cases": len(cases), "dofs": dof, "steps": args.steps,
+                          "launches": b.launches, "tile_shape_per_degree": shapes}))
+        return
     if args.profile == "mlp4096":
         # the surrogate network's training step, replayed from its graph
         import numpy as np
@@ -645,7 +668,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3],
                     help="tile shape of the headline's mixed kernel (0: first-step tuner)")
-    ap.add_argument("--profile", choices=["mixed512", "mixed128", "fp64_128", "sip128", "tc512", "tcsip512", "tc6_375", "mlp4096"], default=None)
+    ap.add_argument("--profile", choices=["mixed512", "mixed128", "fp64_128", "sip128", "tc512", "tcsip512", "tc6_375", "mlp4096",
+                             "batch64"], default=None)
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
