@@ -89,6 +89,17 @@ dg_status dg_batch_set_stage_variant(dg_batch *b, int variant);
  * graphs.  Errors: DG_EINVAL, DG_ECUDA. */
 dg_status dg_batch_set_fused_steps(dg_batch *b, int on);
 
+/* Fixed time steps: dt[ncases] (host, copied) replaces step 1's
+ * dt_i = cfl / max_K Lambda_K by dt_i for every following dg_batch_run (the
+ * cfl argument is then ignored); the bound is still evaluated every step,
+ * recorded in the history and a case whose bound is not finite is still
+ * frozen.  For runs over a stretch of physical time at a step the caller
+ * chose (Sec. 3.2 runs at the largest stable step found by trial).
+ * dt == NULL returns to the CFL bound.  Drops captured graphs when the mode
+ * changes; synchronises the batch stream.
+ * Errors: DG_EINVAL (a step not finite or <= 0), DG_ECUDA. */
+dg_status dg_batch_set_fixed_dt(dg_batch *b, const double *dt);
+
 /* The tile shape the group of case i uses (1, 2 or 3); 0 for a bad argument. */
 int dg_batch_stage_variant(const dg_batch *b, int i);
 

@@ -186,7 +186,8 @@ class Problem:
 
     def dt(self, U, cfl, vw=(0.0, 0.0)):
         """CFL / max_K Lambda_K (Eq. rayleigh_bound, readings in dg_oracle.c).
-        Parity unpinned beyond scaling checks: the paper's dt table needs its mesh."""
+        Pinned against the spectral radius of the linearised residual and the
+        p-ratios of the paper's dt table (tests/test_oracle_dt.py)."""
         U = _f64(U)
         lam = np.empty(self.K)
         out = np.zeros(1)

@@ -740,25 +740,33 @@ int oracle_face_sigma(const oracle_problem *P, const double *U, const double vw[
     return 0;
 }
 
-/* Face Gbar_e of every face, [K][3] (max spectral norm over both sides). */
-static double face_gbar(const oracle_problem *P, long long k, int f,
-                        const double (*Uplus)[4], const double (*Uother)[4])
+/* Largest diffusivity of the system on face f of element k: the largest
+ * eigenvalue of N G N^T over the face nodes of both traces.  For a unit normal
+ * N G N^T maps the normal derivative of U to the normal viscous flux; written
+ * in (rho, rho v.n, rho v.t, eps) it is lower triangular with diagonal
+ * (0, 4/3, 1, gamma/Pr) mu/rho, so the eigenvalue is max(4/3, gamma/Pr) mu/rho
+ * whatever the normal (and whatever variables the system is written in). */
+static double face_diffusivity(const oracle_problem *P, const double (*Uplus)[4],
+                               const double (*Uother)[4])
 {
-    double n[2] = {P->nx[k * 3 + f], P->ny[k * 3 + f]};
-    double Gbar = 0;
+    double gmax = P->gamma / P->Pr > 4.0 / 3.0 ? P->gamma / P->Pr : 4.0 / 3.0;
+    double G = 0;
     for (int i = 0; i < P->Nfp; ++i) {
-        double a = oracle_penalty_norm(Uplus[i], n, P->gamma, P->Pr, P->mu);
-        double b = oracle_penalty_norm(Uother[i], n, P->gamma, P->Pr, P->mu);
-        if (a > Gbar) Gbar = a;
-        if (b > Gbar) Gbar = b;
+        double a = gmax * P->mu / Uplus[i][0];
+        double b = gmax * P->mu / Uother[i][0];
+        if (a > G) G = a;
+        if (b > G) G = b;
     }
-    return Gbar;
+    return G;
 }
 
 /* Time step from Eq. rayleigh_bound: dt = CFL / max_K Lambda_K with
  * Lambda_K = 3/2 C_inv2(K) G_K + (d+1) C_inv,K (3 sigma_K + beta_K) + beta'_K.
  * Readings: C_inv2 = p^4 / rho_K^2 (C_grad = 1, rho_K the inradius);
- * G_K = max over the faces of K of Gbar_e; sigma_K = max_e sigma_e;
+ * G_K, the diffusion coefficient of the Appendix's scalar model problem, is the
+ * largest diffusivity of the system, max(4/3, gamma/Pr) mu/rho, over the
+ * face-node traces of both sides of every face of K (face_diffusivity);
+ * sigma_K = max_e sigma_e, the penalty of Eq. penalty_final actually applied;
  * C_inv,K = max_e C_inv(e,K,p); beta_K = max over nodes of |b_ns|_2 with
  * (b_ns)_j = |v_j - v_w,j| + sqrt(gamma p / rho) (Eq. cfl_general); beta'_K = 0. */
 int oracle_dt(const oracle_problem *P, const double *U, double cfl, const double vw[2],
@@ -777,7 +785,7 @@ int oracle_dt(const oracle_problem *P, const double *U, double cfl, const double
         for (int f = 0; f < 3; ++f) {
             double Up[8][4], Upx[8][4], Upy[8][4], Uo[8][4], Uox[8][4], Uoy[8][4];
             face_traces(P, U, Ux, Uy, vw, k, f, Up, Upx, Upy, Uo, Uox, Uoy);
-            double gb = face_gbar(P, k, f, (const double (*)[4])Up, (const double (*)[4])Uo);
+            double gb = face_diffusivity(P, (const double (*)[4])Up, (const double (*)[4])Uo);
             double sg = face_sigma(P, k, f, (const double (*)[4])Up, (const double (*)[4])Uo);
             double ci = cinv(P, k, f);
             if (gb > GK) GK = gb;

@@ -100,6 +100,7 @@ EXPORTED = {
     "dg_batch_set_stage_variant": (C.c_int, [C.c_void_p, C.c_int]),
     "dg_batch_stage_variant": (C.c_int, [C.c_void_p, C.c_int]),
     "dg_batch_set_fused_steps": (C.c_int, [C.c_void_p, C.c_int]),
+    "dg_batch_set_fixed_dt": (C.c_int, [C.c_void_p, _dp]),
     "dg_batch_case_size": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
     "dg_batch_node_coords": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp]),
     "dg_batch_set_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
@@ -433,6 +434,15 @@ def dg_batch_set_fused_steps(b, on):
     _bcheck(lib().dg_batch_set_fused_steps(b, int(bool(on))), b)
 
 
+def dg_batch_set_fixed_dt(b, dt):
+    """dt: per-case steps (sequence of ncases floats), or None for the CFL bound."""
+    if dt is None:
+        _bcheck(lib().dg_batch_set_fixed_dt(b, None), b)
+        return
+    arr = _f64(dt)
+    _bcheck(lib().dg_batch_set_fixed_dt(b, _dptr(arr)), b)
+
+
 def dg_batch_stream(b):
     """Integer handle of the batch's cudaStream_t."""
     return int(lib().dg_batch_stream(b) or 0)
@@ -557,6 +567,12 @@ class BatchSolver:
     def set_fused(self, on):
         """One cooperative launch per degree group and step."""
         dg_batch_set_fused_steps(self.b, on)
+
+    def set_fixed_dt(self, dt):
+        """Per-case fixed steps (None: back to the CFL bound)."""
+        if dt is not None:
+            dt = np.broadcast_to(np.asarray(dt, dtype=np.float64), (self.ncases,))
+        dg_batch_set_fixed_dt(self.b, dt)
 
 
 # ---- include/dg_mlp.h -----------------------------------------------------

@@ -16,9 +16,12 @@ __device__ __forceinline__ void load_node(const double *U, int Np, long long k, 
 
 // One thread per element: Lambda_K of Eq. rayleigh_bound,
 //   Lambda_K = 3/2 C_inv,2(K) G_K + (d+1) C_inv,K (3 sigma_K + beta_K) + beta'_K,
-// with C_inv,2 = p^4 / rho_K^2 (rho_K the inradius 2|K| / perimeter), G_K the
-// largest Gbar_e over the faces of K, sigma_K, C_inv,K the largest over its
-// faces, beta_K = max over nodes of |b_ns|_2, (b_ns)_j = |v_j - v_w,j| + c
+// with C_inv,2 = p^4 / rho_K^2 (rho_K the inradius 2|K| / perimeter); G_K the
+// largest diffusivity of the system, max(4/3, gamma/Pr) mu / rho, over the
+// face-node traces of both sides of the faces of K (the largest eigenvalue of
+// N G N^T, which does not depend on the normal); sigma_K the largest penalty
+// sigma_e of Eq. penalty_final over the faces of K and C_inv,K the largest
+// C_inv; beta_K = max over nodes of |b_ns|_2, (b_ns)_j = |v_j - v_w,j| + c
 // (Eq. cfl_general), beta'_K = 0.
 __global__ void dt_lambda_kernel(AuxMesh m, Phys<double> ph, double sig_fac, double *lam)
 {
@@ -34,26 +37,30 @@ __global__ void dt_lambda_kernel(AuxMesh m, Phys<double> ph, double sig_fac, dou
     const int4 cn = m.conn[k];
     double GK = 0, sigK = 0, ciK = 0, perim = 0;
     const double pp = (p + 1.0) * (p + 2.0);
+    const double gdiff = fmax(4.0 / 3.0, ph.gPr);
     for (int f = 0; f < 3; ++f) {
         long long nb = (f == 0) ? cn.x : (f == 1 ? cn.y : cn.z);
         int f2 = (cn.w >> (2 * f)) & 3;
         int bt = (cn.w >> (8 + 2 * f)) & 3;
         double n1 = g[G_NX + f], n2 = g[G_NY + f], fs = g[G_FS + f];
-        double gbar = 0;
+        double gbar = 0, rmin = INFINITY;
         for (int i = 0; i < Nfp; ++i) {
             int vm = m.fmask[f * Nfp + i];
             double u[4];
             load_node(m.U, Np, k, vm, u);
             double a = penalty_norm(u[0], u[1] / u[0], u[2] / u[0], u[3] / u[0], n1, n2, ph);
             double b;
+            rmin = fmin(rmin, u[0]);
             if (bt == BCT_INTERIOR) {
                 double w[4];
                 load_node(m.U, Np, nb, m.fmask[f2 * Nfp + (Nfp - 1 - i)], w);
                 b = penalty_norm(w[0], w[1] / w[0], w[2] / w[0], w[3] / w[0], n1, n2, ph);
+                rmin = fmin(rmin, w[0]);
             } else if (bt == BCT_FARFIELD) {
                 const double *w = ph.Uinf;
                 b = penalty_norm(w[0], w[1] / w[0], w[2] / w[0], w[3] / w[0], n1, n2, ph);
-            } else {
+                rmin = fmin(rmin, w[0]);
+            } else {   // wall ghost: the interior density
                 double pw = pressure<double>(u, u[3], ph.gm1);
                 double eb = (pw / ph.gm1 + 0.5 * u[0] * (ph.vw1 * ph.vw1 + ph.vw2 * ph.vw2)) / u[0];
                 b = penalty_norm(u[0], ph.vw1, ph.vw2, eb, n1, n2, ph);
@@ -64,7 +71,7 @@ __global__ void dt_lambda_kernel(AuxMesh m, Phys<double> ph, double sig_fac, dou
         double cmax = ci;
         if (bt == BCT_INTERIOR) cmax = fmax(ci, pp * m.geo[nb * 16 + G_FS + f2] * 0.5);
         double sig = sig_fac * gbar * cmax;
-        GK = fmax(GK, gbar);
+        GK = fmax(GK, gdiff * ph.mu / rmin);
         sigK = fmax(sigK, sig);
         ciK = fmax(ciK, ci);
         perim += 2.0 * fs * g[G_J];     // |e| = 2 sJ = 2 Fscale J
@@ -187,9 +194,12 @@ __global__ void nonfinite_kernel(const double *x, long long n, int *flag)
 // ---- batch of independent cases (Algorithm 3 per case, on the device)
 
 // One block per case: max_K Lambda_K over the case's elements, then
-// dt = cfl / max (Eq. rayleigh_bound); a bound that is not finite freezes the
-// case (dt = 0, bad = 1) instead of spreading NaN.
-__global__ void batch_dt_kernel(const double *lam, const long long *seg, BatchCase *cases, double cfl)
+// dt = cfl / max (Eq. rayleigh_bound), or the case's entry of `fixed` when
+// the caller fixed the steps (the bound is still evaluated and recorded); a
+// bound that is not finite freezes the case (dt = 0, bad = 1) instead of
+// spreading NaN.
+__global__ void batch_dt_kernel(const double *lam, const long long *seg, BatchCase *cases, double cfl,
+                                const double *fixed)
 {
     __shared__ double s[256];
     const int i = blockIdx.x;
@@ -218,7 +228,7 @@ __global__ void batch_dt_kernel(const double *lam, const long long *seg, BatchCa
             cs.bad = 1;
             cs.dt = 0.0;
         } else {
-            cs.dt = cfl / l;
+            cs.dt = fixed ? fixed[i] : cfl / l;
         }
     }
 }
@@ -290,9 +300,9 @@ __global__ void batch_record_kernel(const BatchCase *cases, int n, double *hist,
 }  // namespace
 
 cudaError_t launch_batch_dt(const double *lam, const long long *seg, BatchCase *cases, int ncases, double cfl,
-                            cudaStream_t st)
+                            const double *fixed, cudaStream_t st)
 {
-    batch_dt_kernel<<<ncases, 256, 0, st>>>(lam, seg, cases, cfl);
+    batch_dt_kernel<<<ncases, 256, 0, st>>>(lam, seg, cases, cfl, fixed);
     return cudaGetLastError();
 }
 

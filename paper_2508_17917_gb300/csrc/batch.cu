@@ -74,6 +74,8 @@ struct dg_batch {
     std::vector<dg::BatchCase> init;
     DevBuf<dg::BatchCase> dcases;
     DevBuf<double> lam, fpart;
+    DevBuf<double> fixed_dt;         // per-case steps set by dg_batch_set_fixed_dt
+    bool use_fixed = false;
     DevBuf<long long> seg;
     DevBuf<int> wseg, counter;
     bool cur_is_a = true;
@@ -194,7 +196,8 @@ dg_status enqueue_step(dg_batch *b, double cfl, double *hist, int rows)
                                              ph32, static_cast<float>(sf), b->lam.ptr + g.lam_base, b->stream));
         b->launches += 1;
     }
-    B_CUDA(b, dg::launch_batch_dt(b->lam.ptr, b->seg.ptr, b->dcases.ptr, n, cfl, b->stream));
+    B_CUDA(b, dg::launch_batch_dt(b->lam.ptr, b->seg.ptr, b->dcases.ptr, n, cfl,
+                                  b->use_fixed ? b->fixed_dt.ptr : nullptr, b->stream));
     B_CUDA(b, dg::launch_batch_newmark(b->dcases.ptr, n, b->stream));
     b->launches += 2;
     for (int s = 0; s < (b->fused ? 1 : 5); ++s) {
@@ -577,6 +580,34 @@ dg_status dg_batch_set_stage_variant(dg_batch *b, int variant)
     b->tuned = false;
     b->drop_graphs();
     b->graph_cfl = 0.0;
+    return DG_OK;
+}
+
+dg_status dg_batch_set_fixed_dt(dg_batch *b, const double *dt)
+{
+    if (!b) return DG_EINVAL;
+    b->err.clear();
+    const size_t n = b->cases.size();
+    if (!dt) {
+        if (b->use_fixed) {
+            b->use_fixed = false;
+            b->drop_graphs();
+            b->graph_cfl = 0.0;
+        }
+        return DG_OK;
+    }
+    for (size_t i = 0; i < n; ++i)
+        if (!(dt[i] > 0.0) || !std::isfinite(dt[i]))
+            return bfail(b, DG_EINVAL, "fixed step of case " + std::to_string(i) + " must be finite and > 0");
+    if (!b->fixed_dt.ptr) B_CUDA(b, b->fixed_dt.alloc(n));
+    // the batch stream may still read the previous steps
+    B_CUDA(b, cudaStreamSynchronize(b->stream));
+    B_CUDA(b, cudaMemcpy(b->fixed_dt.ptr, dt, n * sizeof(double), cudaMemcpyHostToDevice));
+    if (!b->use_fixed) {
+        b->use_fixed = true;
+        b->drop_graphs();
+        b->graph_cfl = 0.0;
+    }
     return DG_OK;
 }
 

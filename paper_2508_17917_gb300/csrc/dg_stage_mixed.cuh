@@ -552,9 +552,10 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
 // Lambda_K of Eq. rayleigh_bound in FP32 from the FP32 state copy and the
 // FP64-recovered pressures, one block per tile (same node / face-node thread
 // map as the stage kernel).  Same readings as the FP64 time-step kernel:
-// C_inv,2 = p^4 / rho_K^2 with rho_K = 2|K| / perimeter, G_K and sigma_K the
-// largest over the faces of K, C_inv,K the largest over its faces, beta_K the
-// largest |b_ns|_2 over its nodes, beta'_K = 0.  Batch: the tile table gives
+// C_inv,2 = p^4 / rho_K^2 with rho_K = 2|K| / perimeter, G_K the largest
+// diffusivity max(4/3, gamma/Pr) mu / rho over the face-node traces of both
+// sides, sigma_K the largest penalty over the faces of K, C_inv,K the largest
+// over its faces, beta_K the largest |b_ns|_2 over its nodes, beta'_K = 0.  Batch: the tile table gives
 // the elements and the case (mu, v_b); otherwise tiles are E consecutive
 // elements and ph holds mu and v_w.
 template <int P>
@@ -567,6 +568,7 @@ dt_lambda_mixed_kernel(const float4 *S, const float *Pr, const float *geo, const
     constexpr int Np = Sh::Np, Nfp = Sh::Nfp, NF = Sh::NF, E = Sh::E, NT = Sh::NT;
     constexpr int NpP = (Np + 3) & ~3;
     __shared__ float sNorm[E * NF];
+    __shared__ float sRmin[E * NF];
     __shared__ float sBeta[E * Np];
     __shared__ int sFm[NF];
     const int tid = threadIdx.x;
@@ -593,21 +595,24 @@ dt_lambda_mixed_kernel(const float4 *S, const float *Pr, const float *geo, const
         const float4 u = S[k * Np + vm];
         const float ir = 1.0f / u.x;
         const float a = penalty_norm(u.x, u.y * ir, u.z * ir, u.w * ir, n1, n2, ph);
-        float b;
+        float b, rmin = u.x;
         if (bt == BCT_INTERIOR) {
             const long long nb = (ff == 0) ? cn.x : (ff == 1 ? cn.y : cn.z);
             const float4 w = S[nb * Np + vp];
             const float iw = 1.0f / w.x;
             b = penalty_norm(w.x, w.y * iw, w.z * iw, w.w * iw, n1, n2, ph);
+            rmin = fminf(rmin, w.x);
         } else if (bt == BCT_FARFIELD) {
             const float iw = 1.0f / ph.Uinf[0];
             b = penalty_norm(ph.Uinf[0], ph.Uinf[1] * iw, ph.Uinf[2] * iw, ph.Uinf[3] * iw, n1, n2, ph);
+            rmin = fminf(rmin, ph.Uinf[0]);
         } else {
             const float pw = Pr[k * NpP + vm];
             const float eb = (pw / ph.gm1 + 0.5f * u.x * (ph.vw1 * ph.vw1 + ph.vw2 * ph.vw2)) * ir;
             b = penalty_norm(u.x, ph.vw1, ph.vw2, eb, n1, n2, ph);
         }
         sNorm[fe * NF + fm] = fmaxf(a, b);
+        sRmin[fe * NF + fm] = rmin;
     }
     const int ve = tid / Np, vi = tid - (tid / Np) * Np;
     if (ve < ne) {
@@ -625,10 +630,14 @@ dt_lambda_mixed_kernel(const float4 *S, const float *Pr, const float *geo, const
         const int4 cn = conn[k];
         const float pp = float((P + 1) * (P + 2));
         float GK = 0.f, sigK = 0.f, ciK = 0.f, perim = 0.f, beta = 0.f;
+        const float gdiff = fmaxf(4.0f / 3.0f, ph.gPr) * ph.mu;
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
-            float gbar = 0.f;
-            for (int i = 0; i < Nfp; ++i) gbar = fmaxf(gbar, sNorm[tid * NF + f * Nfp + i]);
+            float gbar = 0.f, rmin = INFINITY;
+            for (int i = 0; i < Nfp; ++i) {
+                gbar = fmaxf(gbar, sNorm[tid * NF + f * Nfp + i]);
+                rmin = fminf(rmin, sRmin[tid * NF + f * Nfp + i]);
+            }
             const float fs = g[G_FS + f];
             const float ci = 0.5f * pp * fs;
             float cmax = ci;
@@ -637,7 +646,7 @@ dt_lambda_mixed_kernel(const float4 *S, const float *Pr, const float *geo, const
                 const int f2 = (cn.w >> (2 * f)) & 3;
                 cmax = fmaxf(ci, 0.5f * pp * geo[nb * 16 + G_FS + f2]);
             }
-            GK = fmaxf(GK, gbar);
+            GK = fmaxf(GK, gdiff / rmin);
             sigK = fmaxf(sigK, sig_fac * gbar * cmax);
             ciK = fmaxf(ciK, ci);
             perim += 2.0f * fs * g[G_J];

@@ -125,9 +125,10 @@ cudaError_t launch_wall_force_faces(const AuxMesh &m, const Phys<double> &ph, co
 cudaError_t launch_sum3(const double *partial, int n, double *out, cudaStream_t st);
 
 // batch: one block per case, max of lam over the case's element range
-// [seg[2i], seg[2i+1]) -> cases[i].lam and dt = cfl / lam (0 and bad = 1 if not finite)
+// [seg[2i], seg[2i+1]) -> cases[i].lam and dt = cfl / lam, or fixed[i] when
+// fixed is not null (0 and bad = 1 if the bound is not finite)
 cudaError_t launch_batch_dt(const double *lam, const long long *seg, BatchCase *cases, int ncases, double cfl,
-                            cudaStream_t st);
+                            const double *fixed, cudaStream_t st);
 // batch: Newmark step of every case with its lagged lift and its dt; sets v_b, advances t
 cudaError_t launch_batch_newmark(BatchCase *cases, int ncases, cudaStream_t st);
 // batch: one block per case, sum of the wall-face partials [wseg[2i], wseg[2i+1]) -> Fx, Fy, Mz

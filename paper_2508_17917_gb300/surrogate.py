@@ -86,10 +86,10 @@ class LoadSurrogate:
 
 
 def coupled_run(solver, surrogate, coeff, mass, ustar, mstar, re, nsteps, cfl=0.3, tol=0.05,
-                state0=(0.0, 0.0, 0.0), q=Q_REF):
+                state0=(0.0, 0.0, 0.0), q=Q_REF, dt_fixed=None):
     """Algorithm 3 on one case with the surrogate as the load predictor.
 
-    Each step: dt from the CFL bound; the Newmark step takes the predicted
+    Each step: dt from the CFL bound (or dt_fixed when given); the Newmark step takes the predicted
     end-of-step lift when the window is full and the previous prediction
     passed the judge, else the lagged DG lift; the DG step runs with
     v_w = (0, v_b); its forces judge the prediction (relative miss measured
@@ -101,7 +101,7 @@ def coupled_run(solver, surrogate, coeff, mass, ustar, mstar, re, nsteps, cfl=0.
     rows, out = [], []
     trusted = True
     for _ in range(nsteps):
-        dt = solver.dt(cfl, (0.0, vb))
+        dt = solver.dt(cfl, (0.0, vb)) if dt_fixed is None else float(dt_fixed)
         pred = np.nan
         if len(rows) >= surrogate.window:
             X, _, S, C = make_windows(np.array(rows[-surrogate.window:] + [rows[-1]]), ustar, mstar, re,

@@ -10,8 +10,9 @@ rayleigh_bound).
   load, the known period elongation 2 arctan(w dt / 2), static offset F/K.
 * Forces: zero for uniform pressure; Archimedes' law -g*Area for a linear
   pressure; 2 mu a Area for the shear flow v = (a y^2, 0) on the polygon.
-* dt: scales linearly with the CFL number (the absolute value is "parity
-  unpinned": the paper's dt table needs its own mesh).
+* dt: scales linearly with the CFL number (its p-scaling, its size against
+  the operator's spectral radius and the paper's dt table are pinned in
+  test_oracle_dt.py).
 """
 import numpy as np
 import pytest
