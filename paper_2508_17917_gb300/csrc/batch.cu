@@ -281,9 +281,18 @@ dg_status tune_groups(dg_batch *b)
 {
     if (b->tuned) return DG_OK;
     const dg::Phys<float> ph32 = phys_of<float>(b->prm);
-    cudaEvent_t e0, e1;
-    B_CUDA(b, cudaEventCreate(&e0));
-    B_CUDA(b, cudaEventCreate(&e1));
+    // events destroyed on every return path
+    struct Events {
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Events()
+        {
+            for (auto &x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev;
+    B_CUDA(b, cudaEventCreate(&ev.e[0]));
+    B_CUDA(b, cudaEventCreate(&ev.e[1]));
+    cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
     for (auto &g : b->groups) {
         if (b->variant_req != 0) {
             // the tensor-core shape covers p <= 6; other groups would take the two-node shape
@@ -340,8 +349,6 @@ dg_status tune_groups(dg_batch *b)
             }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     b->tuned = true;
     return DG_OK;
 }

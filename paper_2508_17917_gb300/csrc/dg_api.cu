@@ -458,6 +458,7 @@ dg_status dg_set_mesh(dg_ctx *c, int64_t Nv, const double *vx, const double *vy,
     if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel configuration");
     c->shape1 = c->shape;
     c->tuned = false;
+    c->fshape_variant = 0;           // the cooperative grid is sized per mesh
     c->has_tc = false;
     if (c->prm.precision == DG_PRECISION_MIXED) {
         if (!th) {
@@ -560,9 +561,18 @@ static dg_status tune_stage(dg_ctx *c, const double vw[2])
         return DG_OK;
     }
     if (c->rtmp.n != ndof(c)) DG_CUDA(c, c->rtmp.alloc(ndof(c)));
-    cudaEvent_t e0, e1;
-    DG_CUDA(c, cudaEventCreate(&e0));
-    DG_CUDA(c, cudaEventCreate(&e1));
+    // events destroyed on every return path
+    struct Events {
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Events()
+        {
+            for (auto &x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev;
+    DG_CUDA(c, cudaEventCreate(&ev.e[0]));
+    DG_CUDA(c, cudaEventCreate(&ev.e[1]));
+    cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
     float best = 0.f;
     dg::LaunchShape pick = c->shape1;
     for (const dg::LaunchShape *cand : {&c->shape1, &c->shape2, &c->shape3}) {
@@ -583,8 +593,6 @@ static dg_status tune_stage(dg_ctx *c, const double vw[2])
             pick = *cand;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     c->shape = pick;
     c->tuned = true;
     return DG_OK;
