@@ -60,7 +60,7 @@ typedef enum {
 
 enum { DG_PRECISION_FP64 = 0, DG_PRECISION_MIXED = 1 };
 enum { DG_BC_INTERIOR = 0, DG_BC_WALL = 1, DG_BC_FARFIELD = 2 };
-enum { DG_SOURCE_NONE = 0, DG_SOURCE_MANUFACTURED = 1 };
+enum { DG_SOURCE_NONE = 0, DG_SOURCE_MANUFACTURED = 1, DG_SOURCE_VORTEX = 2 };
 
 typedef struct {
     int p;                       /* polynomial degree, 1..6 (Sec. 2.2)                   */
@@ -204,8 +204,17 @@ dg_status dg_check_finite(dg_ctx *ctx, int *ok);
 /* Add a nodal source to every residual evaluation (Sec. 3.1).  kind
  * DG_SOURCE_MANUFACTURED takes params = (kappa, C2) and adds the source of
  * the manufactured steady solution U = (w, w, w, w^2), w = sin(kappa(x+y)) + C2,
- * evaluated at the nodes; DG_SOURCE_NONE removes it.
- * Errors: DG_EINVAL (no mesh, unknown kind, null params). */
+ * evaluated at the nodes.  kind DG_SOURCE_VORTEX takes params =
+ * (beta, x0, y0, L, u0, v0) and adds S = -div F_v(U_v(x, t)), the viscous
+ * source that makes the isentropic vortex U_v of strength beta, centred at
+ * (x0, y0) at t = 0, carried at (u0, v0) on a periodic square of side L
+ * (rho_inf = p_inf = 1), an exact Navier-Stokes solution (the source of the
+ * advected-vortex workload; the paper's Sec. 3.1 builds its source the same
+ * way from a manufactured solution); it is evaluated at the nodes at every
+ * stage's time t + c_i dt by a kernel of its own (FP64 arithmetic on the FP64
+ * path, FP32 on the mixed path), and with it fused steps fall back to five
+ * stage launches per step.  DG_SOURCE_NONE removes any source.
+ * Errors: DG_EINVAL (no mesh, unknown kind, null params, L <= 0), DG_ECUDA. */
 dg_status dg_set_source(dg_ctx *ctx, int kind, const double *params);
 
 /* Node coordinates of the current mesh, x and y each [K][Np] FP64 host

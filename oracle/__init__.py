@@ -125,7 +125,13 @@ class Problem:
         s.gamma, s.Pr, s.mu, s.theta, s.C1 = gamma, Pr, mu, theta, C1
         s.rho_inf, s.u_inf, s.v_inf, s.p_inf = rho_inf, u_inf, v_inf, p_inf
         s.adiabatic_zero_heatflux = int(adiabatic_zero_heatflux)
-        if source is not None:          # ("manufactured", kappa, C2) of Sec. 3.1
+        self.vortex = None
+        if source is not None and source[0] == "vortex":
+            # ("vortex", beta, x0, y0, L, u0, v0): S = -div F_v of the advected
+            # vortex, added on the Python side (vortex_source.py)
+            b, x0, y0, L, u0, v0 = (float(q) for q in source[1:7])
+            self.vortex = dict(beta=b, center=(x0, y0), L=L, u0=u0, v0=v0)
+        elif source is not None:        # ("manufactured", kappa, C2) of Sec. 3.1
             s.source_kind, s.src_kappa, s.src_C2 = 1, float(source[1]), float(source[2])
         if overint:                     # volume flux integrated with cubature(overint)
             oi = refelem.overint_operators(p, int(overint))
@@ -149,6 +155,14 @@ class Problem:
     def _ptr(self):
         return C.byref(self._s)
 
+    def vortex_source(self, t):
+        """Nodal S(x, t) of the vortex source, [K][4][Np]."""
+        from .vortex_source import vortex_viscous_source
+        v = self.vortex
+        S = vortex_viscous_source(self.x, self.y, t, self.params["gamma"], self.params["Pr"],
+                                  self.params["mu"], v["beta"], v["center"], v["L"], v["u0"], v["v0"])
+        return np.ascontiguousarray(np.transpose(S, (0, 2, 1)))
+
     def rhs(self, U, t=0.0, vw=(0.0, 0.0)):
         """dU/dt = M^-1 R(t, U) (Eq. dg_on_K), [K][4][Np]."""
         U = _f64(U)
@@ -157,11 +171,21 @@ class Problem:
         st = lib().oracle_rhs(self._ptr(), _p(U), float(t), _p(vwa), _p(R))
         if st != 0:
             raise RuntimeError(f"oracle_rhs failed ({st})")
+        if self.vortex is not None:
+            R += self.vortex_source(t)
         return R
 
     def lsrk_step(self, U, t, dt, vw=(0.0, 0.0)):
         """One five-stage 2N-storage step (Algorithm 1); returns the new state."""
         U = _f64(U).copy()
+        if self.vortex is not None:
+            # Algorithm 1 around the Python-side residual (time-dependent source)
+            A, B, c = lsrk_coeffs()
+            K1 = np.zeros_like(U)
+            for i in range(5):
+                K1 = A[i] * K1 + dt * self.rhs(U, t + c[i] * dt, vw)
+                U = U + B[i] * K1
+            return U
         vwa = _f64(vw)
         st = lib().oracle_lsrk_step(self._ptr(), _p(U), float(t), float(dt), _p(vwa))
         if st != 0:

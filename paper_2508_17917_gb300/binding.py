@@ -12,7 +12,7 @@ import os
 import numpy as np
 
 __all__ = ["DG_OK", "DG_PRECISION_FP64", "DG_PRECISION_MIXED", "DG_SOURCE_NONE",
-           "DG_SOURCE_MANUFACTURED", "DgParams", "DGError", "lib", "library_path",
+           "DG_SOURCE_MANUFACTURED", "DG_SOURCE_VORTEX", "DgParams", "DGError", "lib", "library_path",
            "dg_create", "dg_destroy", "dg_set_mesh", "dg_set_state", "dg_get_state", "dg_rhs",
            "dg_lsrk_step", "dg_lsrk_steps", "dg_compute_dt", "dg_wall_forces",
            "dg_wall_forces_noalloc", "DG_NOALLOC_MAX_WALL_FACES", "dg_rigid_step",
@@ -31,7 +31,7 @@ __all__ = ["DG_OK", "DG_PRECISION_FP64", "DG_PRECISION_MIXED", "DG_SOURCE_NONE",
 
 DG_OK = 0
 DG_PRECISION_FP64, DG_PRECISION_MIXED = 0, 1
-DG_SOURCE_NONE, DG_SOURCE_MANUFACTURED = 0, 1
+DG_SOURCE_NONE, DG_SOURCE_MANUFACTURED, DG_SOURCE_VORTEX = 0, 1, 2
 DG_NOALLOC_MAX_WALL_FACES = 16384
 STATUS = {0: "DG_OK", -1: "DG_EINVAL", -2: "DG_EMESH", -3: "DG_ECUDA", -4: "DG_ENONFINITE",
           -5: "DG_ETIMEOUT", -6: "DG_EUNSUPPORTED"}

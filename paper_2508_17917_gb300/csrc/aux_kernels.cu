@@ -297,7 +297,59 @@ __global__ void batch_record_kernel(const BatchCase *cases, int n, double *hist,
     if (threadIdx.x == 0) *counter = row + 1;
 }
 
+// Viscous source of the advected isentropic vortex, S = -div F_v(U_v), in
+// closed form.  With (dx, dy) the offset of the node from the nearest
+// periodic image of the centre (x0 + u0 t, y0 + v0 t), r^2 = dx^2 + dy^2,
+// f = beta / (2 pi) exp((1 - r^2) / 2) and (du, dv) = f (-dy, dx) the
+// velocity perturbation: the perturbation is divergence free and its
+// Laplacian is -(4 - r^2)(du, dv), the stress work tau : grad v is
+// mu f^2 r^4 and the Laplacian of T = 1 - a exp(1 - r^2) is
+// 4 a exp(1 - r^2)(1 - r^2), so
+//   S_rho = 0,   S_m = mu (4 - r^2) (du, dv),
+//   S_E = mu (4 - r^2)(u0 du + v0 dv)
+//         + mu beta^2 / (2 pi^2) exp(1 - r^2) (r^2 (2 - r^2) - (1 - r^2) / Pr).
+// One thread per node; `real` is the arithmetic (FP64 path: double; mixed:
+// float after the offset is formed in double).
+template <typename real>
+__global__ void vortex_source_kernel(const double *xy, long long nn, int Np, VortexSource v, double t,
+                                     double *S)
+{
+    const long long n = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (n >= nn) return;
+    double ddx = xy[n] - (v.x0 + v.u0 * t);
+    double ddy = xy[nn + n] - (v.y0 + v.v0 * t);
+    ddx -= v.L * rint(ddx / v.L);
+    ddy -= v.L * rint(ddy / v.L);
+    const real dx = real(ddx), dy = real(ddy);
+    const real r2 = dx * dx + dy * dy;
+    const real e1 = exp(real(1) - r2);
+    const real f = real(v.beta / (2.0 * 3.14159265358979323846)) * sqrt(e1);
+    const real du = -f * dy, dv = f * dx;
+    const real mu = real(v.mu), w = mu * (real(4) - r2);
+    const real c = real(v.beta * v.beta / (2.0 * 3.14159265358979323846 * 3.14159265358979323846));
+    const real sE = w * (real(v.u0) * du + real(v.v0) * dv) +
+                    mu * c * e1 * (r2 * (real(2) - r2) - (real(1) - r2) / real(v.Pr));
+    const long long k = n / Np;
+    const int i = static_cast<int>(n - k * Np);
+    double *o = S + k * 4 * Np + i;
+    o[0] = 0.0;
+    o[Np] = static_cast<double>(w * du);
+    o[2 * Np] = static_cast<double>(w * dv);
+    o[3 * Np] = static_cast<double>(sE);
+}
+
 }  // namespace
+
+cudaError_t launch_vortex_source(bool fp64, const double *xy, long long nn, int Np, const VortexSource &v,
+                                 double t, double *S, cudaStream_t st)
+{
+    const unsigned blocks = static_cast<unsigned>((nn + 255) / 256);
+    if (fp64)
+        vortex_source_kernel<double><<<blocks, 256, 0, st>>>(xy, nn, Np, v, t, S);
+    else
+        vortex_source_kernel<float><<<blocks, 256, 0, st>>>(xy, nn, Np, v, t, S);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_batch_dt(const double *lam, const long long *seg, BatchCase *cases, int ncases, double cfl,
                             const double *fixed, cudaStream_t st)

@@ -67,6 +67,8 @@ struct dg_ctx {
     unsigned bar_limit = 1u << 24;
     bool bar_used = false;
     int source_kind = DG_SOURCE_NONE;
+    dg::VortexSource vortex{};         // DG_SOURCE_VORTEX parameters
+    dg::DevBuf<double> src_xy;        // node coordinates for the vortex source
 
     double *cur() { return cur_is_a ? K0a.ptr : K0b.ptr; }
     double *other() { return cur_is_a ? K0b.ptr : K0a.ptr; }
@@ -162,6 +164,12 @@ dg_status run_stage(dg_ctx *c, int s, double t, double dt, const double vw[2], i
     sp.Rout = rout;
     sp.conn = c->conn.ptr;
     sp.fmask = c->fmask.ptr;
+    if (c->source_kind == DG_SOURCE_VORTEX) {
+        // time-dependent source at the stage's time, evaluated before the stage
+        DG_CUDA(c, dg::launch_vortex_source(c->prm.precision == DG_PRECISION_FP64, c->src_xy.ptr,
+                                            c->K * c->ops.Np, c->ops.Np, c->vortex, t, c->src.ptr, c->stream));
+        c->launches += 1;
+    }
     sp.src = (c->source_kind != DG_SOURCE_NONE) ? c->src.ptr : nullptr;
     sp.Sin = c->scur();
     sp.Pin = c->pcur();
@@ -534,10 +542,25 @@ dg_status dg_set_source(dg_ctx *c, int kind, const double *params)
         c->source_kind = kind;
         return DG_OK;
     }
-    if (kind != DG_SOURCE_MANUFACTURED || !params) return fail(c, DG_EINVAL, "unknown source kind");
+    if ((kind != DG_SOURCE_MANUFACTURED && kind != DG_SOURCE_VORTEX) || !params)
+        return fail(c, DG_EINVAL, "unknown source kind");
     const int Np = c->ops.Np;
     std::vector<double> x(static_cast<size_t>(c->K) * Np), y(x.size());
     dg_node_coords(c, x.data(), y.data());
+    if (kind == DG_SOURCE_VORTEX) {
+        for (int q = 0; q < 6; ++q)
+            if (!std::isfinite(params[q])) return fail(c, DG_EINVAL, "vortex source parameters must be finite");
+        if (!(params[3] > 0.0)) return fail(c, DG_EINVAL, "vortex source period L must be > 0");
+        c->vortex = dg::VortexSource{params[0], params[1], params[2], params[3], params[4], params[5],
+                                     c->prm.mu, c->prm.Pr};
+        DG_CUDA(c, c->src_xy.alloc(2 * x.size()));
+        DG_CUDA(c, cudaMemcpy(c->src_xy.ptr, x.data(), x.size() * sizeof(double), cudaMemcpyHostToDevice));
+        DG_CUDA(c, cudaMemcpy(c->src_xy.ptr + x.size(), y.data(), y.size() * sizeof(double),
+                              cudaMemcpyHostToDevice));
+        DG_CUDA(c, c->src.alloc(ndof(c)));
+        c->source_kind = kind;
+        return DG_OK;
+    }
     std::vector<double> S(ndof(c));
     for (long long k = 0; k < c->K; ++k)
         for (int i = 0; i < Np; ++i) {
@@ -677,7 +700,8 @@ dg_status dg_lsrk_step(dg_ctx *c, double t, double dt, const double vw[2])
         dg_status st = tune_stage(c, vw);
         if (st != DG_OK) return st;
     }
-    if (c->fused) return run_fused_step(c, dt, vw);
+    // a time-dependent source is evaluated per stage: five launches
+    if (c->fused && c->source_kind != DG_SOURCE_VORTEX) return run_fused_step(c, dt, vw);
     for (int s = 0; s < 5; ++s) {
         dg_status st = run_stage(c, s, t + kRkC[s] * dt, dt, vw, dg::STAGE_UPDATE, c->cur(), c->other(), nullptr);
         if (st != DG_OK) return st;

@@ -141,4 +141,14 @@ cudaError_t launch_batch_record(const BatchCase *cases, int ncases, double *hist
 // *flag = 1 if any of x[0..n) is not finite (flag must be zeroed first)
 cudaError_t launch_nonfinite(const double *x, long long n, int *flag, cudaStream_t st);
 
+// viscous source of the advected isentropic vortex (dg_set_source kind 2)
+struct VortexSource {
+    double beta, x0, y0, L, u0, v0;   // strength, centre at t = 0, period, advection velocity
+    double mu, Pr;
+};
+// S[K][4][Np] at time t from node coordinates xy = (x[K*Np], y[K*Np]);
+// fp64: double arithmetic, else float after the offsets
+cudaError_t launch_vortex_source(bool fp64, const double *xy, long long nn, int Np, const VortexSource &v,
+                                 double t, double *S, cudaStream_t st);
+
 }  // namespace dg

@@ -12,6 +12,7 @@ import pytest
 import dg_inputs
 import oracle
 from dg_inputs.states import to_kcn
+from _parity import INC_TOL, check_rhs, inc_err, rel_l2
 
 pytestmark = pytest.mark.gpu
 GAMMA, MACH = 1.4, 0.2
@@ -142,10 +143,12 @@ def test_batch_case_matches_oracle_loop(small_run, i, run):
         assert rel_err(got[:, col], ref[:, col]) <= TOL, (name, rel_err(got[:, col], ref[:, col]))
     # drag relative to its mean
     assert np.abs(got[:, 5] - ref[:, 5]).max() <= TOL * np.abs(ref[:, 5]).mean()
-    d = Us[i] - U_ref
-    J, M = P.geo["J"], P.ops["M"]
-    err = np.sqrt(np.einsum("k,kcn,nm,kcm->c", J, d, M, d) / np.einsum("k,kcn,nm,kcm->c", J, U_ref, M, U_ref))
+    err = rel_l2(P, Us[i] - U_ref, U_ref)
     assert np.all(err <= 2e-5), err
+    # the state moves by ~1e-5 of itself over the window: the increment is
+    # what tells updated states from stale ones
+    inc = inc_err(P, Us[i], U_ref, states[i])
+    assert np.all(inc <= INC_TOL["mixed"]), inc
     assert rigid[i, 9] == 0
 
 
@@ -190,7 +193,9 @@ def test_batch_rejects_bad_mesh(dg):
 def test_full_sweep_sampled_cases(dg):
     """The 64-case sweep (10k-60k triangles, p = 3..6; the bench's workload):
     two steps of the whole batch, then the smallest case of each degree
-    against the oracle."""
+    against the oracle (state and increment per field, lift), plus the
+    residual per field of that case's mesh and start state through a
+    single-case context."""
     sweep = dg_inputs.viv_sweep()
     cases = []
     for c in sweep:
@@ -209,10 +214,16 @@ def test_full_sweep_sampled_cases(dg):
     for i, c in enumerate(cases):
         if c["p"] not in picks or c["mesh"].K < cases[picks[c["p"]]]["mesh"].K:
             picks[c["p"]] = i
+    import torch
     for p, i in sorted(picks.items()):
         ref, U_ref, P = oracle_loop(cases[i], states[i], 2)
         assert rel_err(rigid[i, 7], ref[-1, 6]) <= TOL, (p, i)
-        d = b.get_state(i) - U_ref
-        J, M = P.geo["J"], P.ops["M"]
-        err = np.sqrt(np.einsum("k,kcn,nm,kcm->c", J, d, M, d) / np.einsum("k,kcn,nm,kcm->c", J, U_ref, M, U_ref))
+        got = b.get_state(i)
+        err = rel_l2(P, got - U_ref, U_ref)
         assert np.all(err <= 2e-5), (p, i, err)
+        inc = inc_err(P, got, U_ref, states[i])
+        assert np.all(inc <= INC_TOL["mixed"]), (p, i, inc)
+        s = dg.Solver(cases[i]["mesh"], p, "mixed", stream=torch.cuda.current_stream().cuda_stream,
+                      mu=cases[i]["mu"], **FAR)
+        s.set_state(states[i])
+        check_rhs(P, states[i], s.rhs(0.0), "mixed")

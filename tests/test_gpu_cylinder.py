@@ -14,6 +14,7 @@ import pytest
 import dg_inputs
 import oracle
 from dg_inputs.states import to_kcn
+from _parity import INC_TOL, STATE_TOL, check_rhs, inc_err, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -40,13 +41,14 @@ def stream():
     return torch.cuda.current_stream().cuda_stream
 
 
-def start_state(P, seed=0):
+def start_state(P, seed=0, cross=0.0):
     r = np.hypot(P.x, P.y)
     U = to_kcn(dg_inputs.free_stream(P.x.shape, rho=1.0, u=1.0, v=0.0, p=P_INF))
     # smooth near-wall deficit so the start is not impulsive, plus a seeded perturbation
     damp = np.tanh(4.0 * (r - 0.5))
     U[:, 1] *= damp
-    U[:, 3] = P_INF / (GAMMA - 1) + 0.5 * U[:, 1] ** 2 / U[:, 0]
+    U[:, 2] = cross * damp * np.sin(np.arctan2(P.y, P.x))     # optional cross-flow: no field is zero
+    U[:, 3] = P_INF / (GAMMA - 1) + 0.5 * (U[:, 1] ** 2 + U[:, 2] ** 2) / U[:, 0]
     return dg_inputs.perturb(U, seed=seed, amp=1e-3)
 
 
@@ -81,19 +83,35 @@ def test_cylinder_cl_cd_window(dg, precision):
     assert e_cl <= TOL[precision] and e_cd <= TOL[precision], (e_cl, e_cd)
 
 
+_FULL = {}
+
+
+def full_mesh():
+    if not _FULL:
+        mesh = dg_inputs.ogrid_cylinder(120, 170, 0.5, 30.0, seed=0)
+        assert mesh.K == 40800
+        P = oracle.Problem(mesh, 4, **KW)
+        U0 = start_state(P, seed=1, cross=0.05)
+        dt, _ = P.dt(U0, 0.3)
+        _FULL.update(mesh=mesh, P=P, U0=U0, dt=dt, ref=P.run(U0, 0.0, dt, 10))
+    return _FULL
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_cylinder_full_mesh_short(dg, precision):
-    """The 120 x 170 seeded O-grid (K = 40,800) at p = 4, ten steps."""
-    mesh = dg_inputs.ogrid_cylinder(120, 170, 0.5, 30.0, seed=0)
-    assert mesh.K == 40800
-    P = oracle.Problem(mesh, 4, **KW)
-    U0 = start_state(P, seed=1)
-    dt, _ = P.dt(U0, 0.3)
-    ref = P.run(U0, 0.0, dt, 10)
-    s = dg.Solver(mesh, 4, precision, stream=stream(), **KW)
+    """The 120 x 170 seeded O-grid (K = 40,800) at p = 4: residual per field,
+    ten steps (state and increment per field), wall forces."""
+    f = full_mesh()
+    P, U0, dt, ref = f["P"], f["U0"], f["dt"], f["ref"]
+    s = dg.Solver(f["mesh"], 4, precision, stream=stream(), **KW)
     s.set_state(U0)
+    check_rhs(P, U0, s.rhs(0.0), precision)
     assert abs(s.dt(0.3) - dt) <= 1e-12 * dt
     s.steps(0.0, dt, 10)
+    got = s.get_state()
+    assert np.all(rel_l2(P, got - ref, ref) <= STATE_TOL[precision])
+    inc = inc_err(P, got, ref, U0)
+    assert np.all(inc <= INC_TOL[precision]), inc
     F_ref = P.wall_forces(ref)
     F_got = s.wall_forces()
     assert np.all(np.abs(F_got - F_ref) <= TOL[precision] * np.abs(F_ref).max()), (F_got, F_ref)

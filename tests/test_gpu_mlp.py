@@ -242,3 +242,43 @@ def test_switching_implementations_keeps_the_weights(dg):
     assert rel_l2(y_chunked, y_layers) <= 1e-3
     ref, _ = omlp.forward(net.get_params().astype(np.float64), sizes(), x.cpu().numpy(), bf16=True)
     assert rel_l2(y_chunked, ref) <= 2e-3
+
+
+def test_switch_between_graph_replayed_runs(dg):
+    """A graph-replayed run (8 steps) on the chunked path, then the
+    layer-by-layer path with the same tensors and history buffer: the step
+    count and the loss history continue (the cached graph of the first path
+    is not replayed for the second), nothing is written outside the history
+    window, and the result equals the same 16 steps taken one call at a time
+    and follows the oracle's Adam steps on the oracle's own gradients."""
+    import torch
+    rng = np.random.default_rng(31)
+    x = torch.from_numpy(rng.normal(size=(384, N_IN)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.normal(size=(384, N_OUT)).astype(np.float32)).cuda()
+    lr = 1e-3
+    a = make(dg, "chunked", N_IN, WIDTH, DEPTH, N_OUT, max_batch=512, seed=14)
+    b = make(dg, "chunked", N_IN, WIDTH, DEPTH, N_OUT, max_batch=512, seed=14)
+    p0 = a.get_params().astype(np.float64)
+    guard = torch.full((10,), 12345.0, dtype=torch.float32, device="cuda")
+    hist = guard[1:9]                       # the loss history, with one guard value each side
+    h1 = a.train(x, t, 8, lr, out=hist).cpu().numpy().copy()
+    a.fused = False
+    h2 = a.train(x, t, 8, lr, out=hist).cpu().numpy().copy()
+    g = guard.cpu().numpy()
+    assert g[0] == 12345.0 and g[9] == 12345.0, g
+    hb1 = np.concatenate([b.train(x, t, 1, lr).cpu().numpy() for _ in range(8)])
+    b.fused = False
+    hb2 = np.concatenate([b.train(x, t, 1, lr).cpu().numpy() for _ in range(8)])
+    assert np.array_equal(h1, hb1) and np.array_equal(h2, hb2)
+    assert np.array_equal(a.get_params(), b.get_params())
+    # the oracle's 16 Adam steps (bf16 rounding points as in the kernels)
+    p, m, v = p0.copy(), np.zeros_like(p0), np.zeros_like(p0)
+    losses = []
+    xs, ts = x.cpu().numpy(), t.cpu().numpy()
+    for step in range(1, 17):
+        loss, gr = omlp.loss_and_grad(p, sizes(), xs, ts, bf16=True)
+        losses.append(loss)
+        p, m, v = omlp.adam_step(p, gr, m, v, step, lr)
+    got = np.concatenate([h1, h2])
+    assert np.abs(got - np.array(losses)).max() <= 1e-3 * abs(losses[0]), (got, losses)
+    assert rel_l2(a.get_params().astype(np.float64) - p0, p - p0) <= 2e-2

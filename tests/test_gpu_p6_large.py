@@ -1,13 +1,14 @@
 """p = 6 (Np = 28) on an 80,000-triangle seeded O-grid (200 x 200 cells,
 r in [0.5, 30], wall and far field), Re = 150, M = 0.2: the library against
-the oracle over three LSRK steps (state per field and wall forces), in both
-precisions, plus the time step."""
+the oracle, in both precisions: the residual per field, three LSRK steps
+(state and increment per field, wall forces) and the time step."""
 import numpy as np
 import pytest
 
 import dg_inputs
 import oracle
 from dg_inputs.states import to_kcn
+from _parity import INC_TOL, check_rhs, inc_err, rel_l2
 
 pytestmark = pytest.mark.gpu
 GAMMA, MACH, RE = 1.4, 0.2, 150.0
@@ -46,12 +47,15 @@ def test_p6_80k_three_steps(case, precision):
     mesh, P, U0, dt, ref, F_ref = case
     s = dg.Solver(mesh, 6, precision, stream=torch.cuda.current_stream().cuda_stream, **KW)
     s.set_state(U0)
+    check_rhs(P, U0, s.rhs(0.0), precision)
     assert abs(s.dt(0.3) - dt) <= 1e-12 * dt
     s.steps(0.0, dt, 3)
     got = s.get_state()
-    d = got - ref
-    J, M = P.geo["J"], P.ops["M"]
-    err = np.sqrt(np.einsum("k,kcn,nm,kcm->c", J, d, M, d) / np.einsum("k,kcn,nm,kcm->c", J, ref, M, ref))
+    err = rel_l2(P, got - ref, ref)
     assert np.all(err <= TOL[precision]), err
+    # the state moves by ~1e-6 of itself in three steps: the increment is
+    # what tells an updated state from a stale one
+    inc = inc_err(P, got, ref, U0)
+    assert np.all(inc <= INC_TOL[precision]), inc
     F = s.wall_forces()
     assert np.all(np.abs(F - F_ref) <= FORCE_TOL[precision] * np.abs(F_ref).max()), (F, F_ref)

@@ -1,16 +1,17 @@
 """Both tile shapes of the mixed-precision stage kernel against the oracle:
 one node per thread (variant 1) and two volume nodes plus two face nodes of
 one face per thread (variant 2), forced through dg_set_stage_variant; and the
-first-step tuner's choice.  Tolerances as for the mixed path: 2e-5 relative
-to the largest residual entry up to p = 4; beyond, the FP32 rounding of the
-state is amplified by the derivative matrices, whose largest absolute row
-sums grow like p^2, so the residual bound grows by (p / 4)^2."""
+first-step tuner's choice.  Tolerances as for the mixed path
+(tests/_parity.py): 2e-5 relative to the largest residual entry and, per
+field, 10 x the change of the oracle's residual under FP32 rounding of its
+input state, at every p."""
 import numpy as np
 import pytest
 
 import dg_inputs
 import oracle
 from dg_inputs.states import to_kcn
+from _parity import check_rhs
 
 pytestmark = pytest.mark.gpu
 
@@ -24,10 +25,6 @@ def dg():
     build.build()
     import paper_2508_17917_gb300 as dg
     return dg
-
-
-def rhs_tol(p):
-    return 2e-5 * max(1.0, (p / 4.0) ** 2)
 
 
 def stream():
@@ -48,7 +45,7 @@ def test_rhs_periodic_variant(dg, p, variant):
     assert s.variant == variant
     s.set_state(U)
     got = s.rhs(0.0, vw)
-    assert np.abs(got - ref).max() / np.abs(ref).max() <= rhs_tol(p)
+    check_rhs(P, U, got, "mixed", 0.0, vw, ref)
 
 
 @pytest.mark.parametrize("variant", [1, 2])
@@ -67,7 +64,7 @@ def test_rhs_ogrid_variant(dg, p, variant):
     s.set_variant(variant)
     s.set_state(U)
     got = s.rhs(0.0, vw)
-    assert np.abs(got - ref).max() / np.abs(ref).max() <= rhs_tol(p)
+    check_rhs(P, U, got, "mixed", 0.0, vw, ref)
 
 
 @pytest.mark.parametrize("variant", [2, 0])

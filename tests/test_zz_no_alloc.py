@@ -66,3 +66,28 @@ def test_noalloc_rejects_too_many_wall_faces(dg):
         dg.dg_wall_forces_noalloc(s.ctx, (0.0, 0.0))
     assert e.value.status == -1
     assert "wall faces" in str(e.value) and "dg_wall_forces" in str(e.value)
+
+
+def test_noalloc_at_the_limit_allocates_nothing(dg):
+    """Exactly DG_NOALLOC_MAX_WALL_FACES wall faces (the largest accepted
+    size): the result matches dg_wall_forces, and after a first call (which
+    looks up the array's address) further calls leave the device's free
+    memory unchanged -- any cudaMalloc would take at least one 2 MB page."""
+    import torch
+    n = dg.DG_NOALLOC_MAX_WALL_FACES
+    mesh = dg_inputs.ogrid_cylinder(n, 1, 0.5, 0.6, seed=0)
+    kw = dict(mu=0.01, rho_inf=1.0, u_inf=1.0, v_inf=0.0, p_inf=17.857142857142858)
+    s = dg.Solver(mesh, 1, "fp64", stream=stream(), **kw)
+    x, y = s.node_coords()
+    s.set_state(wall_state(x, y, kw["p_inf"]))
+    ref = s.wall_forces((0.0, 0.0))
+    first = dg.dg_wall_forces_noalloc(s.ctx, (0.0, 0.0))
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    again = [dg.dg_wall_forces_noalloc(s.ctx, (0.0, 0.0)) for _ in range(3)]
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    scale = np.abs(ref).max()
+    for got in [first] + again:
+        assert np.all(np.abs(got - ref) <= 1e-12 * scale), (got, ref)
