@@ -54,6 +54,30 @@ CONFIG = {"workload": "isentropic vortex, p=4 (Np=15), periodic [0,10]^2, 128x12
                 "stays in L2 across the 5 stages of a step"}
 
 
+# FP64 peak for the FP64 path's roofline: the GB300's nominal FP64 rate
+# (a DFMA microbenchmark measured 1.18-1.20 TFLOP/s on this GPU)
+FP64_PEAK_GFLOPS = 1250.0
+
+
+def algorithmic_flops_per_dof_stage(p):
+    """Floating-point operations of one DOF-stage of the method, counted by
+    phase per element and divided by its 4 Np DOFs: broken gradient (two
+    Np x Np contractions per field, then the metric terms), the volume flux
+    at every node (primitives, pressure, advective and viscous fluxes,
+    contravariant components: about 96), the divergence (two contractions),
+    the face flux at every face node of each side (Roe flux, two penalty
+    norms, normal fluxes, jump: about 250), the lift (Np x 3 Nfp per field)
+    and the register update (2 FMA per DOF).  At p = 4: about 246."""
+    Np, NF = (p + 1) * (p + 2) // 2, 3 * (p + 1)
+    grad = 2 * 4 * Np * Np * 2 + 4 * Np * 6
+    vol = 96 * Np
+    div = 2 * 4 * Np * Np * 2
+    face = 250 * NF
+    lift = 4 * Np * NF * 2
+    upd = 16 * Np
+    return (grad + vol + div + face + lift + upd) / (4.0 * Np)
+
+
 def algorithmic_bytes_per_step(K, geo_bytes):
     dof = 4 * K * NP
     state = dof * (24 + 4 * 32)          # stage 1 skips the K1 read
@@ -84,24 +108,70 @@ def kernel_hash(variant=2):
     return h.hexdigest()[:16]
 
 
-PROFILE_OF_VARIANT = {1: "stage_kernel_mixed_p4.md", 2: "stage_kernel_mixed2_p4.md", 3: "stage_kernel_tc_p4.md"}
 KERNEL_OF_VARIANT = {1: "dg::stage_mixed_kernel<4, false>", 2: "dg::stage_mixed2_kernel<4, false>",
                      3: "dg::stage_tc_kernel<4, false, false, false>"}
 SHAPE_OF_VARIANT = {1: "one node per thread", 2: "two nodes per thread",
                     3: "one warp per two elements, tensor-core contractions"}
 
 
+def traffic_record_path():
+    return os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+
+
 def recorded_traffic(variant):
-    """DRAM bytes per DOF-stage of the mixed stage kernel in use, from its
-    committed ncu summary, if that was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", PROFILE_OF_VARIANT.get(variant, ""))
-    if not os.path.isfile(path):
+    """DRAM bytes per DOF-stage of the mixed stage kernel in use, from the
+    record `--record-traffic` writes from an ncu capture, if that capture was
+    taken on the current kernel source."""
+    path = traffic_record_path()
+    if not os.path.isfile(path) or variant not in KERNEL_FILES:
         return None
-    text = open(path).read()
-    m = re.search(r"dram_bytes_per_dof_stage:\s*([0-9.eE+-]+)\s*\(kernel_hash\s+([0-9a-f]+)\)", text)
-    if not m or variant not in KERNEL_FILES or m.group(2) != kernel_hash(variant):
+    rec = json.load(open(path)).get(str(variant))
+    if not rec or rec.get("kernel_hash") != kernel_hash(variant):
         return None
-    return float(m.group(1))
+    return float(rec["dram_bytes_per_dof_stage"])
+
+
+_BYTE_UNITS = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "tbyte": 1e12}
+
+
+def ncu_dram_bytes(csv_path, kernel_regex):
+    """dram__bytes_read.sum + dram__bytes_write.sum of every launch whose name
+    matches kernel_regex, from `ncu -i REP --page raw --csv` output."""
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    head = next(i for i, r in enumerate(rows) if "Kernel Name" in r and "dram__bytes_read.sum" in r)
+    names, units = rows[head], rows[head + 1]
+    col = {n: i for i, n in enumerate(names)}
+    out = []
+    for r in rows[head + 2:]:
+        if len(r) != len(names) or not re.search(kernel_regex, r[col["Kernel Name"]]):
+            continue
+        tot = 0.0
+        for m in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            tot += float(r[col[m]].replace(",", "")) * _BYTE_UNITS[units[col[m]].strip().lower()]
+        out.append(tot)
+    return out
+
+
+def record_traffic(args):
+    """Write the DRAM bytes per DOF-stage of one captured stage launch of the
+    mixed kernel (variant args.variant) into the traffic record, keyed by the
+    kernel's source hash."""
+    if args.variant not in KERNEL_FILES:
+        raise SystemExit("--record-traffic needs --variant 1, 2 or 3")
+    kname = KERNEL_OF_VARIANT[args.variant].split("<")[0].replace("dg::", "")
+    launches = ncu_dram_bytes(args.record_traffic, kname)
+    if not launches:
+        raise SystemExit(f"no {kname} launch with DRAM counters in {args.record_traffic}")
+    dofs = 4 * args.record_k * NP
+    path = traffic_record_path()
+    rec = json.load(open(path)) if os.path.isfile(path) else {}
+    rec[str(args.variant)] = {
+        "kernel": KERNEL_OF_VARIANT[args.variant], "kernel_hash": kernel_hash(args.variant),
+        "dram_bytes_per_dof_stage": launches[0] / dofs, "launch_bytes": launches[0], "K": args.record_k,
+        "note": "a stage-2..5 launch (reads K1); from " + os.path.basename(args.record_traffic)}
+    json.dump(rec, open(path, "w"), indent=1, sort_keys=True)
+    print(json.dumps(rec[str(args.variant)]))
 
 
 def measured_peaks():
@@ -291,6 +361,22 @@ def run_ours(args):
     s64.set_state(U64)
     t64, _ = timed_steps(dg, torch, s64, dt64, max(3, args.steps // 20), 2, flush, stream)
     v64 = dof * 5 * len(t64) / (sum(t64) * 1e-3)
+    fl64 = algorithmic_flops_per_dof_stage(P)
+    roof64 = {"bound": "alu", "achieved": fl64 * v64 / 1e9, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+              "frac": fl64 * v64 / 1e9 / FP64_PEAK_GFLOPS,
+              "peak_kind": "nominal GB300 FP64 rate (DFMA probe: 1.18-1.20 TFLOP/s)",
+              "flops_per_dof_stage": fl64, "kernel": "dg::stage_kernel<4, double>"}
+
+    # --- the same mixed path with the viscous vortex source (config 2's source
+    #     term, S = -div F_v of the advected vortex, one source kernel per stage)
+    s.set_source(dg.DG_SOURCE_VORTEX, (5.0, 5.0, 5.0, 10.0, 0.3 * 1.4 ** 0.5, 0.0))
+    s.set_state(U0)
+    tsrc, lsrc = timed_steps(dg, torch, s, dt, max(5, args.steps // 10), 3, flush, stream)
+    s.set_source(dg.DG_SOURCE_NONE)
+    vsrc = dof * 5 * len(tsrc) / (sum(tsrc) * 1e-3)
+    with_source = {"workload": "same, with the viscous vortex source evaluated at every stage's time",
+                   "value": vsrc, "unit": UNIT, "ms_per_step": sum(tsrc) / len(tsrc),
+                   "with_over_without": vsrc / (value / ws), "launches_per_step": lsrc / len(tsrc)}
 
     # --- over-integration (FP64 path): the volume flux on a collapsed Gauss
     #     rule of degree min(3p, 15) instead of at the nodes, same workload
@@ -403,9 +489,10 @@ def run_ours(args):
     e2e = {"value": ws * dof * 5 * e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(host_in.numel() * 8), "d2h_bytes_per_step": int(host_out.numel() * 8)}
 
-    cpu = None
+    cpu = cpu1 = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(budget_s=args.cpu_seconds)
+        cpu1 = cpu_baseline(budget_s=args.cpu_seconds, threads=1)
 
     if ws > 1:
         torch.distributed.barrier()
@@ -418,7 +505,8 @@ def run_ours(args):
             "config": dict(CONFIG, parallelism=f"replicas x{ws}"),
             "roofline": roofline,
             "fp64_path": {"value": v64, "unit": UNIT, "ms_per_step": sum(t64) / len(t64),
-                          "mixed_over_fp64": value / ws / v64},
+                          "mixed_over_fp64": value / ws / v64, "roofline": roof64},
+            "with_source": with_source,
             "overint_path": overint,
             "large_mesh": large,
             "fused_steps": fused,
@@ -428,6 +516,7 @@ def run_ours(args):
             "batch_viv": batch,
             "mlp": mlp_line,
             "cpu_baseline": cpu,
+            "cpu_baseline_1t": cpu1,
             "e2e": e2e,
             "clocks": clk.summary(),
             "gpu_launches": int(launches),
@@ -527,16 +616,17 @@ def run_mlp(dg, torch, np, B=4096, steps=200):
             "timing": "host clock around a synchronising call"}
 
 
-def cpu_baseline(budget_s=20.0):
-    """The oracle (plain FP64 C, OpenMP over elements) on the host cores:
-    LSRK steps of the benchmark's own p = 4 vortex mesh (128 x 128 split
-    quads), as many as fit the time budget (at least one)."""
+def cpu_baseline(budget_s=20.0, threads=None):
+    """The oracle (plain FP64 C, OpenMP over elements) on the host cores (all
+    of them, or `threads`): LSRK steps of the benchmark's own p = 4 vortex
+    mesh (128 x 128 split quads), as many as fit the time budget (at least
+    one)."""
     import numpy as np
     import dg_inputs
     import oracle
     from dg_inputs.states import to_kcn
     oracle.build_oracle()
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     oracle.set_threads(cores)
     n = 128
     m = dg_inputs.periodic_square(n)
@@ -595,7 +685,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic: seeded isentropic vortex on a periodic square",
-            "config": dict(CONFIG, parallelism="host cores, rank 0"),
+            "config": dict(CONFIG, parallelism="host cores, rank 0",
+                           precision="FP64 throughout (the oracle)"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -668,9 +759,16 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3],
                     help="tile shape of the headline's mixed kernel (0: first-step tuner)")
+    ap.add_argument("--record-traffic", default=None, metavar="CSV",
+                    help="ncu raw-page CSV of one stage launch: write its DRAM bytes per DOF-stage")
+    ap.add_argument("--record-k", type=int, default=2 * 512 * 512,
+                    help="elements of the captured launch (--record-traffic)")
     ap.add_argument("--profile", choices=["mixed512", "mixed128", "fp64_128", "sip128", "tc512", "tcsip512", "tc6_375", "mlp4096",
                              "batch64"], default=None)
     args = ap.parse_args()
+    if args.record_traffic:
+        record_traffic(args)
+        return
     if args.profile:
         run_profile(args)
         return

@@ -14,24 +14,27 @@
 * inc_err: relative L2 error per field of the increment U_n - U_0, which a
   run that skipped its updates fails with error 1.
 
-Tolerances (each derived in the test that uses it):
-  FP64 path: all-field residual 1e-12 and per field 1e-11 (a field whose
-  residual is small next to its largest flux term, as rho v1 next to the
-  pressure p_inf = 17.9 on the O-grid, is about 300 times more sensitive to
-  rounding than its size: 1.3e-12 was measured there); state 1e-12; increment
-  1e-9 (FP64 rounding of the state, 1e-16 |U|, against increments of 1e-6 |U|
-  and more);
-  mixed path: all-field residual 2e-5 and per field MIXED_SENS x the FP32
-  sensitivity; state 2e-5; increment 5e-4 (the increment is a sum of dt R, so
-  it carries the residual's relative error, at most about 2e-4 per field on
-  the O-grid states).
+Tolerances:
+  FP64 path: residual 1e-12 relative to its largest entry and 1e-11 per field
+  (a field whose residual is small next to its largest flux term, as rho v1
+  next to the pressure p_inf = 17.9 on the O-grid, is about 300 times more
+  sensitive to rounding than its size: 1.3e-12 was measured there); state
+  1e-12; increment 1e-9 (FP64 rounding of the state, 1e-16 |U|, against
+  increments of 1e-6 |U| and more);
+  mixed path: residual per field MIXED_SENS x the FP32 sensitivity (a fixed
+  max-norm bound does not fit: the sensitivity grows with the number of
+  elements sampled and with p, from 5e-7 on 50 elements at p = 1 to 5.6e-5
+  on 32,768 elements at p = 4); state 2e-5 relative L2 per field (the bound
+  the method is held to after 100 steps); increment 5e-4 (the increment is a
+  sum of dt R, so it carries the residual's relative error, at most about
+  2e-4 per field on the O-grid states).
 """
 import numpy as np
 
 MIXED_SENS = 10.0
 INC_TOL = {"fp64": 1e-9, "mixed": 5e-4}
 STATE_TOL = {"fp64": 1e-12, "mixed": 2e-5}
-RHS_TOL_ALL = {"fp64": 1e-12, "mixed": 2e-5}
+RHS_TOL_ALL_FP64 = 1e-12
 RHS_TOL_FIELD_FP64 = 1e-11
 
 
@@ -62,14 +65,14 @@ def fp32_sensitivity(P, U, t=0.0, vw=(0.0, 0.0), scale=None):
 
 
 def check_rhs(P, U, got, precision, t=0.0, vw=(0.0, 0.0), ref=None):
-    """Residual parity: the all-field bound and the per-field bound of the
-    precision; returns (all-field error, per-field errors, per-field bounds)."""
+    """Residual parity with the bounds of the precision; returns (all-field
+    error, per-field errors, per-field bounds)."""
     ref = P.rhs(U, t, vw) if ref is None else ref
     ea, ef = all_err(got, ref), field_err(got, ref)
     if precision == "fp64":
         bound = np.full(4, RHS_TOL_FIELD_FP64)
+        assert ea <= RHS_TOL_ALL_FP64, (ea, ef)
     else:
         bound = MIXED_SENS * fp32_sensitivity(P, U, t, vw)
-    assert ea <= RHS_TOL_ALL[precision], (ea, ef)
     assert np.all(ef <= bound), (ef, bound)
     return ea, ef, bound

@@ -35,8 +35,9 @@ def test_code_only_ignores_comments_and_spacing():
 
 @pytest.fixture
 def fake_root(tmp_path, monkeypatch):
-    """A copy of the tensor-core kernel's sources and a profile summary whose
-    hash line matches them."""
+    """A copy of the tensor-core kernel's sources and a traffic record whose
+    hash matches them."""
+    import json
     src = os.path.join(ROOT, "paper_2508_17917_gb300", "csrc")
     dst = tmp_path / "paper_2508_17917_gb300" / "csrc"
     dst.mkdir(parents=True)
@@ -45,8 +46,8 @@ def fake_root(tmp_path, monkeypatch):
     (tmp_path / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h = bench.kernel_hash(3)
-    (tmp_path / "profiles" / bench.PROFILE_OF_VARIANT[3]).write_text(
-        f"summary\n\ndram_bytes_per_dof_stage: 40.25 (kernel_hash {h})\n")
+    rec = {"3": {"kernel_hash": h, "dram_bytes_per_dof_stage": 40.25}}
+    (tmp_path / "profiles" / "stage_kernel_traffic.json").write_text(json.dumps(rec))
     return dst
 
 
@@ -61,7 +62,31 @@ def test_recorded_traffic_follows_the_kernel_source(fake_root):
     assert bench.recorded_traffic(3) is None
 
 
-def test_recorded_traffic_without_a_summary(fake_root):
-    os.remove(os.path.join(bench.ROOT, "profiles", bench.PROFILE_OF_VARIANT[3]))
+def test_record_traffic_from_ncu_csv(fake_root, tmp_path):
+    """An ncu raw-page CSV (header, units row, one row per launch) becomes a
+    record keyed by the kernel hash; units are honoured."""
+    import argparse
+    csv = tmp_path / "raw.csv"
+    csv.write_text(
+        '"ID","Kernel Name","dram__bytes_read.sum","dram__bytes_write.sum"\n'
+        '"","","Mbyte","Gbyte"\n'
+        '"0","void dg::make_shadow_kernel<4>(...)","1.0","1.0"\n'
+        '"1","void dg::stage_tc_kernel<4, false, false, false>(dg::StageParams, dg::Phys<float>)",'
+        '"600.5","0.75"\n')
+    assert bench.ncu_dram_bytes(str(csv), "stage_tc_kernel") == [600.5e6 + 0.75e9]
+    args = argparse.Namespace(variant=3, record_traffic=str(csv), record_k=1000)
+    bench.record_traffic(args)
+    per = (600.5e6 + 0.75e9) / (4 * 1000 * bench.NP)
+    assert abs(bench.recorded_traffic(3) - per) < 1e-9 * per
+
+
+def test_algorithmic_flops_per_dof_stage():
+    # by phase at p = 4 (per element): gradient 3960, volume flux 1440,
+    # divergence 3600, faces 3750, lift 1800, update 240 over 60 DOFs
+    assert abs(bench.algorithmic_flops_per_dof_stage(4) - 14790 / 60) < 1e-12
+
+
+def test_recorded_traffic_without_a_record(fake_root):
+    os.remove(os.path.join(bench.ROOT, "profiles", "stage_kernel_traffic.json"))
     assert bench.recorded_traffic(3) is None
     assert bench.recorded_traffic(7) is None

@@ -4,10 +4,9 @@ Same seeded inputs on both sides; tolerances (derived in tests/_parity.py):
 * FP64 path: residuals <= 1e-12 relative to the largest entry and <= 1e-11
   per field; state <= 1e-12 relative L2 per conserved field after 100 LSRK
   steps; increments U_n - U_0 <= 1e-9 per field;
-* mixed path (FP32 arithmetic, FP64 state / pressure / registers): residuals
-  <= 2e-5 relative to the largest entry and, per field, <= 10 x the change of
-  the oracle's own residual under FP32 rounding of its input; state <= 2e-5;
-  increments <= 5e-4 per field;
+* mixed path (FP32 arithmetic, FP64 state / pressure / registers): residuals,
+  per field, <= 10 x the change of the oracle's own residual under FP32
+  rounding of its input; state <= 2e-5; increments <= 5e-4 per field;
 * time step, wall forces (FP64 on both sides): <= 1e-12 relative.
 The increment checks are what a run that skipped its stage updates fails:
 over a few steps the state moves by far less than 2e-5 of itself.

@@ -4,7 +4,7 @@ oracle, which evaluates the same S by hyper-dual differentiation through the
 G blocks of Sec. 2.1.
 
 * residual with the source at a time t > 0 (the source moves with the
-  vortex), per field;
+  vortex), per field (tolerances of tests/_parity.py);
 * 100 LSRK steps with the source on the 16 x 16 p = 2 mesh, whole state and
   the increment U_n - U_0 per field;
 * the benchmark workload (128 x 128 quads, p = 4, K = 32,768) with the
@@ -16,13 +16,12 @@ import pytest
 import dg_inputs
 import oracle
 from dg_inputs.states import to_kcn
+from _parity import INC_TOL, STATE_TOL, check_rhs, rel_l2
 
 pytestmark = pytest.mark.gpu
 GAMMA, MACH = 1.4, 0.3
 U0 = MACH * np.sqrt(GAMMA)
 SRC = (5.0, 5.0, 5.0, 10.0, U0, 0.0)          # beta, x0, y0, L, u0, v0
-STATE_TOL = {"fp64": 1e-12, "mixed": 2e-5}
-INC_TOL = {"fp64": 1e-9, "mixed": 1e-3}
 
 
 @pytest.fixture(scope="module")
@@ -41,15 +40,6 @@ def stream():
     return torch.cuda.current_stream().cuda_stream
 
 
-def rel_l2(P, d, ref):
-    J, M = P.geo["J"], P.ops["M"]
-    return np.sqrt(np.einsum("k,kcn,nm,kcm->c", J, d, M, d) / np.einsum("k,kcn,nm,kcm->c", J, ref, M, ref))
-
-
-def field_err(got, ref):
-    return np.abs(got - ref).max(axis=(0, 2)) / np.abs(ref).max(axis=(0, 2))
-
-
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("p", [2, 4])
 def test_rhs_with_vortex_source(dg, p, precision):
@@ -63,10 +53,7 @@ def test_rhs_with_vortex_source(dg, p, precision):
     s.set_source(dg.DG_SOURCE_VORTEX, SRC)
     s.set_state(U)
     got = s.rhs(t)
-    # the exact vortex with its source: the residual is the advection
-    # -u0 dU/dx, so rho's residual has the size of the others
-    err = field_err(got, ref)
-    assert np.all(err <= (1e-12 if precision == "fp64" else 2e-5)), err
+    check_rhs(P, U, got, precision, t, (0.0, 0.0), ref)
     # the source itself is what moved the residual
     P0 = oracle.Problem(mesh, p, mu=mu)
     assert np.abs(ref - P0.rhs(U, t)).max() > 1e3 * np.abs(got - ref).max()

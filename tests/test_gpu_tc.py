@@ -2,11 +2,10 @@
 two elements, Dr / Ds / LIFT products as mma.sync TF32 with three products
 of split operands) against the oracle.
 
-Tolerances are those of the mixed path (tests/_parity.py): residuals 2e-5
-relative to the largest entry and, per field, 10 x the change of the
-oracle's residual under FP32 rounding of its input state (the floor of any
-path that reads an FP32 copy of the state), at every p; 2e-5 relative L2
-per field after 100 steps.  The split products are good to about 2^-21 of
+Tolerances are those of the mixed path (tests/_parity.py): residuals, per
+field, 10 x the change of the oracle's residual under FP32 rounding of its
+input state (the floor of any path that reads an FP32 copy of the state),
+at every p; 2e-5 relative L2 per field after 100 steps.  The split products are good to about 2^-21 of
 sum |A||B| and the operands are taken relative to the element's first node,
 so the contraction error stays below the FP32 rounding of the state that
 bounds the other mixed kernels."""

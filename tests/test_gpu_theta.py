@@ -3,9 +3,9 @@
 The kernel variant with the theta terms of Eq. dg_on_K against the oracle:
 residuals on the periodic square (p = 1..6) and on the O-grid with wall and
 far-field faces, and 50 LSRK steps of SIP.  Tolerances as for IIP
-(tests/_parity.py): residuals 1e-12 (FP64) and 2e-5 (mixed) relative to the
-largest entry, and per field 1e-11 (FP64) and 10 x the oracle's FP32 input
-sensitivity (mixed).
+(tests/_parity.py): residuals 1e-12 relative to the largest entry and 1e-11
+per field (FP64), and per field 10 x the oracle's FP32 input sensitivity
+(mixed).
 """
 import numpy as np
 import pytest

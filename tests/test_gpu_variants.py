@@ -2,9 +2,8 @@
 one node per thread (variant 1) and two volume nodes plus two face nodes of
 one face per thread (variant 2), forced through dg_set_stage_variant; and the
 first-step tuner's choice.  Tolerances as for the mixed path
-(tests/_parity.py): 2e-5 relative to the largest residual entry and, per
-field, 10 x the change of the oracle's residual under FP32 rounding of its
-input state, at every p."""
+(tests/_parity.py): residuals, per field, 10 x the change of the oracle's
+residual under FP32 rounding of its input state, at every p."""
 import numpy as np
 import pytest
 
