@@ -693,6 +693,82 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def strouhal(t, cl):
+    """Shedding frequency (D = |v_inf| = 1) from the upward zero crossings of
+    C_L - mean C_L; None with fewer than three crossings."""
+    import numpy as np
+    c = cl - cl.mean()
+    up = np.where((c[:-1] < 0) & (c[1:] >= 0))[0]
+    if len(up) < 3:
+        return None
+    tz = t[up] - c[up] * (t[up + 1] - t[up]) / (c[up + 1] - c[up])
+    return float((len(tz) - 1) / (tz[-1] - tz[0]))
+
+
+def run_config3(args):
+    """Config 3: the 120 x 170 seeded O-grid (K = 40,800), p = 4, Re = 100,
+    M = 0.2, from a smoothed free-stream start, `--config3-steps` steps of the
+    mixed path and of the FP64 path at one fixed step (CFL `--config3-cfl` of
+    the FP64 bound of the start state), C_L and C_D every 20 steps; prints
+    the statistics of both histories, their largest difference (C_L relative
+    to max |C_L|, C_D to mean C_D) and the wall times."""
+    import numpy as np
+    import torch
+    import dg_inputs
+    import paper_2508_17917_gb300 as dg
+    from dg_inputs.states import to_kcn
+    torch.cuda.set_device(0)
+    gamma, mach, re = 1.4, 0.2, 100.0
+    p_inf = 1.0 / (gamma * mach * mach)
+    kw = dict(mu=1.0 / re, rho_inf=1.0, u_inf=1.0, v_inf=0.0, p_inf=p_inf)
+    mesh = dg_inputs.ogrid_cylinder(120, 170, 0.5, 30.0, seed=0)
+    sh = torch.cuda.current_stream().cuda_stream
+    out, hists = {}, {}
+    every = 20
+    dt = None
+    for prec in ("mixed", "fp64"):
+        s = dg.Solver(mesh, 4, prec, stream=sh, **kw)
+        x, y = s.node_coords()
+        U = to_kcn(dg_inputs.free_stream(x.shape, rho=1.0, u=1.0, v=0.0, p=p_inf))
+        damp = np.tanh(4.0 * (np.hypot(x, y) - 0.5))
+        U[:, 1] *= damp
+        U[:, 3] = p_inf / (gamma - 1) + 0.5 * U[:, 1] ** 2 / U[:, 0]
+        s.set_state(dg_inputs.perturb(U, seed=0, amp=1e-3))
+        if dt is None:
+            s64 = dg.Solver(mesh, 4, "fp64", stream=sh, **kw)
+            s64.set_state(dg_inputs.perturb(U, seed=0, amp=1e-3))
+            dt = s64.dt(args.config3_cfl)
+            del s64
+        rows = [(0.0,) + tuple(s.wall_forces()[:2] / 0.5)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n = 0
+        while n < args.config3_steps:
+            k = min(every, args.config3_steps - n)
+            s.steps(n * dt, dt, k)
+            n += k
+            F = s.wall_forces()
+            rows.append((n * dt, F[0] / 0.5, F[1] / 0.5))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        h = np.array(rows)
+        hists[prec] = h
+        out[prec] = {"wall_s": wall, "ms_per_step_incl_forces": wall / args.config3_steps * 1e3,
+                     "mean_cd": float(h[:, 1].mean()), "cd_end": float(h[-1, 1]),
+                     "cl_amplitude": float(0.5 * np.ptp(h[:, 2])), "cl_end": float(h[-1, 2]),
+                     "strouhal": strouhal(h[:, 0], h[:, 2]), "finite": bool(s.check_finite())}
+        del s
+    a, b = hists["mixed"], hists["fp64"]
+    out["mixed_vs_fp64"] = {"cl": float(np.abs(a[:, 2] - b[:, 2]).max() / np.abs(b[:, 2]).max()),
+                            "cd": float(np.abs(a[:, 1] - b[:, 1]).max() / np.abs(b[:, 1]).mean())}
+    out.update(workload="config 3: O-grid 120x170 (K=40800), p=4, Re=100, M=0.2, smoothed free-stream start",
+               steps=args.config3_steps, dt=dt, t_end=dt * args.config3_steps, cfl=args.config3_cfl,
+               forces_every=every)
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    np.savez(os.path.join(ROOT, "gpurun_out", "config3_histories.npz"), mixed=a, fp64=b)
+    print(json.dumps(out))
+
+
 def run_profile(args):
     """A few steps of one workload, for ncu captures (no timing, no extras)."""
     import torch
@@ -759,6 +835,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3],
                     help="tile shape of the headline's mixed kernel (0: first-step tuner)")
+    ap.add_argument("--config3", action="store_true",
+                    help="long C_L / C_D histories of config 3 in both precisions (not the bench line)")
+    ap.add_argument("--config3-steps", type=int, default=20000)
+    ap.add_argument("--config3-cfl", type=float, default=2.0)
     ap.add_argument("--record-traffic", default=None, metavar="CSV",
                     help="ncu raw-page CSV of one stage launch: write its DRAM bytes per DOF-stage")
     ap.add_argument("--record-k", type=int, default=2 * 512 * 512,
@@ -768,6 +848,9 @@ def main():
     args = ap.parse_args()
     if args.record_traffic:
         record_traffic(args)
+        return
+    if args.config3:
+        run_config3(args)
         return
     if args.profile:
         run_profile(args)

@@ -308,27 +308,25 @@ __global__ void batch_record_kernel(const BatchCase *cases, int n, double *hist,
 //   S_rho = 0,   S_m = mu (4 - r^2) (du, dv),
 //   S_E = mu (4 - r^2)(u0 du + v0 dv)
 //         + mu beta^2 / (2 pi^2) exp(1 - r^2) (r^2 (2 - r^2) - (1 - r^2) / Pr).
-// One thread per node; `real` is the arithmetic (FP64 path: double; mixed:
-// float after the offset is formed in double).
+// One thread per node; (xc, yc) is the centre at the stage's time (host,
+// FP64); `real` is the arithmetic after the FP64 offsets (FP64 path: double;
+// mixed: float).  The constants come precomputed (VortexSource).
 template <typename real>
-__global__ void vortex_source_kernel(const double *xy, long long nn, int Np, VortexSource v, double t,
-                                     double *S)
+__global__ void vortex_source_kernel(const double *xy, long long nn, int Np, VortexSource v, double xc,
+                                     double yc, double *S)
 {
     const long long n = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
     if (n >= nn) return;
-    double ddx = xy[n] - (v.x0 + v.u0 * t);
-    double ddy = xy[nn + n] - (v.y0 + v.v0 * t);
-    ddx -= v.L * rint(ddx / v.L);
-    ddy -= v.L * rint(ddy / v.L);
-    const real dx = real(ddx), dy = real(ddy);
+    real dx = real(xy[n] - xc), dy = real(xy[nn + n] - yc);
+    dx -= real(v.L) * rint(dx * real(v.invL));
+    dy -= real(v.L) * rint(dy * real(v.invL));
     const real r2 = dx * dx + dy * dy;
     const real e1 = exp(real(1) - r2);
-    const real f = real(v.beta / (2.0 * 3.14159265358979323846)) * sqrt(e1);
+    const real f = real(v.f0) * sqrt(e1);
     const real du = -f * dy, dv = f * dx;
     const real mu = real(v.mu), w = mu * (real(4) - r2);
-    const real c = real(v.beta * v.beta / (2.0 * 3.14159265358979323846 * 3.14159265358979323846));
     const real sE = w * (real(v.u0) * du + real(v.v0) * dv) +
-                    mu * c * e1 * (r2 * (real(2) - r2) - (real(1) - r2) / real(v.Pr));
+                    mu * real(v.c2) * e1 * (r2 * (real(2) - r2) - (real(1) - r2) * real(v.invPr));
     const long long k = n / Np;
     const int i = static_cast<int>(n - k * Np);
     double *o = S + k * 4 * Np + i;
@@ -344,10 +342,11 @@ cudaError_t launch_vortex_source(bool fp64, const double *xy, long long nn, int 
                                  double t, double *S, cudaStream_t st)
 {
     const unsigned blocks = static_cast<unsigned>((nn + 255) / 256);
+    const double xc = v.x0 + v.u0 * t, yc = v.y0 + v.v0 * t;
     if (fp64)
-        vortex_source_kernel<double><<<blocks, 256, 0, st>>>(xy, nn, Np, v, t, S);
+        vortex_source_kernel<double><<<blocks, 256, 0, st>>>(xy, nn, Np, v, xc, yc, S);
     else
-        vortex_source_kernel<float><<<blocks, 256, 0, st>>>(xy, nn, Np, v, t, S);
+        vortex_source_kernel<float><<<blocks, 256, 0, st>>>(xy, nn, Np, v, xc, yc, S);
     return cudaGetLastError();
 }
 

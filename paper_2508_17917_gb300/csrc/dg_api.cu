@@ -551,8 +551,10 @@ dg_status dg_set_source(dg_ctx *c, int kind, const double *params)
         for (int q = 0; q < 6; ++q)
             if (!std::isfinite(params[q])) return fail(c, DG_EINVAL, "vortex source parameters must be finite");
         if (!(params[3] > 0.0)) return fail(c, DG_EINVAL, "vortex source period L must be > 0");
+        const double pi = 3.14159265358979323846;
         c->vortex = dg::VortexSource{params[0], params[1], params[2], params[3], params[4], params[5],
-                                     c->prm.mu, c->prm.Pr};
+                                     c->prm.mu, c->prm.Pr, 1.0 / params[3], params[0] / (2.0 * pi),
+                                     params[0] * params[0] / (2.0 * pi * pi), 1.0 / c->prm.Pr};
         DG_CUDA(c, c->src_xy.alloc(2 * x.size()));
         DG_CUDA(c, cudaMemcpy(c->src_xy.ptr, x.data(), x.size() * sizeof(double), cudaMemcpyHostToDevice));
         DG_CUDA(c, cudaMemcpy(c->src_xy.ptr + x.size(), y.data(), y.size() * sizeof(double),

@@ -145,6 +145,7 @@ cudaError_t launch_nonfinite(const double *x, long long n, int *flag, cudaStream
 struct VortexSource {
     double beta, x0, y0, L, u0, v0;   // strength, centre at t = 0, period, advection velocity
     double mu, Pr;
+    double invL, f0, c2, invPr;       // 1/L, beta/(2 pi), beta^2/(2 pi^2), 1/Pr
 };
 // S[K][4][Np] at time t from node coordinates xy = (x[K*Np], y[K*Np]);
 // fp64: double arithmetic, else float after the offsets

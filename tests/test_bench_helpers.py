@@ -90,3 +90,12 @@ def test_recorded_traffic_without_a_record(fake_root):
     os.remove(os.path.join(bench.ROOT, "profiles", "stage_kernel_traffic.json"))
     assert bench.recorded_traffic(3) is None
     assert bench.recorded_traffic(7) is None
+
+
+def test_strouhal_from_zero_crossings():
+    import numpy as np
+    t = np.linspace(0.0, 40.0, 8001)
+    cl = 0.3 * np.sin(2 * np.pi * 0.165 * t + 0.4) + 0.02
+    assert abs(bench.strouhal(t, cl) - 0.165) < 1e-6
+    # fewer than three crossings: no frequency
+    assert bench.strouhal(t[:600], cl[:600]) is None

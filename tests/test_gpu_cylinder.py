@@ -156,3 +156,54 @@ def test_viv_coupled_loop(dg, precision):
     y_err = np.abs(traj_g[:, 0] - traj_o[:, 0]).max() / np.abs(traj_o[:, 0]).max()
     cl_err = np.abs(traj_g[:, 1] - traj_o[:, 1]).max() / np.abs(traj_o[:, 1]).max()
     assert y_err <= TOL[precision] and cl_err <= TOL[precision], (y_err, cl_err)
+
+
+def force_history(run_steps, wall_forces, nwin, every):
+    rows = []
+    for _ in range(nwin // every):
+        run_steps(every)
+        F = wall_forces()
+        rows.append((F[0] / QINF, F[1] / QINF))
+    return np.array(rows)
+
+
+def test_config3_cl_cd_windows(dg):
+    """Config 3 (120 x 170 O-grid, K = 40,800, p = 4, Re = 100, M = 0.2):
+    the mixed path runs 1,000 steps from the seeded start; from its states
+    at steps 0, 500 and 1,000 (saved, common to all three runs) the oracle,
+    the FP64 path and the mixed path each run a window of 200 steps; their
+    C_L, C_D histories (every 10 steps) agree to 1e-4 (C_L relative to
+    max |C_L| over the window, C_D to its mean).  Steps at CFL 2 (the time-step
+    bound is 4-7 times the operator's spectral radius, so this is about 1/6
+    of the five-stage scheme's stability edge), so that lift and drag move by
+    much more than the tolerance over a window."""
+    cfl = 2.0
+    f = full_mesh()
+    P, mesh = f["P"], f["mesh"]
+    U0 = start_state(P, seed=3, cross=0.05)
+    lead = dg.Solver(mesh, 4, "mixed", stream=stream(), **KW)
+    lead.set_state(U0)
+    dt_lead = lead.dt(cfl)
+    saved = [U0]
+    for _ in range(2):
+        lead.steps(0.0, dt_lead, 500)
+        saved.append(lead.get_state())
+    nwin, every = 200, 10
+    runs = {prec: dg.Solver(mesh, 4, prec, stream=stream(), **KW) for prec in ("fp64", "mixed")}
+    for Us in saved:
+        dt, _ = P.dt(Us, cfl)
+        Uo = [Us.copy()]
+
+        def oracle_steps(n):
+            Uo[0] = P.run(Uo[0], 0.0, dt, n)
+
+        ref = force_history(oracle_steps, lambda: P.wall_forces(Uo[0]), nwin, every)
+        for prec, s in runs.items():
+            s.set_state(Us)
+            got = force_history(lambda n: s.steps(0.0, dt, n), s.wall_forces, nwin, every)
+            e_cl, e_cd = history_errors(ref, got)
+            assert e_cl <= TOL["mixed"] and e_cd <= TOL["mixed"], (prec, e_cl, e_cd)
+        # the window is not empty: lift and drag move over it by far more
+        # than the tolerance, so a stale state would fail
+        assert np.ptp(ref[:, 1]) > 1e-2 * np.abs(ref[:, 1]).max(), ref[:, 1]
+        assert np.ptp(ref[:, 0]) > 1e-3 * np.abs(ref[:, 0]).mean(), ref[:, 0]
