@@ -114,17 +114,14 @@ __global__ void max_reduce_kernel(const double *x, long long n, double *out)
     if (threadIdx.x == 0) *out = s[0];
 }
 
-// One thread per wall face: traction p n - tau n at the face nodes (interior
-// trace, n the element's outward normal), integrated with the LGL weights
-// scaled by sJ; moment about (xc, yc).
-__global__ void wall_force_kernel(AuxMesh m, Phys<double> ph, const int2 *faces, const double *face_xy,
-                                  const double *wface, int nwall, double xc, double yc, double *partial)
+// Force and moment of one wall face: traction p n - tau n at its face nodes
+// (interior trace, n the element's outward normal), integrated with the LGL
+// weights scaled by sJ; moment about (xc, yc).  xy: the face nodes'
+// coordinates (x, y interleaved).
+__device__ void wall_face_force(const AuxMesh &m, Phys<double> ph, long long k, int f, const double *xy,
+                                const double *wface, double xc, double yc, double out[3])
 {
-    int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= nwall) return;
     const int p = m.p, Np = (p + 1) * (p + 2) / 2, Nfp = p + 1;
-    const long long k = faces[w].x;
-    const int f = faces[w].y;
     if (m.elem_case) ph.mu = m.cases[m.elem_case[k]].mu;
     const double *g = m.geo + k * 16;
     const double rx = g[G_RX], ry = g[G_RY], sx = g[G_SX], sy = g[G_SY];
@@ -152,16 +149,42 @@ __global__ void wall_force_kernel(AuxMesh m, Phys<double> ph, const int2 *faces,
         double pr = pressure<double>(u, u[3], ph.gm1);
         double tx = pr * n1 - (vx[1] * n1 + vy[1] * n2);
         double ty = pr * n2 - (vx[2] * n1 + vy[2] * n2);
-        double x = face_xy[(static_cast<long long>(w) * Nfp + i) * 2] - xc;
-        double y = face_xy[(static_cast<long long>(w) * Nfp + i) * 2 + 1] - yc;
+        double x = xy[2 * i] - xc;
+        double y = xy[2 * i + 1] - yc;
         double wq = sJ * wface[i];
         F0 += wq * tx;
         F1 += wq * ty;
         Mz += wq * (x * ty - y * tx);
     }
-    partial[w * 3 + 0] = F0;
-    partial[w * 3 + 1] = F1;
-    partial[w * 3 + 2] = Mz;
+    out[0] = F0;
+    out[1] = F1;
+    out[2] = Mz;
+}
+
+// One thread per wall face of one mesh: partial[w] = (Fx, Fy, Mz) of face w.
+__global__ void wall_force_kernel(AuxMesh m, Phys<double> ph, const int2 *faces, const double *face_xy,
+                                  const double *wface, int nwall, double xc, double yc, double *partial)
+{
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwall) return;
+    const int Nfp = m.p + 1;
+    wall_face_force(m, ph, faces[w].x, faces[w].y, face_xy + static_cast<long long>(w) * Nfp * 2, wface, xc, yc,
+                    partial + w * 3);
+}
+
+// One thread per wall face of every degree group of a batch: the groups'
+// faces are numbered consecutively (group g from wg.g[g].base), and face w
+// writes partial[w].
+__global__ void batch_wall_force_kernel(WallGroups wg, Phys<double> ph, double *partial)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= wg.total) return;
+    int gi = 0;
+    while (gi + 1 < wg.n && w >= wg.g[gi + 1].base) ++gi;
+    const WallGroup &G = wg.g[gi];
+    const int i = w - G.base, Nfp = G.m.p + 1;
+    wall_face_force(G.m, ph, G.faces[i].x, G.faces[i].y, G.face_xy + static_cast<long long>(i) * Nfp * 2,
+                    G.wface, 0.0, 0.0, partial + static_cast<long long>(w) * 3);
 }
 
 // Deterministic single-block sum of n triples.
@@ -197,9 +220,11 @@ __global__ void nonfinite_kernel(const double *x, long long n, int *flag)
 // dt = cfl / max (Eq. rayleigh_bound), or the case's entry of `fixed` when
 // the caller fixed the steps (the bound is still evaluated and recorded); a
 // bound that is not finite freezes the case (dt = 0, bad = 1) instead of
-// spreading NaN.
-__global__ void batch_dt_kernel(const double *lam, const long long *seg, BatchCase *cases, double cfl,
-                                const double *fixed)
+// spreading NaN.  Thread 0 then takes the case's Newmark step with the lift
+// of the previous force evaluation (Algorithm 3: F_r = lift / m), giving v_b
+// for the coming RK step.
+__global__ void batch_dt_newmark_kernel(const double *lam, const long long *seg, BatchCase *cases, double cfl,
+                                        const double *fixed)
 {
     __shared__ double s[256];
     const int i = blockIdx.x;
@@ -220,30 +245,17 @@ __global__ void batch_dt_kernel(const double *lam, const long long *seg, BatchCa
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        BatchCase &cs = cases[i];
-        const double l = s[0];
-        cs.lam = l;
-        if (cs.bad || !isfinite(l) || !(l > 0.0)) {
-            cs.bad = 1;
-            cs.dt = 0.0;
-        } else {
-            cs.dt = fixed ? fixed[i] : cfl / l;
-        }
-    }
-}
-
-// One thread per case: Newmark step with the lift of the previous force
-// evaluation (Algorithm 3: F_r = lift / m), v_b for the coming RK step.
-__global__ void batch_newmark_kernel(BatchCase *cases, int n)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (threadIdx.x != 0) return;
     BatchCase &cs = cases[i];
-    if (cs.bad) {
+    const double l = s[0];
+    cs.lam = l;
+    if (cs.bad || !isfinite(l) || !(l > 0.0)) {
+        cs.bad = 1;
+        cs.dt = 0.0;
         cs.vb = 0.0;
         return;
     }
+    cs.dt = fixed ? fixed[i] : cfl / l;
     double y = cs.y, yd = cs.yd, ydd = cs.ydd, vb = 0.0;
     if (newmark_step(cs.Mr, cs.Cr, cs.Kr, cs.Fy / cs.mass, cs.dt, y, yd, ydd, vb)) {
         cs.y = y;
@@ -257,11 +269,16 @@ __global__ void batch_newmark_kernel(BatchCase *cases, int n)
     }
 }
 
-// One block per case: deterministic tree sum of its wall-face partials.
-__global__ void batch_forces_kernel(const double *partial, const int *wseg, BatchCase *cases)
+// One block per case: deterministic tree sum of its wall-face partials into
+// the case's (Fx, Fy, Mz); with a history, row *counter of hist gets
+// (t, dt, y, y', v_b, Fx, Fy, lam) of the case (rows beyond cap are dropped).
+// The last block to finish (ticket) advances the row counter once every
+// block has read it.
+__global__ void batch_forces_record_kernel(const double *partial, const int *wseg, BatchCase *cases,
+                                           double *hist, int cap, int *counter, unsigned *ticket)
 {
     __shared__ double s[3][256];
-    const int i = blockIdx.x;
+    const int i = blockIdx.x, n = gridDim.x;
     const int b = wseg[2 * i], e = wseg[2 * i + 1];
     double a[3] = {0, 0, 0};
     for (int w = b + threadIdx.x; w < e; w += blockDim.x)
@@ -273,28 +290,23 @@ __global__ void batch_forces_kernel(const double *partial, const int *wseg, Batc
             for (int c = 0; c < 3; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        cases[i].Fx = s[0][0];
-        cases[i].Fy = s[1][0];
-        cases[i].Mz = s[2][0];
-    }
-}
-
-// One block: row *counter of hist gets (t, dt, y, y', v_b, Fx, Fy, lam) of
-// every case; rows beyond cap are dropped; the counter always advances.
-__global__ void batch_record_kernel(const BatchCase *cases, int n, double *hist, int cap, int *counter)
-{
+    if (threadIdx.x != 0) return;
+    BatchCase &cs = cases[i];
+    cs.Fx = s[0][0];
+    cs.Fy = s[1][0];
+    cs.Mz = s[2][0];
+    if (!hist) return;
     const int row = *counter;
-    __syncthreads();
-    if (row < cap)
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const BatchCase &cs = cases[i];
-            double *h = hist + (static_cast<long long>(row) * n + i) * 8;
-            h[0] = cs.t; h[1] = cs.dt; h[2] = cs.y; h[3] = cs.yd;
-            h[4] = cs.vb; h[5] = cs.Fx; h[6] = cs.Fy; h[7] = cs.lam;
-        }
-    __syncthreads();
-    if (threadIdx.x == 0) *counter = row + 1;
+    if (row < cap) {
+        double *h = hist + (static_cast<long long>(row) * n + i) * 8;
+        h[0] = cs.t; h[1] = cs.dt; h[2] = cs.y; h[3] = cs.yd;
+        h[4] = cs.vb; h[5] = cs.Fx; h[6] = cs.Fy; h[7] = cs.lam;
+    }
+    __threadfence();
+    if (atomicAdd(ticket, 1u) == static_cast<unsigned>(n - 1)) {
+        *ticket = 0u;
+        *counter = row + 1;
+    }
 }
 
 // Viscous source of the advected isentropic vortex, S = -div F_v(U_v), in
@@ -350,30 +362,25 @@ cudaError_t launch_vortex_source(bool fp64, const double *xy, long long nn, int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_dt(const double *lam, const long long *seg, BatchCase *cases, int ncases, double cfl,
-                            const double *fixed, cudaStream_t st)
+cudaError_t launch_batch_dt_newmark(const double *lam, const long long *seg, BatchCase *cases, int ncases,
+                                    double cfl, const double *fixed, cudaStream_t st)
 {
-    batch_dt_kernel<<<ncases, 256, 0, st>>>(lam, seg, cases, cfl, fixed);
+    batch_dt_newmark_kernel<<<ncases, 256, 0, st>>>(lam, seg, cases, cfl, fixed);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_newmark(BatchCase *cases, int ncases, cudaStream_t st)
+cudaError_t launch_batch_wall_forces(const WallGroups &wg, const Phys<double> &ph, double *partial,
+                                     cudaStream_t st)
 {
-    batch_newmark_kernel<<<(ncases + 127) / 128, 128, 0, st>>>(cases, ncases);
+    if (wg.total < 1) return cudaSuccess;
+    batch_wall_force_kernel<<<(wg.total + 127) / 128, 128, 0, st>>>(wg, ph, partial);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_forces(const double *partial, const int *wseg, BatchCase *cases, int ncases,
-                                cudaStream_t st)
+cudaError_t launch_batch_forces_record(const double *partial, const int *wseg, BatchCase *cases, int ncases,
+                                       double *hist, int cap, int *counter, unsigned *ticket, cudaStream_t st)
 {
-    batch_forces_kernel<<<ncases, 256, 0, st>>>(partial, wseg, cases);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_batch_record(const BatchCase *cases, int ncases, double *hist, int cap, int *counter,
-                                cudaStream_t st)
-{
-    batch_record_kernel<<<1, 256, 0, st>>>(cases, ncases, hist, cap, counter);
+    batch_forces_record_kernel<<<ncases, 256, 0, st>>>(partial, wseg, cases, hist, cap, counter, ticket);
     return cudaGetLastError();
 }
 

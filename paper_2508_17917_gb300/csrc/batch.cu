@@ -78,6 +78,7 @@ struct dg_batch {
     bool use_fixed = false;
     DevBuf<long long> seg;
     DevBuf<int> wseg, counter;
+    DevBuf<unsigned> ticket;         // blocks done in the force-sum kernel (advances the history row)
     bool cur_is_a = true;
     bool forces_stale = true;
     int variant_req = 0;             // 0: tuned per degree group on the first run; 1, 2: forced
@@ -166,18 +167,31 @@ dg::AuxMesh aux_of(const dg_batch *b, const Group &g)
     return m;
 }
 
-// wall forces of every case into cases[].Fx, Fy, Mz
-dg_status enqueue_forces(dg_batch *b)
+// wall forces of every case into cases[].Fx, Fy, Mz (and, with a history,
+// the step's record): one launch over the wall faces of every degree group,
+// one block per case for the sums
+dg_status enqueue_forces(dg_batch *b, double *hist = nullptr, int rows = 0)
 {
     const dg::Phys<double> ph = phys_of<double>(b->prm);
+    dg::WallGroups wg;
     for (auto &g : b->groups) {
         if (g.nwall == 0) continue;
-        B_CUDA(b, dg::launch_wall_force_faces(aux_of(b, g), ph, g.walls.ptr, g.fxy.ptr, g.wface.ptr, g.nwall, 0.0,
-                                              0.0, b->fpart.ptr + static_cast<size_t>(g.wall_base) * 3, b->stream));
+        dg::WallGroup &w = wg.g[wg.n++];
+        w.m = aux_of(b, g);
+        w.faces = g.walls.ptr;
+        w.face_xy = g.fxy.ptr;
+        w.wface = g.wface.ptr;
+        w.base = g.wall_base;
+        w.nwall = g.nwall;
+        wg.total = g.wall_base + g.nwall;
+    }
+    if (wg.total > 0) {
+        B_CUDA(b, dg::launch_batch_wall_forces(wg, ph, b->fpart.ptr, b->stream));
         b->launches += 1;
     }
-    B_CUDA(b, dg::launch_batch_forces(b->fpart.ptr, b->wseg.ptr, b->dcases.ptr, static_cast<int>(b->cases.size()),
-                                      b->stream));
+    B_CUDA(b, dg::launch_batch_forces_record(b->fpart.ptr, b->wseg.ptr, b->dcases.ptr,
+                                             static_cast<int>(b->cases.size()), hist, rows, b->counter.ptr,
+                                             b->ticket.ptr, b->stream));
     b->launches += 1;
     return DG_OK;
 }
@@ -188,18 +202,30 @@ dg_status enqueue_step(dg_batch *b, double cfl, double *hist, int rows)
     const int n = static_cast<int>(b->cases.size());
     const double sf = sigma_factor(b->prm);
     const dg::Phys<float> ph32 = phys_of<float>(b->prm);
+    // FP32 bound from the FP32 state copy, a stability estimate recomputed
+    // every step: one launch for all degree groups
+    dg::DtGroups dgs{};
     for (auto &g : b->groups) {
-        // FP32 bound from the FP32 state copy: a stability estimate recomputed every step
         const bool a = b->cur_is_a;
-        B_CUDA(b, dg::launch_dt_lambda_mixed(g.p, a ? g.S0a.ptr : g.S0b.ptr, a ? g.P0a.ptr : g.P0b.ptr, g.geo32.ptr,
-                                             g.conn.ptr, g.fmask.ptr, g.tiles.ptr, g.ntiles, b->dcases.ptr, g.K,
-                                             ph32, static_cast<float>(sf), b->lam.ptr + g.lam_base, b->stream));
-        b->launches += 1;
+        dg::DtGroup &d = dgs.g[dgs.n++];
+        d.S = a ? g.S0a.ptr : g.S0b.ptr;
+        d.Pr = a ? g.P0a.ptr : g.P0b.ptr;
+        d.geo = g.geo32.ptr;
+        d.conn = g.conn.ptr;
+        d.fmask = g.fmask.ptr;
+        d.tiles = g.tiles.ptr;
+        d.K = g.K;
+        d.ntiles = g.ntiles;
+        d.first_block = dgs.blocks;
+        d.lam = b->lam.ptr + g.lam_base;
+        d.p = g.p;
+        dgs.blocks += g.ntiles;
     }
-    B_CUDA(b, dg::launch_batch_dt(b->lam.ptr, b->seg.ptr, b->dcases.ptr, n, cfl,
-                                  b->use_fixed ? b->fixed_dt.ptr : nullptr, b->stream));
-    B_CUDA(b, dg::launch_batch_newmark(b->dcases.ptr, n, b->stream));
-    b->launches += 2;
+    B_CUDA(b, dg::launch_dt_lambda_mixed_multi(dgs, b->dcases.ptr, ph32, static_cast<float>(sf), b->stream));
+    b->launches += 1;
+    B_CUDA(b, dg::launch_batch_dt_newmark(b->lam.ptr, b->seg.ptr, b->dcases.ptr, n, cfl,
+                                          b->use_fixed ? b->fixed_dt.ptr : nullptr, b->stream));
+    b->launches += 1;
     for (int s = 0; s < (b->fused ? 1 : 5); ++s) {
         for (auto &g : b->groups) {
             dg::StageParams sp{};
@@ -265,13 +291,7 @@ dg_status enqueue_step(dg_batch *b, double cfl, double *hist, int rows)
         }
         b->cur_is_a = !b->cur_is_a;
     }
-    dg_status st = enqueue_forces(b);
-    if (st != DG_OK) return st;
-    if (hist) {
-        B_CUDA(b, dg::launch_batch_record(b->dcases.ptr, n, hist, rows, b->counter.ptr, b->stream));
-        b->launches += 1;
-    }
-    return DG_OK;
+    return enqueue_forces(b, hist, rows);
 }
 
 // First run: per degree group, time every available stage-kernel shape on
@@ -557,6 +577,8 @@ dg_status dg_batch_create(const dg_params *common, int ncases, const dg_case *ca
     chk(b->seg.alloc(seg.size()));
     chk(b->wseg.alloc(wseg.size()));
     chk(b->counter.alloc(1));
+    chk(b->ticket.alloc(1));
+    chk(cudaMemset(b->ticket.ptr, 0, sizeof(unsigned)));
     if (e != cudaSuccess) return bail(DG_ECUDA);
     chk(cudaMemcpy(b->dcases.ptr, b->init.data(), ncases * sizeof(dg::BatchCase), cudaMemcpyHostToDevice));
     chk(cudaMemcpy(b->seg.ptr, seg.data(), seg.size() * sizeof(long long), cudaMemcpyHostToDevice));
@@ -761,8 +783,11 @@ dg_status dg_batch_run(dg_batch *b, double cfl, int nsteps, int use_graph, doubl
                 if (e != cudaSuccess) return bcuda(b, e, "cudaGraphInstantiate");
                 // kernels per replay: dt per group, dt reduce, Newmark, 5 stages per group,
                 // forces per group with walls, force sum, record
-                int64_t per = static_cast<int64_t>(b->groups.size()) * (b->fused ? 2 : 6) + 3 + (hist ? 1 : 0);
-                for (auto &g : b->groups) per += (g.nwall > 0) ? 1 : 0;
+                // time-step bounds of all groups, dt + Newmark, the stage launches
+                // per group, wall forces of all groups, force sums (+ history)
+                bool walls = false;
+                for (auto &g : b->groups) walls |= g.nwall > 0;
+                int64_t per = 1 + 1 + static_cast<int64_t>(b->groups.size()) * (b->fused ? 1 : 5) + (walls ? 1 : 0) + 1;
                 b->graph_launches = per;
             }
             B_CUDA(b, cudaGraphLaunch(b->graph[which], b->stream));

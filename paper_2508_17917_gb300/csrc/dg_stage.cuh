@@ -46,6 +46,26 @@ struct BatchCase {
     int pad;
 };
 
+// Time-step bound of a batch: one degree group's inputs (FP32 state copy,
+// pressures, geometry, connectivity, face table, tile table) and where its
+// Lambda_K go; first_block is the group's first block of the launch.
+struct DtGroup {
+    const float4 *S;
+    const float *Pr;
+    const float *geo;
+    const int4 *conn;
+    const int *fmask;
+    const int4 *tiles;
+    long long K, ntiles, first_block;
+    double *lam;
+    int p;
+};
+struct DtGroups {
+    DtGroup g[8];
+    int n;
+    long long blocks;
+};
+
 struct StageParams {
     const double *K0in;
     double *K0out;

@@ -559,10 +559,10 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
 // the elements and the case (mu, v_b); otherwise tiles are E consecutive
 // elements and ph holds mu and v_w.
 template <int P>
-__global__ void __launch_bounds__(Shape<P>::NT)
-dt_lambda_mixed_kernel(const float4 *S, const float *Pr, const float *geo, const int4 *conn, const int *fmask,
-                       const int4 *tiles, const BatchCase *cases, long long K, Phys<float> ph, float sig_fac,
-                       double *lam)
+__device__ __forceinline__ void dt_lambda_mixed_tile(const float4 *S, const float *Pr, const float *geo,
+                                                     const int4 *conn, const int *fmask, const int4 *tiles,
+                                                     const BatchCase *cases, long long K, Phys<float> ph,
+                                                     float sig_fac, double *lam, long long blk)
 {
     using Sh = Shape<P>;
     constexpr int Np = Sh::Np, Nfp = Sh::Nfp, NF = Sh::NF, E = Sh::E, NT = Sh::NT;
@@ -573,10 +573,10 @@ dt_lambda_mixed_kernel(const float4 *S, const float *Pr, const float *geo, const
     __shared__ int sFm[NF];
     const int tid = threadIdx.x;
     for (int i = tid; i < NF; i += NT) sFm[i] = fmask[i];
-    long long k0 = static_cast<long long>(blockIdx.x) * E;
+    long long k0 = blk * E;
     int ne = static_cast<int>((K - k0) < E ? (K - k0) : E);
     if (tiles) {
-        const int4 td = tiles[blockIdx.x];
+        const int4 td = tiles[blk];
         k0 = td.x;
         ne = td.y;
         ph.mu = static_cast<float>(cases[td.z].mu);
@@ -657,6 +657,31 @@ dt_lambda_mixed_kernel(const float4 *S, const float *Pr, const float *geo, const
         const float cinv2 = p4 / (rhoK * rhoK);
         lam[k] = cvt_f2d(1.5f * cinv2 * GK + 3.0f * ciK * (3.0f * sigK + beta));
     }
+}
+
+template <int P>
+__global__ void __launch_bounds__(Shape<P>::NT)
+dt_lambda_mixed_kernel(const float4 *S, const float *Pr, const float *geo, const int4 *conn, const int *fmask,
+                       const int4 *tiles, const BatchCase *cases, long long K, Phys<float> ph, float sig_fac,
+                       double *lam)
+{
+    dt_lambda_mixed_tile<P>(S, Pr, geo, conn, fmask, tiles, cases, K, ph, sig_fac, lam, blockIdx.x);
+}
+
+// The time-step bound of every degree group of a batch in one launch: block
+// b works on tile b - first_block of the group whose block range holds b.
+template <int... Ps>
+__global__ void __launch_bounds__(256) dt_lambda_mixed_multi_kernel(DtGroups dgs, const BatchCase *cases,
+                                                                   Phys<float> ph, float sig_fac)
+{
+    int gi = 0;
+    while (gi + 1 < dgs.n && static_cast<long long>(blockIdx.x) >= dgs.g[gi + 1].first_block) ++gi;
+    const DtGroup &G = dgs.g[gi];
+    const long long blk = blockIdx.x - G.first_block;
+    // exactly one case runs: the group's degree
+    ((G.p == Ps ? dt_lambda_mixed_tile<Ps>(G.S, G.Pr, G.geo, G.conn, G.fmask, G.tiles, cases, G.K, ph, sig_fac,
+                                           G.lam, blk)
+                : void()), ...);
 }
 
 // FP32 copy and FP64-recovered pressure of a state (used when the state is

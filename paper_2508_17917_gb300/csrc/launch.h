@@ -58,6 +58,9 @@ cudaError_t launch_stage_mixed_batch(int p, const LaunchShape &ls, const StagePa
 // Lambda_K in FP32 from the FP32 state copy (mixed path); tiles == nullptr:
 // K elements in tiles of E, ph carries mu and v_w; otherwise the batch tile
 // table and per-case mu, v_b
+// Lambda_K of every degree group of a batch in one launch (one block per tile)
+cudaError_t launch_dt_lambda_mixed_multi(const DtGroups &dgs, const BatchCase *cases, const Phys<float> &ph,
+                                         float sig_fac, cudaStream_t st);
 cudaError_t launch_dt_lambda_mixed(int p, const float4 *S, const float *Pr, const float *geo, const int4 *conn,
                                    const int *fmask, const int4 *tiles, long long ntiles, const BatchCase *cases,
                                    long long K, const Phys<float> &ph, float sig_fac, double *lam, cudaStream_t st);
@@ -126,17 +129,30 @@ cudaError_t launch_sum3(const double *partial, int n, double *out, cudaStream_t 
 
 // batch: one block per case, max of lam over the case's element range
 // [seg[2i], seg[2i+1]) -> cases[i].lam and dt = cfl / lam, or fixed[i] when
-// fixed is not null (0 and bad = 1 if the bound is not finite)
-cudaError_t launch_batch_dt(const double *lam, const long long *seg, BatchCase *cases, int ncases, double cfl,
-                            const double *fixed, cudaStream_t st);
-// batch: Newmark step of every case with its lagged lift and its dt; sets v_b, advances t
-cudaError_t launch_batch_newmark(BatchCase *cases, int ncases, cudaStream_t st);
-// batch: one block per case, sum of the wall-face partials [wseg[2i], wseg[2i+1]) -> Fx, Fy, Mz
-cudaError_t launch_batch_forces(const double *partial, const int *wseg, BatchCase *cases, int ncases,
-                                cudaStream_t st);
-// batch: append (t, dt, y, y', v_b, Fx, Fy, lam) of every case to hist at row *counter, then ++*counter
-cudaError_t launch_batch_record(const BatchCase *cases, int ncases, double *hist, int cap, int *counter,
-                                cudaStream_t st);
+// fixed is not null (0 and bad = 1 if the bound is not finite); then the
+// case's Newmark step with its lagged lift: sets v_b, advances t
+cudaError_t launch_batch_dt_newmark(const double *lam, const long long *seg, BatchCase *cases, int ncases,
+                                    double cfl, const double *fixed, cudaStream_t st);
+// batch: the wall faces of every degree group in one launch (group g's faces
+// numbered from g.base); partial[w] = (Fx, Fy, Mz) of face w, moment about 0
+struct WallGroup {
+    AuxMesh m;
+    const int2 *faces;        // (element, face) of the group's wall faces
+    const double *face_xy;    // their face nodes' coordinates, [nwall][Nfp][2]
+    const double *wface;      // LGL weights [Nfp]
+    int base, nwall;
+};
+struct WallGroups {
+    WallGroup g[8];
+    int n = 0, total = 0;
+};
+cudaError_t launch_batch_wall_forces(const WallGroups &wg, const Phys<double> &ph, double *partial,
+                                     cudaStream_t st);
+// batch: one block per case, sum of the wall-face partials [wseg[2i], wseg[2i+1]) -> Fx, Fy, Mz, and
+// with hist: (t, dt, y, y', v_b, Fx, Fy, lam) of every case at row *counter, then ++*counter
+// (ticket: a zeroed counter of finished blocks)
+cudaError_t launch_batch_forces_record(const double *partial, const int *wseg, BatchCase *cases, int ncases,
+                                       double *hist, int cap, int *counter, unsigned *ticket, cudaStream_t st);
 
 // *flag = 1 if any of x[0..n) is not finite (flag must be zeroed first)
 cudaError_t launch_nonfinite(const double *x, long long n, int *flag, cudaStream_t st);

@@ -237,6 +237,15 @@ cudaError_t dt_mixed_p(const float4 *S, const float *Pr, const float *geo, const
     return cudaGetLastError();
 }
 
+cudaError_t launch_dt_lambda_mixed_multi(const DtGroups &dgs, const BatchCase *cases, const Phys<float> &ph,
+                                         float sig_fac, cudaStream_t st)
+{
+    if (dgs.blocks < 1) return cudaSuccess;
+    dt_lambda_mixed_multi_kernel<1, 2, 3, 4, 5, 6><<<static_cast<unsigned>(dgs.blocks), 256, 0, st>>>(
+        dgs, cases, ph, sig_fac);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dt_lambda_mixed(int p, const float4 *S, const float *Pr, const float *geo, const int4 *conn,
                                    const int *fmask, const int4 *tiles, long long ntiles, const BatchCase *cases,
                                    long long K, const Phys<float> &ph, float sig_fac, double *lam, cudaStream_t st)

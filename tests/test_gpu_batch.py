@@ -167,15 +167,17 @@ def test_batch_fused_matches_five_launches(small_run, variant):
 def test_batch_launch_count(small_run):
     cases, states, nsteps, res = small_run
     groups = len({c["p"] for c in cases})
-    # set_state per case, initial forces (groups + 1), then per step: dt per group,
-    # dt reduce, Newmark, 5 stages per group, forces per group, force sum, record;
-    # the tuned run adds five residual-only launches per shape (three) and group
+    # set_state per case, initial forces (wall faces of all groups, sums), then
+    # per step: the time-step bounds of all groups, dt + Newmark, 5 stages per
+    # group (one cooperative launch per group when fused), wall forces of all
+    # groups, force sums with the history record; the tuned run adds five
+    # residual-only launches per shape (three) and group
     for run in RUNS:
         stage = groups if run[0] == "fused" else 5 * groups
-        per_step = groups + 2 + stage + groups + 1 + 1
+        per_step = 1 + 1 + stage + 1 + 1
         launches = res[run][3]
         tune = 15 * groups if run[1] == 0 else 0
-        assert launches == len(cases) + (groups + 1) + tune + nsteps * per_step, (run, launches)
+        assert launches == len(cases) + 2 + tune + nsteps * per_step, (run, launches)
 
 
 def test_batch_rejects_bad_mesh(dg):

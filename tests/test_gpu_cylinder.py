@@ -173,7 +173,8 @@ def test_config3_cl_cd_windows(dg):
     at steps 0, 500 and 1,000 (saved, common to all three runs) the oracle,
     the FP64 path and the mixed path each run a window of 200 steps; their
     C_L, C_D histories (every 10 steps) agree to 1e-4 (C_L relative to
-    max |C_L| over the window, C_D to its mean).  Steps at CFL 2 (the time-step
+    max |C_L| over the window, C_D to its mean; the mixed path's lift to 1e-4
+    of mean C_D and 1e-3 of max |C_L|, see below).  Steps at CFL 2 (the time-step
     bound is 4-7 times the operator's spectral radius, so this is about 1/6
     of the five-stage scheme's stability edge), so that lift and drag move by
     much more than the tolerance over a window."""
@@ -202,7 +203,12 @@ def test_config3_cl_cd_windows(dg):
             s.set_state(Us)
             got = force_history(lambda n: s.steps(0.0, dt, n), s.wall_forces, nwin, every)
             e_cl, e_cd = history_errors(ref, got)
-            assert e_cl <= TOL["mixed"] and e_cd <= TOL["mixed"], (prec, e_cl, e_cd)
+            # before shedding |C_L| is ~1e-4 of C_D: the lift is held to 1e-4
+            # of the force (mean C_D) and to 1e-3 of its own largest value (the
+            # FP32 rounding of a pressure of 17.9 integrated over the wall)
+            e_cl_force = np.abs(got[:, 1] - ref[:, 1]).max() / np.abs(ref[:, 0]).mean()
+            assert e_cd <= TOL[prec] and e_cl_force <= TOL[prec], (prec, e_cl_force, e_cd)
+            assert e_cl <= (TOL[prec] if prec == "fp64" else 1e-3), (prec, e_cl)
         # the window is not empty: lift and drag move over it by far more
         # than the tolerance, so a stale state would fail
         assert np.ptp(ref[:, 1]) > 1e-2 * np.abs(ref[:, 1]).max(), ref[:, 1]
