@@ -210,10 +210,11 @@ dg_status dg_check_finite(dg_ctx *ctx, int *ok);
  * (x0, y0) at t = 0, carried at (u0, v0) on a periodic square of side L
  * (rho_inf = p_inf = 1), an exact Navier-Stokes solution (the source of the
  * advected-vortex workload; the paper's Sec. 3.1 builds its source the same
- * way from a manufactured solution); it is evaluated at the nodes at every
- * stage's time t + c_i dt by a kernel of its own (FP64 arithmetic on the FP64
- * path, FP32 on the mixed path), and with it fused steps fall back to five
- * stage launches per step.  DG_SOURCE_NONE removes any source.
+ * way from a manufactured solution); it is evaluated at the nodes at the
+ * five stage times t + c_i dt of a step by one kernel launch before the
+ * stages (FP64 arithmetic on the FP64 path, FP32 on the mixed path; the
+ * library holds five state-sized arrays for it), and with it fused steps fall
+ * back to five stage launches per step.  DG_SOURCE_NONE removes any source.
  * Errors: DG_EINVAL (no mesh, unknown kind, null params, L <= 0), DG_ECUDA. */
 dg_status dg_set_source(dg_ctx *ctx, int kind, const double *params);
 

@@ -324,11 +324,9 @@ __global__ void batch_forces_record_kernel(const double *partial, const int *wse
 // FP64); `real` is the arithmetic after the FP64 offsets (FP64 path: double;
 // mixed: float).  The constants come precomputed (VortexSource).
 template <typename real>
-__global__ void vortex_source_kernel(const double *xy, long long nn, int Np, VortexSource v, double xc,
-                                     double yc, double *S)
+__device__ __forceinline__ void vortex_source_node(const double *xy, long long nn, long long n, int Np,
+                                                   const VortexSource &v, double xc, double yc, double *S)
 {
-    const long long n = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-    if (n >= nn) return;
     real dx = real(xy[n] - xc), dy = real(xy[nn + n] - yc);
     dx -= real(v.L) * rint(dx * real(v.invL));
     dy -= real(v.L) * rint(dy * real(v.invL));
@@ -348,17 +346,35 @@ __global__ void vortex_source_kernel(const double *xy, long long nn, int Np, Vor
     o[3 * Np] = static_cast<double>(sE);
 }
 
+// ns source arrays (one per stage time, centres (xc[s], yc[s]) given) in one
+// launch: S + s * 4 nn holds the source at stage time s.
+template <typename real>
+__global__ void vortex_source_kernel(const double *xy, long long nn, int Np, VortexSource v, VortexCentres cen,
+                                     double *S)
+{
+    const long long n = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (n >= nn) return;
+    for (int s = 0; s < cen.ns; ++s)
+        vortex_source_node<real>(xy, nn, n, Np, v, cen.xc[s], cen.yc[s], S + s * 4 * nn);
+}
+
 }  // namespace
 
 cudaError_t launch_vortex_source(bool fp64, const double *xy, long long nn, int Np, const VortexSource &v,
-                                 double t, double *S, cudaStream_t st)
+                                 const double *t, int ns, double *S, cudaStream_t st)
 {
+    if (ns < 1 || ns > 5) return cudaErrorInvalidValue;
     const unsigned blocks = static_cast<unsigned>((nn + 255) / 256);
-    const double xc = v.x0 + v.u0 * t, yc = v.y0 + v.v0 * t;
+    VortexCentres cen{};
+    cen.ns = ns;
+    for (int s = 0; s < ns; ++s) {
+        cen.xc[s] = v.x0 + v.u0 * t[s];
+        cen.yc[s] = v.y0 + v.v0 * t[s];
+    }
     if (fp64)
-        vortex_source_kernel<double><<<blocks, 256, 0, st>>>(xy, nn, Np, v, xc, yc, S);
+        vortex_source_kernel<double><<<blocks, 256, 0, st>>>(xy, nn, Np, v, cen, S);
     else
-        vortex_source_kernel<float><<<blocks, 256, 0, st>>>(xy, nn, Np, v, xc, yc, S);
+        vortex_source_kernel<float><<<blocks, 256, 0, st>>>(xy, nn, Np, v, cen, S);
     return cudaGetLastError();
 }
 

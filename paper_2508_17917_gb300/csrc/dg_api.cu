@@ -164,13 +164,20 @@ dg_status run_stage(dg_ctx *c, int s, double t, double dt, const double vw[2], i
     sp.Rout = rout;
     sp.conn = c->conn.ptr;
     sp.fmask = c->fmask.ptr;
+    const double *src = (c->source_kind != DG_SOURCE_NONE) ? c->src.ptr : nullptr;
     if (c->source_kind == DG_SOURCE_VORTEX) {
-        // time-dependent source at the stage's time, evaluated before the stage
-        DG_CUDA(c, dg::launch_vortex_source(c->prm.precision == DG_PRECISION_FP64, c->src_xy.ptr,
-                                            c->K * c->ops.Np, c->ops.Np, c->vortex, t, c->src.ptr, c->stream));
-        c->launches += 1;
+        if (s < 0) {
+            // a single residual: the time-dependent source at its time, into slot 0
+            DG_CUDA(c, dg::launch_vortex_source(c->prm.precision == DG_PRECISION_FP64, c->src_xy.ptr,
+                                                c->K * c->ops.Np, c->ops.Np, c->vortex, &t, 1, c->src.ptr,
+                                                c->stream));
+            c->launches += 1;
+        } else {
+            // the step's five stage times were evaluated by dg_lsrk_step
+            src = c->src.ptr + static_cast<size_t>(s) * ndof(c);
+        }
     }
-    sp.src = (c->source_kind != DG_SOURCE_NONE) ? c->src.ptr : nullptr;
+    sp.src = src;
     sp.Sin = c->scur();
     sp.Pin = c->pcur();
     sp.Sout = c->sother();
@@ -559,7 +566,7 @@ dg_status dg_set_source(dg_ctx *c, int kind, const double *params)
         DG_CUDA(c, cudaMemcpy(c->src_xy.ptr, x.data(), x.size() * sizeof(double), cudaMemcpyHostToDevice));
         DG_CUDA(c, cudaMemcpy(c->src_xy.ptr + x.size(), y.data(), y.size() * sizeof(double),
                               cudaMemcpyHostToDevice));
-        DG_CUDA(c, c->src.alloc(ndof(c)));
+        DG_CUDA(c, c->src.alloc(5 * ndof(c)));         // one array per stage time of a step
         c->source_kind = kind;
         return DG_OK;
     }
@@ -702,8 +709,16 @@ dg_status dg_lsrk_step(dg_ctx *c, double t, double dt, const double vw[2])
         dg_status st = tune_stage(c, vw);
         if (st != DG_OK) return st;
     }
-    // a time-dependent source is evaluated per stage: five launches
+    // a time-dependent source is evaluated at the five stage times in one
+    // launch before the stages, which then run as five launches
     if (c->fused && c->source_kind != DG_SOURCE_VORTEX) return run_fused_step(c, dt, vw);
+    if (c->source_kind == DG_SOURCE_VORTEX) {
+        double ts[5];
+        for (int s = 0; s < 5; ++s) ts[s] = t + kRkC[s] * dt;
+        DG_CUDA(c, dg::launch_vortex_source(c->prm.precision == DG_PRECISION_FP64, c->src_xy.ptr, c->K * c->ops.Np,
+                                            c->ops.Np, c->vortex, ts, 5, c->src.ptr, c->stream));
+        c->launches += 1;
+    }
     for (int s = 0; s < 5; ++s) {
         dg_status st = run_stage(c, s, t + kRkC[s] * dt, dt, vw, dg::STAGE_UPDATE, c->cur(), c->other(), nullptr);
         if (st != DG_OK) return st;

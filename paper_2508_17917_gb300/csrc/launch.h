@@ -163,9 +163,14 @@ struct VortexSource {
     double mu, Pr;
     double invL, f0, c2, invPr;       // 1/L, beta/(2 pi), beta^2/(2 pi^2), 1/Pr
 };
-// S[K][4][Np] at time t from node coordinates xy = (x[K*Np], y[K*Np]);
-// fp64: double arithmetic, else float after the offsets
+struct VortexCentres {
+    double xc[5], yc[5];
+    int ns;
+};
+// S[s][K][4][Np] at the times t[s], s < ns <= 5, from node coordinates
+// xy = (x[K*Np], y[K*Np]) in one launch; fp64: double arithmetic, else float
+// after the offsets
 cudaError_t launch_vortex_source(bool fp64, const double *xy, long long nn, int Np, const VortexSource &v,
-                                 double t, double *S, cudaStream_t st);
+                                 const double *t, int ns, double *S, cudaStream_t st);
 
 }  // namespace dg
