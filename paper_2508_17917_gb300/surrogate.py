@@ -120,3 +120,72 @@ def coupled_run(solver, surrogate, coeff, mass, ustar, mstar, re, nsteps, cfl=0.
         rows.append([t, dt, st[0], st[1], vb, F[0], F[1], 0.0])
         out.append(rows[-1][:7] + [pred, float(use)])
     return np.array(out)
+
+
+# ---- reduced-velocity sweeps over physical time, and the screen ------------
+
+def rigid_to_rows(r):
+    """dg_batch_rigid rows (t, dt, y, y', y'', v_b, Fx, Fy, Mz, frozen) ->
+    history rows (t, dt, y, y', v_b, Fx, Fy, 0) as make_windows reads them."""
+    r = np.asarray(r, dtype=np.float64)
+    out = np.zeros(r.shape[:-1] + (8,))
+    out[..., [0, 1, 2, 3, 4, 5, 6]] = r[..., [0, 1, 2, 3, 5, 6, 7]]
+    return out
+
+
+def sweep_histories(batch, dt, t_end, sample_dt, cfl=1.0):
+    """Advance every case of a BatchSolver at the fixed step dt up to t_end,
+    sampling the rigid-body state and the loads every sample_dt (a whole
+    number of steps; dg_batch_run between samples, one synchronising read per
+    sample).  Returns H [nsamples + 1][ncases][8] in the history-row format,
+    starting with the state at t = 0."""
+    batch.set_fixed_dt(dt)
+    every = max(1, int(round(sample_dt / dt)))
+    rows = [rigid_to_rows(batch.rigid())]
+    n = int(np.ceil(t_end / (every * dt)))
+    for _ in range(n):
+        batch.run(cfl, every, use_graph=True)
+        rows.append(rigid_to_rows(batch.rigid()))
+    return np.array(rows)
+
+
+def amplitude(y):
+    """Half the range of a displacement history."""
+    y = np.asarray(y)
+    return 0.5 * float(y.max() - y.min()) if y.size else 0.0
+
+
+def screen_rollout(surrogate, prefix, coeffs, masses, params, nsteps, q=Q_REF):
+    """The screen's continuation of several cases at once.  prefix: DG rows
+    [n][ncases][8] (history format, uniformly spaced in time); coeffs[i] =
+    (M_r, C_r, K_r), masses[i], params[i] = (U*, m*, Re).  Every step the
+    surrogate predicts the next (C_L, C_D) of every case from its last window,
+    and the Newmark step (Eq. 1dof_oscillator, step = the prefix's sample
+    spacing) takes the predicted lift; nsteps steps.  Returns the continued
+    rows [nsteps][ncases][8]."""
+    P = np.asarray(prefix, dtype=np.float64)
+    nc = P.shape[1]
+    h = P[-1, 0, 0] - P[-2, 0, 0]
+    w = surrogate.window
+    hist = [list(P[max(0, P.shape[0] - w):, i]) for i in range(nc)]
+    hist = [[list(r) for r in rows] for rows in hist]
+    states = []
+    for i in range(nc):
+        r = hist[i][-1]
+        c = coeffs[i]
+        states.append(np.array([r[2], r[3], (r[6] / masses[i] - c[1] * r[3] - c[2] * r[2]) / c[0]]))
+    out = np.zeros((nsteps, nc, 8))
+    for n in range(nsteps):
+        Xs, Ss, Cs = [], [], []
+        for i in range(nc):
+            X, _, S, C = make_windows(np.array(hist[i][-w:] + [hist[i][-1]]), *params[i], w, q)
+            Xs.append(X[0]); Ss.append(S[0]); Cs.append(C[0])
+        dC = surrogate.predict(np.array(Xs)) * np.array(Ss)
+        for i in range(nc):
+            cl, cd = Cs[i][0] + dC[i, 0], Cs[i][1] + dC[i, 1]
+            states[i], vb = dg_rigid_step(coeffs[i], cl * q / masses[i], h, states[i])
+            row = [hist[i][-1][0] + h, h, states[i][0], states[i][1], vb, cd * q, cl * q, 0.0]
+            hist[i].append(row)
+            hist[i] = hist[i][-w:]
+            out[n, i] = row
+    return out
