@@ -21,8 +21,16 @@ from .binding import Mlp, dg_rigid_step
 Q_REF = 0.5          # 1/2 rho_inf |v_inf|^2 D with rho_inf = |v_inf| = D = 1
 
 
-def make_windows(rows, ustar, mstar, re, window=16, q=Q_REF):
-    """Samples from one trajectory, in scale-free form.
+def make_windows(rows, ustar, mstar, re, window=16, q=Q_REF, mode="increments"):
+    """Samples from one trajectory.
+
+    mode "values": the four series (y, y', C_L, C_D) enter as `window` values
+    each, followed by (U*, m*, Re); T [n][2] is the next (C_L, C_D), S = 1 and
+    C = 0.  For trajectories sampled at a fixed step over physical time
+    (sweep_histories), where the series have their physical sizes.
+
+    mode "increments" (scale-free form, for per-step DG histories whose time
+    steps differ between cases by orders of magnitude):
 
     rows: [nsteps][>= 7] per-step records (t, dt, y, y', v_b, Fx, Fy, ...), as
     written by dg_batch_run's history.  For each of the four series
@@ -36,6 +44,13 @@ def make_windows(rows, ustar, mstar, re, window=16, q=Q_REF):
     rows = np.asarray(rows, dtype=np.float64)
     feat = np.stack([rows[:, 2], rows[:, 3], rows[:, 6] / q, rows[:, 5] / q], axis=1)
     X, T, S, C = [], [], [], []
+    if mode == "values":
+        for n in range(window - 1, rows.shape[0] - 1):
+            X.append(np.concatenate([feat[n - window + 1:n + 1].T.ravel(), [ustar, mstar, re]]))
+            T.append(feat[n + 1, [2, 3]])
+            S.append([1.0, 1.0])
+            C.append([0.0, 0.0])
+        return np.array(X), np.array(T), np.array(S), np.array(C)
     for n in range(window - 1, rows.shape[0] - 1):
         w = feat[n - window + 1:n + 1]
         d = np.diff(w, axis=0)                                    # [window - 1][4]
@@ -51,14 +66,19 @@ def make_windows(rows, ustar, mstar, re, window=16, q=Q_REF):
 class LoadSurrogate:
     """The network plus the feature and target scaling fitted on its data.
 
-    The network learns the correction to linear extrapolation: its target is
-    the scaled next increment minus the last scaled increment of the window,
-    so a network that outputs zero reproduces linear extrapolation."""
+    The network learns a correction: in "increments" mode its target is the
+    scaled next increment minus the last scaled increment of the window (a
+    network that outputs zero reproduces linear extrapolation); in "values"
+    mode the next value minus the last one (zero output: the lagged load)."""
 
-    def __init__(self, window=16, width=128, depth=3, seed=0, max_batch=8192):
+    def __init__(self, window=16, width=128, depth=3, seed=0, max_batch=8192, mode="increments"):
         self.window = window
+        self.mode = mode
         self.n_in = 4 * window + 3
-        self.last = [2 * window + window - 2, 3 * window + window - 2]    # last C_L, C_D increments
+        if mode == "values":
+            self.last = [3 * window - 1, 4 * window - 1]                  # last C_L, C_D values
+        else:
+            self.last = [2 * window + window - 2, 3 * window + window - 2]    # last C_L, C_D increments
         self.net = Mlp(self.n_in, width, depth, 2, max_batch=max_batch, seed=seed)
         self.mu_x = self.sd_x = self.mu_t = self.sd_t = None
 
@@ -105,7 +125,7 @@ def coupled_run(solver, surrogate, coeff, mass, ustar, mstar, re, nsteps, cfl=0.
         pred = np.nan
         if len(rows) >= surrogate.window:
             X, _, S, C = make_windows(np.array(rows[-surrogate.window:] + [rows[-1]]), ustar, mstar, re,
-                                      surrogate.window, q)
+                                      surrogate.window, q, surrogate.mode)
             dC = surrogate.predict(X[:1])[0] * S[0]
             pred = (C[0, 0] + dC[0]) * q
         use = trusted and np.isfinite(pred)
@@ -178,7 +198,8 @@ def screen_rollout(surrogate, prefix, coeffs, masses, params, nsteps, q=Q_REF):
     for n in range(nsteps):
         Xs, Ss, Cs = [], [], []
         for i in range(nc):
-            X, _, S, C = make_windows(np.array(hist[i][-w:] + [hist[i][-1]]), *params[i], w, q)
+            X, _, S, C = make_windows(np.array(hist[i][-w:] + [hist[i][-1]]), *params[i], w, q,
+                                      surrogate.mode)
             Xs.append(X[0]); Ss.append(S[0]); Cs.append(C[0])
         dC = surrogate.predict(np.array(Xs)) * np.array(Ss)
         for i in range(nc):
