@@ -259,6 +259,20 @@ dg_status dg_reference_operators(int p, double *r, double *s, double *Dr, double
  * DG_EUNSUPPORTED (device index above 63), DG_ECUDA. */
 dg_status dg_wall_forces_noalloc(dg_ctx *ctx, const double xc[2], double out[3]);
 
+/* Broken gradient of the current state (Sec. 2.2: grad_h U =
+ * (rx Dr + sx Ds, ry Dr + sy Ds) U on every element, the gradient the
+ * residual's viscous fluxes use): gx, gy [K][4][Np] FP64, host pointers if
+ * on_device == 0, device pointers (borrowed for the call) otherwise.
+ * impl 0: FP64 arithmetic on the CUDA cores.  impl 1: the element products
+ * batched 32 elements to a CTA as (128 x K)(K x 2 Np) products on the
+ * fifth-generation tensor cores (tcgen05.mma kind::tf32, three products of
+ * split operands, FP32 accumulation in tensor memory) with the FP64 state
+ * tiles staged by the tensor memory accelerator; good to about 2^-21 of
+ * sum |D||U| relative to the element's first node.  Synchronises (impl 1, or
+ * host outputs).  Errors: DG_EINVAL (null, no mesh, bad impl), DG_ETIMEOUT
+ * (a bounded wait in the impl 1 kernel gave up), DG_ECUDA. */
+dg_status dg_broken_gradient(dg_ctx *ctx, double *gx, double *gy, int on_device, int impl);
+
 /* Number of the library's kernels launched by this context so far. */
 int64_t dg_kernel_launches(const dg_ctx *ctx);
 

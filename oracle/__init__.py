@@ -47,6 +47,7 @@ def lib():
         L.oracle_rhs.argtypes = [C.c_void_p, _dp, C.c_double, _dp, _dp]
         L.oracle_lsrk_step.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, _dp]
         L.oracle_face_sigma.argtypes = [C.c_void_p, _dp, _dp, _dp]
+        L.oracle_broken_gradient.argtypes = [C.c_void_p, _dp, _dp, _dp]
         L.oracle_dt.argtypes = [C.c_void_p, _dp, C.c_double, _dp, _dp, _dp]
         L.oracle_wall_forces.argtypes = [C.c_void_p, _dp, _dp, _dp]
         L.oracle_penalty_norm.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_double]
@@ -199,6 +200,13 @@ class Problem:
             U = self.lsrk_step(U, t, dt, vw)
             t += dt
         return U
+
+    def broken_gradient(self, U):
+        """(Ux, Uy) = ((rx Dr + sx Ds) U, (ry Dr + sy Ds) U) per element, [K][4][Np] each."""
+        U = _f64(U)
+        Ux, Uy = np.empty_like(U), np.empty_like(U)
+        lib().oracle_broken_gradient(self._ptr(), _p(U), _p(Ux), _p(Uy))
+        return Ux, Uy
 
     def face_sigma(self, U, vw=(0.0, 0.0)):
         """Penalty sigma_e per face, [K][3] (Eq. penalty_final)."""

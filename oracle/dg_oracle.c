@@ -720,6 +720,13 @@ int oracle_lsrk_step(const oracle_problem *P, double *U, double t, double dt, co
     return st;
 }
 
+/* Broken gradient of U, Ux and Uy [K][4][Np] (for tests). */
+int oracle_broken_gradient(const oracle_problem *P, const double *U, double *Ux, double *Uy)
+{
+    broken_gradient(P, U, Ux, Uy);
+    return 0;
+}
+
 /* Penalty sigma_e of every face, [K][3] (for tests and the time step). */
 int oracle_face_sigma(const oracle_problem *P, const double *U, const double vw[2], double *sigma)
 {

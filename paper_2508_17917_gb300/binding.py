@@ -17,7 +17,7 @@ __all__ = ["DG_OK", "DG_PRECISION_FP64", "DG_PRECISION_MIXED", "DG_SOURCE_NONE",
            "dg_lsrk_step", "dg_lsrk_steps", "dg_compute_dt", "dg_wall_forces",
            "dg_wall_forces_noalloc", "DG_NOALLOC_MAX_WALL_FACES", "dg_rigid_step",
            "dg_check_finite", "dg_set_source", "dg_node_coords", "dg_reference_operators",
-           "dg_kernel_launches", "dg_last_error", "Solver", "EXPORTED",
+           "dg_kernel_launches", "dg_last_error", "Solver", "EXPORTED", "dg_broken_gradient",
            "dg_set_stage_variant", "dg_stage_variant", "dg_set_fused_steps", "dg_set_barrier_limit",
            "dg_barrier_status", "dg_set_overintegration", "dg_overint_degree",
            "DgCase", "dg_batch_create", "dg_batch_destroy", "dg_batch_last_error",
@@ -101,6 +101,7 @@ EXPORTED = {
     "dg_batch_stage_variant": (C.c_int, [C.c_void_p, C.c_int]),
     "dg_batch_set_fused_steps": (C.c_int, [C.c_void_p, C.c_int]),
     "dg_batch_set_fixed_dt": (C.c_int, [C.c_void_p, _dp]),
+    "dg_broken_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "dg_batch_case_size": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int)]),
     "dg_batch_node_coords": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp]),
     "dg_batch_set_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
@@ -242,6 +243,15 @@ def dg_wall_forces_noalloc(ctx, xc=(0.0, 0.0)):
     return out
 
 
+def dg_broken_gradient(ctx, gx, gy, impl=0):
+    """gx, gy: [K][4][Np] float64 arrays (host numpy or device torch tensors)."""
+    px, dx = _arr_ptr(gx)
+    py, dy = _arr_ptr(gy)
+    if dx != dy:
+        raise ValueError("gx and gy must both be on the host or both on the device")
+    _check(lib().dg_broken_gradient(ctx, px, py, dx, int(impl)), ctx)
+
+
 def dg_rigid_step(coeff, F, dt, state):
     """Returns (new_state, v_b); `state` is not modified."""
     st = _f64(state).copy()
@@ -366,6 +376,12 @@ class Solver:
 
     def wall_forces(self, xc=(0.0, 0.0)):
         return dg_wall_forces(self.ctx, xc)
+
+    def broken_gradient(self, impl=0):
+        """(d/dx, d/dy) of the current state, each [K][4][Np] (host arrays)."""
+        gx, gy = np.zeros(self.shape), np.zeros(self.shape)
+        dg_broken_gradient(self.ctx, gx, gy, impl)
+        return gx, gy
 
     def check_finite(self):
         return dg_check_finite(self.ctx)

@@ -67,6 +67,8 @@ struct dg_ctx {
     unsigned bar_limit = 1u << 24;
     bool bar_used = false;
     int source_kind = DG_SOURCE_NONE;
+    dg::DevBuf<float> gimg;           // split [Dr; Ds] image of the tcgen05 gradient
+    dg::DevBuf<double> gtmp;          // host-output staging of dg_broken_gradient
     dg::VortexSource vortex{};         // DG_SOURCE_VORTEX parameters
     dg::DevBuf<double> src_xy;        // node coordinates for the vortex source
 
@@ -789,6 +791,53 @@ dg_status dg_check_finite(dg_ctx *c, int *ok)
     DG_CUDA(c, cudaMemcpyAsync(&f, c->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     DG_CUDA(c, cudaStreamSynchronize(c->stream));
     *ok = f ? 0 : 1;
+    return DG_OK;
+}
+
+dg_status dg_broken_gradient(dg_ctx *c, double *gx, double *gy, int on_device, int impl)
+{
+    if (!c) return DG_EINVAL;
+    c->err.clear();
+    if (!gx || !gy || c->K < 1) return fail(c, DG_EINVAL, "null output or no mesh");
+    if (impl != 0 && impl != 1) return fail(c, DG_EINVAL, "impl must be 0 (FP64) or 1 (tcgen05)");
+    const size_t n = ndof(c);
+    double *ox = gx, *oy = gy;
+    if (!on_device) {
+        if (c->gtmp.n != 2 * n) DG_CUDA(c, c->gtmp.alloc(2 * n));
+        ox = c->gtmp.ptr;
+        oy = c->gtmp.ptr + n;
+    }
+    dg::GradTc05Args a{};
+    a.U = c->cur();
+    a.Dr = c->ops.Dr.data();
+    a.Ds = c->ops.Ds.data();
+    a.Dr_dev = c->Dr64.ptr;
+    a.Ds_dev = c->Ds64.ptr;
+    a.geo = c->geo64.ptr;
+    a.K = c->K;
+    a.gx = ox;
+    a.gy = oy;
+    a.wait_limit = 1u << 20;
+    if (impl == 1) {
+        const size_t nf = dg::grad_tc05_bimg_floats(c->prm.p);
+        if (c->gimg.n != nf) DG_CUDA(c, c->gimg.alloc(nf));
+        a.bimg = c->gimg.ptr;
+        a.err = c->flag.ptr;
+        DG_CUDA(c, cudaMemsetAsync(c->flag.ptr, 0, sizeof(int), c->stream));
+    }
+    DG_CUDA(c, dg::launch_broken_gradient(c->prm.p, impl, a, c->stream));
+    c->launches += 1;
+    if (impl == 1) {
+        int f = 0;
+        DG_CUDA(c, cudaMemcpyAsync(&f, c->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        DG_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (f) return fail(c, DG_ETIMEOUT, "a bounded wait of the tcgen05 gradient kernel gave up");
+    }
+    if (!on_device) {
+        DG_CUDA(c, cudaMemcpyAsync(gx, ox, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        DG_CUDA(c, cudaMemcpyAsync(gy, oy, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        DG_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
     return DG_OK;
 }
 

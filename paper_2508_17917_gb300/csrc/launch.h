@@ -163,6 +163,22 @@ struct VortexSource {
     double mu, Pr;
     double invL, f0, c2, invPr;       // 1/L, beta/(2 pi), beta^2/(2 pi^2), 1/Pr
 };
+// broken gradient of every element (dg_broken_gradient): impl 0 FP64 on the
+// CUDA cores, impl 1 split TF32 on tcgen05 with the tiles staged by TMA
+struct GradTc05Args {
+    const double *U;            // [K][4][Np] FP64 state (device)
+    const double *Dr, *Ds;      // Np x Np operators (host, for the split image)
+    const double *Dr_dev, *Ds_dev;   // the same on the device (impl 0)
+    const double *geo;          // double[16] per element
+    long long K;
+    double *gx, *gy;            // [K][4][Np] outputs (device)
+    float *bimg;                // device buffer of grad_tc05_bimg_floats(p) floats (impl 1)
+    int *err;                   // set to 1 if a bounded wait gave up (impl 1)
+    unsigned wait_limit;
+};
+size_t grad_tc05_bimg_floats(int p);
+cudaError_t launch_broken_gradient(int p, int impl, const GradTc05Args &a, cudaStream_t st);
+
 struct VortexCentres {
     double xc[5], yc[5];
     int ns;
