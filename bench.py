@@ -469,6 +469,9 @@ def run_ours(args):
     # --- surrogate MLP (67 -> 3 x 128 GELU -> 2): full-batch Adam steps at B = 4096
     mlp_line = run_mlp(dg, torch, np) if not args.no_large else None
 
+    # --- broken gradient (a2) on the tensor cores through tcgen05 against FP64
+    grad_line = run_gradient(dg, torch, dg_inputs, to_kcn, peak) if not args.no_large else None
+
     # --- end to end through the C ABI with host buffers (pinned)
     host_in = torch.empty((K, 4, NP), dtype=torch.float64, pin_memory=True)
     host_in.copy_(torch.from_numpy(U0))
@@ -515,6 +518,7 @@ def run_ours(args):
             "p6_large": p6,
             "batch_viv": batch,
             "mlp": mlp_line,
+            "gradient": grad_line,
             "cpu_baseline": cpu,
             "cpu_baseline_1t": cpu1,
             "e2e": e2e,
@@ -590,6 +594,41 @@ def run_batch(dg, torch, dg_inputs, to_kcn, np, peak, steps):
            "gpu_launches": launches, "finite": bool(ok),
            "fused_steps": {"ms_per_step": ms_fused / steps, "value": dof * 5 * steps / (ms_fused * 1e-3)}}
     del b
+    return out
+
+
+def run_gradient(dg, torch, dg_inputs, to_kcn, peak, n=512, calls=20):
+    """The broken gradient of the benchmark's vortex state on n x n split quads
+    (dg_broken_gradient, device outputs): FP64 on the CUDA cores against the
+    tcgen05 kernel (split TF32 products in tensor memory, TMA-staged tiles);
+    CUDA events over `calls` calls after warm-up."""
+    mesh = vortex_problem(n)
+    st = torch.cuda.current_stream()
+    s = dg.Solver(mesh, P, "mixed", stream=st.cuda_stream, mu=1e-3)
+    x, y = s.node_coords()
+    s.set_state(dg_inputs.perturb(to_kcn(dg_inputs.isentropic_vortex(x, y)), seed=0))
+    gx = torch.empty((mesh.K, 4, NP), dtype=torch.float64, device="cuda")
+    gy = torch.empty_like(gx)
+    dof = 4 * mesh.K * NP
+    # read the state and the geometry record, write both gradients
+    bytes_call = dof * 8 + mesh.K * 128 + 2 * dof * 8
+    out = {"workload": f"broken gradient of the p=4 vortex state, {n}x{n} split quads (K={mesh.K})",
+           "bytes_per_call": bytes_call}
+    for impl, name in ((0, "fp64_cuda_cores"), (1, "tcgen05_tf32x3_tma")):
+        for _ in range(3):
+            dg.dg_broken_gradient(s.ctx, gx, gy, impl)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(calls):
+            dg.dg_broken_gradient(s.ctx, gx, gy, impl)
+        b.record(st)
+        b.synchronize()
+        dg.dg_barrier_status(s.ctx)
+        us = a.elapsed_time(b) / calls * 1e3
+        gbs = bytes_call / (us * 1e-6) / 1e9
+        out[name] = {"us_per_call": us, "achieved_gbs": gbs, "frac_of_hbm": gbs / peak,
+                     "dof_per_s": dof / (us * 1e-6)}
+    del s
     return out
 
 

@@ -147,9 +147,10 @@ dg_status dg_set_fused_steps(dg_ctx *ctx, int on);
  * 2^24, about 1.7 s; 0 makes every wait give up at once). */
 dg_status dg_set_barrier_limit(dg_ctx *ctx, uint32_t waits);
 
-/* DG_ETIMEOUT if a barrier of a fused step since the last check gave up
- * (then clears the flag), DG_OK otherwise.  Synchronises when fused steps
- * ran.  Errors: DG_EINVAL, DG_ECUDA. */
+/* DG_ETIMEOUT if a bounded device wait since the last check gave up -- a
+ * grid barrier of a fused step, or a wait of the tcgen05 gradient kernel of
+ * dg_broken_gradient -- (then clears the flag), DG_OK otherwise.
+ * Synchronises when such kernels ran.  Errors: DG_EINVAL, DG_ECUDA. */
 dg_status dg_barrier_status(dg_ctx *ctx);
 
 /* Copy the state in ([K][4][Np] FP64; host pointer if on_device == 0, device
@@ -268,9 +269,12 @@ dg_status dg_wall_forces_noalloc(dg_ctx *ctx, const double xc[2], double out[3])
  * fifth-generation tensor cores (tcgen05.mma kind::tf32, three products of
  * split operands, FP32 accumulation in tensor memory) with the FP64 state
  * tiles staged by the tensor memory accelerator; good to about 2^-21 of
- * sum |D||U| relative to the element's first node.  Synchronises (impl 1, or
- * host outputs).  Errors: DG_EINVAL (null, no mesh, bad impl), DG_ETIMEOUT
- * (a bounded wait in the impl 1 kernel gave up), DG_ECUDA. */
+ * sum |D||U| relative to the element's first node.  With device outputs the
+ * call is asynchronous on the context's stream and a bounded wait of the
+ * impl 1 kernel that gave up is reported by the next dg_barrier_status,
+ * dg_get_state or dg_check_finite (DG_ETIMEOUT); with host outputs it
+ * synchronises and reports it itself.  Errors: DG_EINVAL (null, no mesh,
+ * bad impl), DG_ETIMEOUT, DG_ECUDA. */
 dg_status dg_broken_gradient(dg_ctx *ctx, double *gx, double *gy, int on_device, int impl);
 
 /* Number of the library's kernels launched by this context so far. */

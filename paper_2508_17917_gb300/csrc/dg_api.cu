@@ -388,7 +388,9 @@ dg_status dg_barrier_status(dg_ctx *c)
     c->bar_used = false;
     if (e) {
         DG_CUDA(c, cudaMemset(c->bar_err.ptr, 0, sizeof(int)));
-        return fail(c, DG_ETIMEOUT, "a grid barrier of a fused step gave up waiting; the state is not valid");
+        return fail(c, DG_ETIMEOUT,
+                    "a bounded device wait gave up (a fused step's grid barrier: the state is not valid; "
+                    "or the tcgen05 gradient kernel: its output is not valid)");
     }
     return DG_OK;
 }
@@ -821,22 +823,21 @@ dg_status dg_broken_gradient(dg_ctx *c, double *gx, double *gy, int on_device, i
     if (impl == 1) {
         const size_t nf = dg::grad_tc05_bimg_floats(c->prm.p);
         if (c->gimg.n != nf) DG_CUDA(c, c->gimg.alloc(nf));
+        if (!c->bar_err.ptr) {
+            DG_CUDA(c, c->bar_err.alloc(1));
+            DG_CUDA(c, cudaMemset(c->bar_err.ptr, 0, sizeof(int)));
+        }
         a.bimg = c->gimg.ptr;
-        a.err = c->flag.ptr;
-        DG_CUDA(c, cudaMemsetAsync(c->flag.ptr, 0, sizeof(int), c->stream));
+        a.err = c->bar_err.ptr;        // reported by dg_barrier_status, as for fused steps
+        c->bar_used = true;
     }
     DG_CUDA(c, dg::launch_broken_gradient(c->prm.p, impl, a, c->stream));
     c->launches += 1;
-    if (impl == 1) {
-        int f = 0;
-        DG_CUDA(c, cudaMemcpyAsync(&f, c->flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-        DG_CUDA(c, cudaStreamSynchronize(c->stream));
-        if (f) return fail(c, DG_ETIMEOUT, "a bounded wait of the tcgen05 gradient kernel gave up");
-    }
     if (!on_device) {
         DG_CUDA(c, cudaMemcpyAsync(gx, ox, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         DG_CUDA(c, cudaMemcpyAsync(gy, oy, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         DG_CUDA(c, cudaStreamSynchronize(c->stream));
+        return dg_barrier_status(c);
     }
     return DG_OK;
 }
