@@ -843,6 +843,21 @@ def run_profile(args):
         assert bool(torch.isfinite(hist).all())
         print(json.dumps({"profile": args.profile, "B": B, "steps": 12, "launches": net.launches}))
         return
+    if args.profile == "grad512":
+        # the tcgen05 broken gradient on the 512^2 vortex state (device outputs)
+        torch.cuda.set_device(0)
+        mesh = vortex_problem(512)
+        s = dg.Solver(mesh, P, "mixed", stream=torch.cuda.current_stream().cuda_stream, mu=1e-3)
+        x, y = s.node_coords()
+        s.set_state(dg_inputs.perturb(to_kcn(dg_inputs.isentropic_vortex(x, y)), seed=0))
+        gx = torch.empty((mesh.K, 4, NP), dtype=torch.float64, device="cuda")
+        gy = torch.empty_like(gx)
+        for impl in (0, 1, 1):
+            dg.dg_broken_gradient(s.ctx, gx, gy, impl)
+        dg.dg_barrier_status(s.ctx)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": args.profile, "K": mesh.K, "launches": s.launches}))
+        return
     prec, n, theta, var, p = {"mixed512": ("mixed", 512, 0.0, 0, P), "mixed128": ("mixed", 128, 0.0, 0, P),
                               "fp64_128": ("fp64", 128, 0.0, 0, P), "sip128": ("mixed", 128, 1.0, 0, P),
                               "tc512": ("mixed", 512, 0.0, 3, P), "tcsip512": ("mixed", 512, 1.0, 3, P),
@@ -883,7 +898,7 @@ def main():
     ap.add_argument("--record-k", type=int, default=2 * 512 * 512,
                     help="elements of the captured launch (--record-traffic)")
     ap.add_argument("--profile", choices=["mixed512", "mixed128", "fp64_128", "sip128", "tc512", "tcsip512", "tc6_375", "mlp4096",
-                             "batch64"], default=None)
+                             "batch64", "grad512"], default=None)
     args = ap.parse_args()
     if args.record_traffic:
         record_traffic(args)

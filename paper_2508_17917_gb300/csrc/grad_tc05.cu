@@ -177,7 +177,9 @@ grad_tc05_kernel(const __grid_constant__ CUtensorMap tmap, const float *bimg, co
         const double ref = u[0];
 #pragma unroll
         for (int kk = 0; kk < S::KP; ++kk) {
-            const float x = (kk < Np) ? static_cast<float>(u[kk] - ref) : 0.f;
+            // FP64 difference, narrowed with integer operations (the FP64
+            // pipe of this GPU is slow; conversions run on it)
+            const float x = (kk < Np) ? cvt_d2f(u[kk] - ref) : 0.f;
             const float hi = tf32_rna(x), lo = x - hi;
             const unsigned off = (kk >> 3) * unsigned(S::A_SLICE) + kmajor_off(tid, kk & 7);
             *reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(Ahi) + off) = hi;
@@ -235,14 +237,15 @@ grad_tc05_kernel(const __grid_constant__ CUtensorMap tmap, const float *bimg, co
         }
         const long long k = k0 + e;
         if (k < K) {
+            // metric terms in FP32 (the products are FP32-accurate), widened exactly
             const double *g = geo + k * 16;
-            const double rx = g[G_RX], ry = g[G_RY], sx = g[G_SX], sy = g[G_SY];
+            const float rx = cvt_d2f(g[G_RX]), ry = cvt_d2f(g[G_RY]), sx = cvt_d2f(g[G_SX]), sy = cvt_d2f(g[G_SY]);
             double *ox = gx + (k * 4 + c) * Np, *oy = gy + (k * 4 + c) * Np;
 #pragma unroll
             for (int j = 0; j < Np; ++j) {
-                const double ur = d[j], us = d[NR + j];
-                ox[j] = rx * ur + sx * us;
-                oy[j] = ry * ur + sy * us;
+                const float ur = d[j], us = d[NR + j];
+                ox[j] = cvt_f2d(fmaf(rx, ur, sx * us));
+                oy[j] = cvt_f2d(fmaf(ry, ur, sy * us));
             }
         }
     } else if (tid == 0) {
