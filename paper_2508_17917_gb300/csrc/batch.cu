@@ -86,11 +86,6 @@ struct dg_batch {
     bool fused = false;              // one cooperative launch per degree group and step
     DevBuf<int> bar_err;
     unsigned bar_limit = 1u << 24;
-    // one stream per degree group for concurrent stage chains, with the
-    // fork and join events (created on the first step with several groups)
-    std::vector<cudaStream_t> gstreams;
-    cudaEvent_t fork = nullptr;
-    std::vector<cudaEvent_t> joins;
     // graphs: [0] starts from buffers a, [1] from buffers b
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t graph_launches = 0;
@@ -101,11 +96,6 @@ struct dg_batch {
     ~dg_batch()
     {
         drop_graphs();
-        for (auto e : joins)
-            if (e) cudaEventDestroy(e);
-        if (fork) cudaEventDestroy(fork);
-        for (auto st : gstreams)
-            if (st) cudaStreamDestroy(st);
         if (stream) cudaStreamDestroy(stream);
     }
     void drop_graphs()
@@ -177,21 +167,6 @@ dg::AuxMesh aux_of(const dg_batch *b, const Group &g)
     return m;
 }
 
-dg_status ensure_group_streams(dg_batch *b)
-{
-    if (b->gstreams.size() == b->groups.size()) return DG_OK;
-    for (size_t gi = b->gstreams.size(); gi < b->groups.size(); ++gi) {
-        cudaStream_t st = nullptr;
-        cudaEvent_t ev = nullptr;
-        B_CUDA(b, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-        b->gstreams.push_back(st);
-        B_CUDA(b, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        b->joins.push_back(ev);
-    }
-    if (!b->fork) B_CUDA(b, cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
-    return DG_OK;
-}
-
 // wall forces of every case into cases[].Fx, Fy, Mz (and, with a history,
 // the step's record): one launch over the wall faces of every degree group,
 // one block per case for the sums
@@ -251,26 +226,10 @@ dg_status enqueue_step(dg_batch *b, double cfl, double *hist, int rows)
     B_CUDA(b, dg::launch_batch_dt_newmark(b->lam.ptr, b->seg.ptr, b->dcases.ptr, n, cfl,
                                           b->use_fixed ? b->fixed_dt.ptr : nullptr, b->stream));
     b->launches += 1;
-    // Stage launches.  The degree groups are independent (their own cases and
-    // buffers), so with more than one group each group's five stages run as
-    // one chain on a stream of its own, forked after the Newmark step and
-    // joined before the forces: the tail of one group's launch overlaps the
-    // next launches of the others.  Fused steps (cooperative launches, which
-    // need the whole GPU) stay on the batch stream.
-    const bool concurrent = !b->fused && b->groups.size() > 1;
-    if (concurrent) {
-        dg_status st = ensure_group_streams(b);
-        if (st != DG_OK) return st;
-        B_CUDA(b, cudaEventRecord(b->fork, b->stream));
-    }
-    const bool start_a = b->cur_is_a;
-    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
-        Group &g = b->groups[gi];
-        cudaStream_t gs = concurrent ? b->gstreams[gi] : b->stream;
-        if (concurrent) B_CUDA(b, cudaStreamWaitEvent(gs, b->fork, 0));
-        bool a = start_a;
-        for (int s = 0; s < (b->fused ? 1 : 5); ++s, a = !a) {
+    for (int s = 0; s < (b->fused ? 1 : 5); ++s) {
+        for (auto &g : b->groups) {
             dg::StageParams sp{};
+            const bool a = b->cur_is_a;
             sp.K0in = a ? g.K0a.ptr : g.K0b.ptr;
             sp.K0out = a ? g.K0b.ptr : g.K0a.ptr;
             sp.K1 = g.K1.ptr;
@@ -309,32 +268,29 @@ dg_status enqueue_step(dg_batch *b, double cfl, double *hist, int rows)
                 sp.bar = g.bar.ptr;
                 sp.bar_err = b->bar_err.ptr;
                 sp.bar_limit = b->bar_limit;
-                B_CUDA(b, cudaMemsetAsync(g.bar.ptr, 0, 2 * sizeof(unsigned), gs));
+                B_CUDA(b, cudaMemsetAsync(g.bar.ptr, 0, 2 * sizeof(unsigned), b->stream));
                 if (g.variant == 3)
-                    B_CUDA(b, dg::launch_stage_tc(g.p, true, true, g.fshape, sp, ph32, gs));
+                    B_CUDA(b, dg::launch_stage_tc(g.p, true, true, g.fshape, sp, ph32, b->stream));
                 else
-                    B_CUDA(b, dg::launch_stage_mixed_fused(g.p, true, g.fshape, sp, ph32, gs));
+                    B_CUDA(b, dg::launch_stage_mixed_fused(g.p, true, g.fshape, sp, ph32, b->stream));
             } else if (g.variant == 3) {
                 sp.tiles = g.tiles3.ptr;
                 sp.ntiles = g.ntiles3;
                 sp.ops = g.tcfrag.ptr;
-                B_CUDA(b, dg::launch_stage_tc(g.p, true, false, g.shape3, sp, ph32, gs));
+                B_CUDA(b, dg::launch_stage_tc(g.p, true, false, g.shape3, sp, ph32, b->stream));
             } else if (g.variant == 2) {
                 sp.tiles = g.tiles2.ptr;
                 sp.ntiles = g.ntiles2;
-                B_CUDA(b, dg::launch_stage_mixed2(g.p, true, g.shape2, sp, ph32, gs));
+                B_CUDA(b, dg::launch_stage_mixed2(g.p, true, g.shape2, sp, ph32, b->stream));
             } else {
                 sp.tiles = g.tiles.ptr;
                 sp.ntiles = g.ntiles;
-                B_CUDA(b, dg::launch_stage_mixed_batch(g.p, g.shape, sp, ph32, gs));
+                B_CUDA(b, dg::launch_stage_mixed_batch(g.p, g.shape, sp, ph32, b->stream));
             }
             b->launches += 1;
         }
-        if (concurrent) B_CUDA(b, cudaEventRecord(b->joins[gi], gs));
+        b->cur_is_a = !b->cur_is_a;
     }
-    if (concurrent)
-        for (size_t gi = 0; gi < b->groups.size(); ++gi) B_CUDA(b, cudaStreamWaitEvent(b->stream, b->joins[gi], 0));
-    b->cur_is_a = !start_a;            // an odd number of stages (five) per step
     return enqueue_forces(b, hist, rows);
 }
 
