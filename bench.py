@@ -88,7 +88,7 @@ def algorithmic_bytes_per_step(K, geo_bytes):
 KERNEL_FILES = {
     1: ("dg_stage.cuh", "dg_stage_mixed.cuh", "dg_device.cuh", "stage_mixed.cu"),
     2: ("dg_stage.cuh", "dg_stage_mixed.cuh", "dg_stage_mixed2.cuh", "dg_device.cuh", "stage_mixed.cu"),
-    3: ("dg_stage.cuh", "dg_stage_mixed.cuh", "dg_stage_tc.cuh", "dg_device.cuh", "stage_tc.cu"),
+    3: ("dg_stage.cuh", "dg_stage_mixed.cuh", "dg_stage_tc.cuh", "pair2.cuh", "dg_device.cuh", "stage_tc.cu"),
 }
 
 

@@ -41,6 +41,7 @@
 // holds one node per tile, and the contractions take up to four k-steps.
 #pragma once
 #include "dg_stage_mixed.cuh"
+#include "pair2.cuh"
 
 namespace dg {
 
@@ -363,22 +364,25 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
             const float pp = sPo[e * NpP + vm];
             float nrm;
             {
+                // the own trace and the other side's state (neighbour trace,
+                // far field or wall ghost), both norms in paired arithmetic
                 const float ir = 1.0f / up[0];
-                const float na = penalty_norm(up[0], up[1] * ir, up[2] * ir, up[3] * ir, n1, n2, ph);
-                float nb;
+                float rb, vb1, vb2, eb;
                 if (bt == BCT_INTERIOR) {
                     float w[4];
                     f4_to(sN[(e * 3 + f) * UN + vp], w);
                     const float iw = 1.0f / w[0];
-                    nb = penalty_norm(w[0], w[1] * iw, w[2] * iw, w[3] * iw, n1, n2, ph);
+                    rb = w[0]; vb1 = w[1] * iw; vb2 = w[2] * iw; eb = w[3] * iw;
                 } else if (bt == BCT_FARFIELD) {
                     const float iw = 1.0f / ph.Uinf[0];
-                    nb = penalty_norm(ph.Uinf[0], ph.Uinf[1] * iw, ph.Uinf[2] * iw, ph.Uinf[3] * iw, n1, n2, ph);
+                    rb = ph.Uinf[0]; vb1 = ph.Uinf[1] * iw; vb2 = ph.Uinf[2] * iw; eb = ph.Uinf[3] * iw;
                 } else {
-                    const float eb = (pp / ph.gm1 + 0.5f * up[0] * (ph.vw1 * ph.vw1 + ph.vw2 * ph.vw2)) * ir;
-                    nb = penalty_norm(up[0], ph.vw1, ph.vw2, eb, n1, n2, ph);
+                    rb = up[0]; vb1 = ph.vw1; vb2 = ph.vw2;
+                    eb = (pp / ph.gm1 + 0.5f * up[0] * (ph.vw1 * ph.vw1 + ph.vw2 * ph.vw2)) * ir;
                 }
-                nrm = fmaxf(na, nb);
+                const pf2 nab = penalty_norm2(mk(up[0], rb), mk(up[1] * ir, vb1), mk(up[2] * ir, vb2),
+                                              mk(up[3] * ir, eb), n1, n2, ph);
+                nrm = fmaxf(nab.v.x, nab.v.y);
             }
             float gbar = 0.f;
 #pragma unroll

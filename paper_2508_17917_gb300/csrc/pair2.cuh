@@ -1,0 +1,68 @@
+// pair2.cuh -- the penalty norm of two states at once with paired FP32
+// arithmetic (fma.rn.f32x2 and friends, one instruction for two lanes of a
+// 64-bit register pair).  The formula of penalty_norm in dg_device.cuh, term
+// by term; where a product and a sum are contracted into one fused
+// multiply-add may differ, so the results agree to FP32 rounding, not bit for
+// bit.  The square roots, reciprocals, arccosine and cosine stay scalar.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "dg_device.cuh"
+
+namespace dg {
+
+struct pf2 {
+    float2 v;
+};
+
+__device__ __forceinline__ pf2 mk(float a, float b) { return pf2{make_float2(a, b)}; }
+__device__ __forceinline__ pf2 sp(float a) { return pf2{make_float2(a, a)}; }
+__device__ __forceinline__ pf2 operator+(pf2 a, pf2 b) { return pf2{__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ pf2 operator-(pf2 a, pf2 b) { return pf2{__fadd2_rn(a.v, make_float2(-b.v.x, -b.v.y))}; }
+__device__ __forceinline__ pf2 operator*(pf2 a, pf2 b) { return pf2{__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ pf2 fma2(pf2 a, pf2 b, pf2 c) { return pf2{__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ pf2 neg(pf2 a) { return mk(-a.v.x, -a.v.y); }
+
+// largest eigenvalue of two symmetric 3x3 matrices (sym3_max_eig, paired)
+__device__ __forceinline__ pf2 sym3_max_eig2(pf2 a11, pf2 a12, pf2 a13, pf2 a22, pf2 a23, pf2 a33)
+{
+    const pf2 p1 = fma2(a23, a23, fma2(a13, a13, a12 * a12));
+    const pf2 q = (a11 + a22 + a33) * sp(1.0f / 3.0f);
+    pf2 b11 = a11 - q, b22 = a22 - q, b33 = a33 - q;
+    const pf2 p2 = fma2(sp(2.0f), p1, fma2(b33, b33, fma2(b22, b22, b11 * b11)));
+    const float ppx = sqrtf(p2.v.x * (1.0f / 6.0f)), ppy = sqrtf(p2.v.y * (1.0f / 6.0f));
+    const pf2 ip = mk(1.0f / ppx, 1.0f / ppy);
+    b11 = b11 * ip;
+    b22 = b22 * ip;
+    b33 = b33 * ip;
+    const pf2 c12 = a12 * ip, c13 = a13 * ip, c23 = a23 * ip;
+    const pf2 m1 = b22 * b33 - c23 * c23, m2 = c12 * b33 - c23 * c13, m3 = c12 * c23 - b22 * c13;
+    const pf2 det = fma2(c13, m3, b11 * m1 - c12 * m2);
+    const pf2 r = det * sp(0.5f);
+    const float rx = fminf(fmaxf(r.v.x, -1.0f), 1.0f), ry = fminf(fmaxf(r.v.y, -1.0f), 1.0f);
+    const float lx = q.v.x + 2.0f * ppx * cosf(acosf(rx) * (1.0f / 3.0f));
+    const float ly = q.v.y + 2.0f * ppy * cosf(acosf(ry) * (1.0f / 3.0f));
+    // a matrix with p2 = 0 is a multiple of the identity
+    return mk(p2.v.x > 0.0f ? lx : q.v.x, p2.v.y > 0.0f ? ly : q.v.y);
+}
+
+// penalty_norm of two states (rho, v1, v2, e) with one normal
+__device__ __forceinline__ pf2 penalty_norm2(pf2 rho, pf2 v1, pf2 v2, pf2 e, float n1, float n2, const Phys<float> &ph)
+{
+    const pf2 N1 = sp(n1), N2 = sp(n2), g = sp(ph.gPr);
+    const pf2 vn = fma2(v1, N1, v2 * N2), vt = fma2(v2, N1, neg(v1 * N2));
+    const pf2 vsq = fma2(v1, v1, v2 * v2);
+    const pf2 a41 = neg(fma2(vn * vn, sp(1.0f / 3.0f), vsq)) - g * (e - vsq);
+    const pf2 c42 = (sp(4.0f / 3.0f) - g) * vn, c43 = (sp(1.0f) - g) * vt;
+    const pf2 s11 = sp(16.0f / 9.0f) * fma2(vn, vn, sp(1.0f));
+    const pf2 s12 = sp(4.0f / 3.0f) * (vn * vt);
+    const pf2 s13 = sp(4.0f / 3.0f) * (c42 - vn * a41);
+    const pf2 s22 = fma2(vt, vt, sp(1.0f));
+    const pf2 s23 = c43 - vt * a41;
+    const pf2 s33 = fma2(g, g, fma2(c43, c43, fma2(c42, c42, a41 * a41)));
+    const pf2 lam = sym3_max_eig2(s11, s12, s13, s22, s23, s33);
+    const float lx = sqrtf(lam.v.x > 0.0f ? lam.v.x : 0.0f), ly = sqrtf(lam.v.y > 0.0f ? lam.v.y : 0.0f);
+    return mk(ph.mu / rho.v.x * lx, ph.mu / rho.v.y * ly);
+}
+
+}  // namespace dg
