@@ -25,6 +25,7 @@
 //     trace read from HBM/L2) instead of from the FP32 copies.
 #pragma once
 #include "dg_stage.cuh"
+#include "pair2.cuh"
 
 namespace dg {
 
@@ -324,23 +325,10 @@ stage_mixed_kernel(StageParams sp, Phys<float> ph)
             const float n1 = g[G_NX + ff], n2 = g[G_NY + ff];
             float u[4];
             f4_to(sU[fe * Np + vm], u);
-            const float ir = 1.0f / u[0];
-            const float a = penalty_norm(u[0], u[1] * ir, u[2] * ir, u[3] * ir, n1, n2, ph);
-            float b;
-            if (btype == BCT_INTERIOR) {
-                float w[4];
-                f4_to(sN[(fe * 3 + ff) * Np + vp], w);
-                const float iw = 1.0f / w[0];
-                b = penalty_norm(w[0], w[1] * iw, w[2] * iw, w[3] * iw, n1, n2, ph);
-            } else if (btype == BCT_FARFIELD) {
-                const float iw = 1.0f / ph.Uinf[0];
-                b = penalty_norm(ph.Uinf[0], ph.Uinf[1] * iw, ph.Uinf[2] * iw, ph.Uinf[3] * iw, n1, n2, ph);
-            } else {
-                const float pw = sPo[fe * NpP + vm];
-                const float eb = (pw / ph.gm1 + 0.5f * u[0] * (ph.vw1 * ph.vw1 + ph.vw2 * ph.vw2)) * ir;
-                b = penalty_norm(u[0], ph.vw1, ph.vw2, eb, n1, n2, ph);
-            }
-            sNorm[fe * NF + fm] = fmaxf(a, b);
+            float w[4];
+            if (btype == BCT_INTERIOR) f4_to(sN[(fe * 3 + ff) * Np + vp], w);
+            const float pw = (btype == BCT_WALL) ? sPo[fe * NpP + vm] : 0.f;
+            sNorm[fe * NF + fm] = trace_norms_max(u, 1.0f / u[0], pw, btype, w, n1, n2, ph);
         }
         __syncthreads();
 
@@ -593,25 +581,17 @@ __device__ __forceinline__ void dt_lambda_mixed_tile(const float4 *S, const floa
         const float *g = geo + k * 16;
         const float n1 = g[G_NX + ff], n2 = g[G_NY + ff];
         const float4 u = S[k * Np + vm];
-        const float ir = 1.0f / u.x;
-        const float a = penalty_norm(u.x, u.y * ir, u.z * ir, u.w * ir, n1, n2, ph);
-        float b, rmin = u.x;
+        const float uu[4] = {u.x, u.y, u.z, u.w};
+        float w[4], rmin = u.x;
         if (bt == BCT_INTERIOR) {
             const long long nb = (ff == 0) ? cn.x : (ff == 1 ? cn.y : cn.z);
-            const float4 w = S[nb * Np + vp];
-            const float iw = 1.0f / w.x;
-            b = penalty_norm(w.x, w.y * iw, w.z * iw, w.w * iw, n1, n2, ph);
-            rmin = fminf(rmin, w.x);
+            f4_to(S[nb * Np + vp], w);
+            rmin = fminf(rmin, w[0]);
         } else if (bt == BCT_FARFIELD) {
-            const float iw = 1.0f / ph.Uinf[0];
-            b = penalty_norm(ph.Uinf[0], ph.Uinf[1] * iw, ph.Uinf[2] * iw, ph.Uinf[3] * iw, n1, n2, ph);
             rmin = fminf(rmin, ph.Uinf[0]);
-        } else {
-            const float pw = Pr[k * NpP + vm];
-            const float eb = (pw / ph.gm1 + 0.5f * u.x * (ph.vw1 * ph.vw1 + ph.vw2 * ph.vw2)) * ir;
-            b = penalty_norm(u.x, ph.vw1, ph.vw2, eb, n1, n2, ph);
         }
-        sNorm[fe * NF + fm] = fmaxf(a, b);
+        const float pw = (bt == BCT_WALL) ? Pr[k * NpP + vm] : 0.f;
+        sNorm[fe * NF + fm] = trace_norms_max(uu, 1.0f / u.x, pw, bt, w, n1, n2, ph);
         sRmin[fe * NF + fm] = rmin;
     }
     const int ve = tid / Np, vi = tid - (tid / Np) * Np;

@@ -233,23 +233,10 @@ stage_mixed2_kernel(StageParams sp, Phys<float> ph)
                 const int vm = sFm[ff * Nfp + fi], vp = sFm[f2 * Nfp + (Nfp - 1 - fi)];
                 float u[4];
                 f4_to(sU[el * Np + vm], u);
-                const float ir = 1.0f / u[0];
-                const float na = penalty_norm(u[0], u[1] * ir, u[2] * ir, u[3] * ir, n1, n2, ph);
-                float nb;
-                if (btype == BCT_INTERIOR) {
-                    float w[4];
-                    f4_to(sN[(el * 3 + ff) * Np + vp], w);
-                    const float iw = 1.0f / w[0];
-                    nb = penalty_norm(w[0], w[1] * iw, w[2] * iw, w[3] * iw, n1, n2, ph);
-                } else if (btype == BCT_FARFIELD) {
-                    const float iw = 1.0f / ph.Uinf[0];
-                    nb = penalty_norm(ph.Uinf[0], ph.Uinf[1] * iw, ph.Uinf[2] * iw, ph.Uinf[3] * iw, n1, n2, ph);
-                } else {
-                    const float pw = sPo[el * NpP + vm];
-                    const float eb = (pw / ph.gm1 + 0.5f * u[0] * (ph.vw1 * ph.vw1 + ph.vw2 * ph.vw2)) * ir;
-                    nb = penalty_norm(u[0], ph.vw1, ph.vw2, eb, n1, n2, ph);
-                }
-                sNorm[el * NF + ff * Nfp + fi] = fmaxf(na, nb);
+                float w[4];
+                if (btype == BCT_INTERIOR) f4_to(sN[(el * 3 + ff) * Np + vp], w);
+                const float pw = (btype == BCT_WALL) ? sPo[el * NpP + vm] : 0.f;
+                sNorm[el * NF + ff * Nfp + fi] = trace_norms_max(u, 1.0f / u[0], pw, btype, w, n1, n2, ph);
             }
         }
         __syncthreads();

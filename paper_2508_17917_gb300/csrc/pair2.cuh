@@ -7,7 +7,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
-#include "dg_device.cuh"
+#include "dg_stage.cuh"
 
 namespace dg {
 
@@ -63,6 +63,28 @@ __device__ __forceinline__ pf2 penalty_norm2(pf2 rho, pf2 v1, pf2 v2, pf2 e, flo
     const pf2 lam = sym3_max_eig2(s11, s12, s13, s22, s23, s33);
     const float lx = sqrtf(lam.v.x > 0.0f ? lam.v.x : 0.0f), ly = sqrtf(lam.v.y > 0.0f ? lam.v.y : 0.0f);
     return mk(ph.mu / rho.v.x * lx, ph.mu / rho.v.y * ly);
+}
+
+// Gbar_e's two terms at one face node (Sec. 2.2): the larger penalty norm of
+// the own trace u (1 / rho = ir, pressure pw) and of the other side, which is
+// the neighbour's trace w on an interior face, the far-field state, or the
+// wall ghost (rho+, v_w, pressure p+).  w is read on interior faces only.
+__device__ __forceinline__ float trace_norms_max(const float u[4], float ir, float pw, int bt, const float w[4],
+                                                 float n1, float n2, const Phys<float> &ph)
+{
+    float rb, vb1, vb2, eb;
+    if (bt == BCT_INTERIOR) {
+        const float iw = 1.0f / w[0];
+        rb = w[0]; vb1 = w[1] * iw; vb2 = w[2] * iw; eb = w[3] * iw;
+    } else if (bt == BCT_FARFIELD) {
+        const float iw = 1.0f / ph.Uinf[0];
+        rb = ph.Uinf[0]; vb1 = ph.Uinf[1] * iw; vb2 = ph.Uinf[2] * iw; eb = ph.Uinf[3] * iw;
+    } else {
+        rb = u[0]; vb1 = ph.vw1; vb2 = ph.vw2;
+        eb = (pw / ph.gm1 + 0.5f * u[0] * (ph.vw1 * ph.vw1 + ph.vw2 * ph.vw2)) * ir;
+    }
+    const pf2 nab = penalty_norm2(mk(u[0], rb), mk(u[1] * ir, vb1), mk(u[2] * ir, vb2), mk(u[3] * ir, eb), n1, n2, ph);
+    return fmaxf(nab.v.x, nab.v.y);
 }
 
 }  // namespace dg
