@@ -68,6 +68,7 @@ struct dg_ctx {
     bool bar_used = false;
     int source_kind = DG_SOURCE_NONE;
     dg::DevBuf<float> gimg;           // split [Dr; Ds] image of the tcgen05 gradient
+    bool gimg_ready = false;          // gimg holds the image
     dg::DevBuf<double> gtmp;          // host-output staging of dg_broken_gradient
     dg::VortexSource vortex{};         // DG_SOURCE_VORTEX parameters
     dg::DevBuf<double> src_xy;        // node coordinates for the vortex source
@@ -822,16 +823,21 @@ dg_status dg_broken_gradient(dg_ctx *c, double *gx, double *gy, int on_device, i
     a.wait_limit = 1u << 20;
     if (impl == 1) {
         const size_t nf = dg::grad_tc05_bimg_floats(c->prm.p);
-        if (c->gimg.n != nf) DG_CUDA(c, c->gimg.alloc(nf));
+        if (c->gimg.n != nf) {
+            DG_CUDA(c, c->gimg.alloc(nf));
+            c->gimg_ready = false;
+        }
         if (!c->bar_err.ptr) {
             DG_CUDA(c, c->bar_err.alloc(1));
             DG_CUDA(c, cudaMemset(c->bar_err.ptr, 0, sizeof(int)));
         }
         a.bimg = c->gimg.ptr;
+        a.upload_ops = !c->gimg_ready;   // the operators are fixed by p: one upload per context
         a.err = c->bar_err.ptr;        // reported by dg_barrier_status, as for fused steps
         c->bar_used = true;
     }
     DG_CUDA(c, dg::launch_broken_gradient(c->prm.p, impl, a, c->stream));
+    if (impl == 1) c->gimg_ready = true;
     c->launches += 1;
     if (!on_device) {
         DG_CUDA(c, cudaMemcpyAsync(gx, ox, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));

@@ -299,22 +299,25 @@ cudaError_t grad_tc05_p(const GradTc05Args &a, cudaStream_t st)
     using S = GradShape<P>;
     constexpr int Np = S::Np;
     if (a.K < 1) return cudaSuccess;
-    // the split [Dr; Ds] in the kernel's shared-memory layout: hi slices, then lo slices
-    std::vector<float> img(2 * S::KS * S::B_SLICE / 4, 0.f);
-    for (int n = 0; n < S::N; ++n) {
-        const int row = n % S::NR;
-        const double *A = (n < S::NR) ? a.Dr : a.Ds;
-        for (int kk = 0; kk < S::KP; ++kk) {
-            const double x = (row < Np && kk < Np) ? A[row * Np + kk] : 0.0;
-            const float hi = tf32_round_host(static_cast<float>(x));
-            const float lo = static_cast<float>(x - static_cast<double>(hi));
-            const size_t off = (kk >> 3) * S::B_SLICE + kmajor_off(n, kk & 7);
-            img[off / 4] = hi;
-            img[(S::KS * S::B_SLICE + off) / 4] = lo;
+    cudaError_t e;
+    if (a.upload_ops) {
+        // the split [Dr; Ds] in the kernel's shared-memory layout: hi slices, then lo slices
+        std::vector<float> img(2 * S::KS * S::B_SLICE / 4, 0.f);
+        for (int n = 0; n < S::N; ++n) {
+            const int row = n % S::NR;
+            const double *A = (n < S::NR) ? a.Dr : a.Ds;
+            for (int kk = 0; kk < S::KP; ++kk) {
+                const double x = (row < Np && kk < Np) ? A[row * Np + kk] : 0.0;
+                const float hi = tf32_round_host(static_cast<float>(x));
+                const float lo = static_cast<float>(x - static_cast<double>(hi));
+                const size_t off = (kk >> 3) * S::B_SLICE + kmajor_off(n, kk & 7);
+                img[off / 4] = hi;
+                img[(S::KS * S::B_SLICE + off) / 4] = lo;
+            }
         }
+        e = cudaMemcpyAsync(a.bimg, img.data(), img.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
     }
-    cudaError_t e = cudaMemcpyAsync(a.bimg, img.data(), img.size() * sizeof(float), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return e;
     // tensor map of the FP64 state: rows of 4 Np doubles, K rows; box of TE rows
     using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,

@@ -173,6 +173,7 @@ struct GradTc05Args {
     long long K;
     double *gx, *gy;            // [K][4][Np] outputs (device)
     float *bimg;                // device buffer of grad_tc05_bimg_floats(p) floats (impl 1)
+    bool upload_ops;            // (re)write the split operator image into bimg first (impl 1)
     int *err;                   // set to 1 if a bounded wait gave up (impl 1)
     unsigned wait_limit;
 };

@@ -94,3 +94,28 @@ def test_gradient_full_size_device_outputs(dg):
         torch.cuda.synchronize()
         assert np.all(field_err(gx.cpu().numpy(), rx) <= TOL[impl])
         assert np.all(field_err(gy.cpu().numpy(), ry) <= TOL[impl])
+
+
+@pytest.mark.parametrize("p,n", [(6, 75), (3, 131)])
+def test_gradient_many_tiles_ragged(dg, p, n):
+    """Hundreds of tiles with a ragged last one (K = 11,250 at p = 6, 34,322
+    at p = 3) into device outputs that start as NaN, so a row that no tile
+    writes fails; a second call reuses the operator image uploaded by the
+    first."""
+    import torch
+    mesh = dg_inputs.periodic_square(n)
+    P = oracle.Problem(mesh, p, mu=1e-3)
+    U = vortex(P, 1)
+    rx, ry = P.broken_gradient(U)
+    s = dg.Solver(mesh, p, "mixed", stream=stream(), mu=1e-3)
+    s.set_state(U)
+    gx = torch.full(U.shape, float("nan"), dtype=torch.float64, device="cuda")
+    gy = torch.full(U.shape, float("nan"), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        dg.dg_broken_gradient(s.ctx, gx, gy, 1)
+        dg.dg_barrier_status(s.ctx)
+        assert np.all(field_err(gx.cpu().numpy(), rx) <= TOL[1])
+        assert np.all(field_err(gy.cpu().numpy(), ry) <= TOL[1])
+        gx.fill_(float("nan"))
+        gy.fill_(float("nan"))
+
