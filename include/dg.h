@@ -110,6 +110,10 @@ dg_status dg_set_mesh(dg_ctx *ctx, int64_t Nv, const double *vx, const double *v
  * p <= 6), 0 = time every available shape (residual-only launches on the
  * current state) at the first time step after a mesh upload and keep the
  * fastest (the default).  The FP64 path has one kernel and accepts 0 and 1.
+ * The shapes round their FP32 arithmetic differently (all within the mixed
+ * path's tolerance), and the tuner's choice depends on timings, so two runs
+ * of the same input can differ in the last FP32 bits under variant 0: a
+ * fixed variant (1, 2 or 3) is the bit-reproducible mode.
  * Errors: DG_EINVAL (variant outside 0..3), DG_EUNSUPPORTED (2 or 3 on the
  * FP64 path, 2 with theta != 0). */
 dg_status dg_set_stage_variant(dg_ctx *ctx, int variant);

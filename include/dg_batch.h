@@ -78,7 +78,8 @@ int64_t dg_batch_kernel_launches(const dg_batch *b);
 
 /* Tile shape of the stage kernel per degree group (see dg_set_stage_variant):
  * 0 = time every available shape per group at the next dg_batch_run (the
- * default), 1, 2 or 3 = forced for every group (3: the tensor-core shape).
+ * default), 1, 2 or 3 = forced for every group (3: the tensor-core shape;
+ * a forced shape is the bit-reproducible mode, as for a single context).
  * Drops captured graphs.  Errors: DG_EINVAL. */
 dg_status dg_batch_set_stage_variant(dg_batch *b, int variant);
 
