@@ -803,8 +803,9 @@ def run_config3(args):
     out.update(workload="config 3: O-grid 120x170 (K=40800), p=4, Re=100, M=0.2, smoothed free-stream start",
                steps=args.config3_steps, dt=dt, t_end=dt * args.config3_steps, cfl=args.config3_cfl,
                forces_every=every)
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    np.savez(os.path.join(ROOT, "gpurun_out", "config3_histories.npz"), mixed=a, fp64=b)
+    if args.config3_out:
+        os.makedirs(os.path.dirname(os.path.abspath(args.config3_out)), exist_ok=True)
+        np.savez(args.config3_out, mixed=a, fp64=b)
     print(json.dumps(out))
 
 
@@ -893,6 +894,8 @@ def main():
                     help="long C_L / C_D histories of config 3 in both precisions (not the bench line)")
     ap.add_argument("--config3-steps", type=int, default=20000)
     ap.add_argument("--config3-cfl", type=float, default=2.0)
+    ap.add_argument("--config3-out", default=None, metavar="NPZ",
+                    help="also save the (t, C_D, C_L) histories of both precisions (--config3)")
     ap.add_argument("--record-traffic", default=None, metavar="CSV",
                     help="ncu raw-page CSV of one stage launch: write its DRAM bytes per DOF-stage")
     ap.add_argument("--record-k", type=int, default=2 * 512 * 512,
