@@ -411,9 +411,21 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
             if (bt != BCT_FARFIELD) {
                 const float4 *src = sN + (e * 3 + f) * UN;
                 const int row = (bt == BCT_INTERIOR) ? vp : vm;
-                float wr[4] = {0.f, 0.f, 0.f, 0.f}, ws[4] = {0.f, 0.f, 0.f, 0.f};
+                // fields in pairs (the two halves of a float4 record) with
+                // paired FMAs: (r0, r1) += (Dr, Dr) (u0, u1), and so on
+                float2 r01 = make_float2(0.f, 0.f), r23 = r01, s01 = r01, s23 = r01;
 #pragma unroll
-                for (int j = 0; j < Np; ++j) acc_rs(wr, ws, sD[row * S::DS + j], src[j]);
+                for (int j = 0; j < Np; ++j) {
+                    const float2 d = sD[row * S::DS + j];
+                    const float4 u = src[j];
+                    const float2 dr = make_float2(d.x, d.x), ds = make_float2(d.y, d.y);
+                    const float2 u01 = make_float2(u.x, u.y), u23 = make_float2(u.z, u.w);
+                    r01 = __ffma2_rn(dr, u01, r01);
+                    r23 = __ffma2_rn(dr, u23, r23);
+                    s01 = __ffma2_rn(ds, u01, s01);
+                    s23 = __ffma2_rn(ds, u23, s23);
+                }
+                const float wr[4] = {r01.x, r01.y, r23.x, r23.y}, ws[4] = {s01.x, s01.y, s23.x, s23.y};
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     go_x[c] = ng[G_RX] * wr[c] + ng[G_SX] * ws[c];
