@@ -43,11 +43,16 @@ __device__ __forceinline__ float cvt_d2f_trunc(double d)
     return __uint_as_float(f | (hi & 0x80000000u));
 }
 
-// r[c] += d.x * u[c], s[c] += d.y * u[c] for the four fields of one node
+// r[c] += d.x * u[c], s[c] += d.y * u[c] for the four fields of one node,
+// with paired FMAs over the field pairs (0, 1) and (2, 3)
 __device__ __forceinline__ void acc_rs(float r[4], float s[4], const float2 d, const float4 u)
 {
-    r[0] = fmaf(d.x, u.x, r[0]); r[1] = fmaf(d.x, u.y, r[1]); r[2] = fmaf(d.x, u.z, r[2]); r[3] = fmaf(d.x, u.w, r[3]);
-    s[0] = fmaf(d.y, u.x, s[0]); s[1] = fmaf(d.y, u.y, s[1]); s[2] = fmaf(d.y, u.z, s[2]); s[3] = fmaf(d.y, u.w, s[3]);
+    const float2 dr = make_float2(d.x, d.x), ds = make_float2(d.y, d.y);
+    const float2 u01 = make_float2(u.x, u.y), u23 = make_float2(u.z, u.w);
+    const float2 r01 = __ffma2_rn(dr, u01, make_float2(r[0], r[1])), r23 = __ffma2_rn(dr, u23, make_float2(r[2], r[3]));
+    const float2 s01 = __ffma2_rn(ds, u01, make_float2(s[0], s[1])), s23 = __ffma2_rn(ds, u23, make_float2(s[2], s[3]));
+    r[0] = r01.x; r[1] = r01.y; r[2] = r23.x; r[3] = r23.y;
+    s[0] = s01.x; s[1] = s01.y; s[2] = s23.x; s[3] = s23.y;
 }
 
 __device__ __forceinline__ void cp_async16(unsigned dst, const void *src)
