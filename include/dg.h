@@ -147,14 +147,18 @@ int dg_overint_degree(int p);
  * Errors: DG_EUNSUPPORTED (FP64 or theta != 0), DG_ECUDA. */
 dg_status dg_set_fused_steps(dg_ctx *ctx, int on);
 
-/* Waits of about 100 ns before a fused step's barrier gives up (default
- * 2^24, about 1.7 s; 0 makes every wait give up at once). */
+/* Waits of about 100 ns before a bounded device wait gives up: a fused
+ * step's grid barrier, and the tensor-core stage kernel's waits for the bulk
+ * copies of its operator table and of each warp's own element records
+ * (default 2^24, about 1.7 s; 0 makes every wait give up unless its event
+ * has already happened). */
 dg_status dg_set_barrier_limit(dg_ctx *ctx, uint32_t waits);
 
 /* DG_ETIMEOUT if a bounded device wait since the last check gave up -- a
- * grid barrier of a fused step, or a wait of the tcgen05 gradient kernel of
- * dg_broken_gradient -- (then clears the flag), DG_OK otherwise.
- * Synchronises when such kernels ran.  Errors: DG_EINVAL, DG_ECUDA. */
+ * grid barrier of a fused step, a copy wait of the tensor-core stage kernel,
+ * or a wait of the tcgen05 gradient kernel of dg_broken_gradient -- (then
+ * clears the flag), DG_OK otherwise.  Synchronises when such kernels ran.
+ * Errors: DG_EINVAL, DG_ECUDA. */
 dg_status dg_barrier_status(dg_ctx *ctx);
 
 /* Copy the state in ([K][4][Np] FP64; host pointer if on_device == 0, device
@@ -162,8 +166,11 @@ dg_status dg_barrier_status(dg_ctx *ctx);
  * Errors: DG_EINVAL (null, no mesh yet), DG_ECUDA. */
 dg_status dg_set_state(dg_ctx *ctx, const double *U, int on_device);
 
-/* Copy the state out ([K][4][Np] FP64).  Host output synchronises the stream.
- * Errors: DG_EINVAL, DG_ECUDA. */
+/* Copy the state out ([K][4][Np] FP64).  Host output synchronises the stream
+ * and reports a bounded device wait that gave up since the last check
+ * (DG_ETIMEOUT: the state is not valid); device output stays asynchronous
+ * (after a fused step it checks the barrier flag first, which synchronises).
+ * Errors: DG_EINVAL, DG_ETIMEOUT, DG_ECUDA. */
 dg_status dg_get_state(dg_ctx *ctx, double *U, int on_device);
 
 /* dU/dt = M^-1 R(t, U) of Eq. dg_on_K for the current state, with mesh

@@ -249,6 +249,8 @@ dg_status enqueue_step(dg_batch *b, double cfl, double *hist, int rows)
             sp.mode = dg::STAGE_UPDATE;
             sp.first_stage = (s == 0) ? 1 : 0;
             sp.cases = b->dcases.ptr;
+            sp.bar_err = b->bar_err.ptr;          // grid barriers and copy waits report here
+            sp.bar_limit = b->bar_limit;
             if (b->fused) {
                 // the five stages in one cooperative launch (grid barriers between stages)
                 sp.tiles = (g.variant == 3) ? g.tiles3.ptr : (g.variant == 2) ? g.tiles2.ptr : g.tiles.ptr;
@@ -266,8 +268,6 @@ dg_status enqueue_step(dg_batch *b, double cfl, double *hist, int rows)
                     sp.B5[i] = dg::kRkB[i];
                 }
                 sp.bar = g.bar.ptr;
-                sp.bar_err = b->bar_err.ptr;
-                sp.bar_limit = b->bar_limit;
                 B_CUDA(b, cudaMemsetAsync(g.bar.ptr, 0, 2 * sizeof(unsigned), b->stream));
                 if (g.variant == 3)
                     B_CUDA(b, dg::launch_stage_tc(g.p, true, true, g.fshape, sp, ph32, b->stream));
@@ -341,6 +341,8 @@ dg_status tune_groups(dg_batch *b)
             sp.mode = dg::STAGE_RHS_ONLY;
             sp.first_stage = 1;
             sp.cases = b->dcases.ptr;
+            sp.bar_err = b->bar_err.ptr;
+            sp.bar_limit = b->bar_limit;
             float ms = 0.f;
             for (int rep = 0; rep < 5; ++rep) {
                 if (rep == 2) B_CUDA(b, cudaEventRecord(e0, b->stream));
@@ -578,7 +580,9 @@ dg_status dg_batch_create(const dg_params *common, int ncases, const dg_case *ca
     chk(b->wseg.alloc(wseg.size()));
     chk(b->counter.alloc(1));
     chk(b->ticket.alloc(1));
+    chk(b->bar_err.alloc(1));
     chk(cudaMemset(b->ticket.ptr, 0, sizeof(unsigned)));
+    chk(cudaMemset(b->bar_err.ptr, 0, sizeof(int)));
     if (e != cudaSuccess) return bail(DG_ECUDA);
     chk(cudaMemcpy(b->dcases.ptr, b->init.data(), ncases * sizeof(dg::BatchCase), cudaMemcpyHostToDevice));
     chk(cudaMemcpy(b->seg.ptr, seg.data(), seg.size() * sizeof(long long), cudaMemcpyHostToDevice));
@@ -644,10 +648,9 @@ dg_status dg_batch_set_fused_steps(dg_batch *b, int on)
 {
     if (!b) return DG_EINVAL;
     b->err.clear();
-    if (on && !b->bar_err.ptr) {
-        B_CUDA(b, b->bar_err.alloc(1));
-        B_CUDA(b, cudaMemset(b->bar_err.ptr, 0, sizeof(int)));
+    if (on) {
         for (auto &g : b->groups) {
+            if (g.bar.ptr) continue;
             B_CUDA(b, g.bar.alloc(2));
             B_CUDA(b, cudaMemset(g.bar.ptr, 0, 2 * sizeof(unsigned)));
         }
@@ -801,12 +804,14 @@ dg_status dg_batch_run(dg_batch *b, double cfl, int nsteps, int use_graph, doubl
         }
     }
     B_CUDA(b, cudaStreamSynchronize(b->stream));
-    if (b->fused) {
+    {
         int e = 0;
         B_CUDA(b, cudaMemcpy(&e, b->bar_err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
         if (e) {
             B_CUDA(b, cudaMemset(b->bar_err.ptr, 0, sizeof(int)));
-            return bfail(b, DG_ETIMEOUT, "a grid barrier of a fused step gave up waiting; the states are not valid");
+            return bfail(b, DG_ETIMEOUT,
+                         "a bounded device wait gave up (a fused step's grid barrier or a stage kernel's copy "
+                         "wait); the states are not valid");
         }
     }
     std::vector<dg::BatchCase> h(b->cases.size());

@@ -66,6 +66,7 @@ struct dg_ctx {
     dg::DevBuf<int> bar_err;
     unsigned bar_limit = 1u << 24;
     bool bar_used = false;
+    bool copy_used = false;           // a stage kernel with bounded copy waits ran (reported where the API synchronises anyway)
     int source_kind = DG_SOURCE_NONE;
     dg::DevBuf<float> gimg;           // split [Dr; Ds] image of the tcgen05 gradient
     bool gimg_ready = false;          // gimg holds the image
@@ -98,6 +99,10 @@ struct dg_ctx {
 };
 
 namespace {
+
+const char *const kWaitGaveUp =
+    "a bounded device wait gave up (a fused step's grid barrier or a stage kernel's copy wait: "
+    "the state is not valid; or the tcgen05 gradient kernel: its output is not valid)";
 
 dg_status fail(dg_ctx *c, dg_status st, const std::string &msg)
 {
@@ -210,8 +215,13 @@ dg_status run_stage(dg_ctx *c, int s, double t, double dt, const double vw[2], i
     } else {
         sp.geo = c->geo32.ptr;
         sp.ops = (c->shape.variant == 3) ? static_cast<const void *>(c->tcfrag.ptr) : c->ops32.ptr;
-        if (c->shape.variant == 3)
+        if (c->shape.variant == 3) {
+            // its bounded copy waits report through the barrier flag
+            sp.bar_err = c->bar_err.ptr;
+            sp.bar_limit = c->bar_limit;
+            c->copy_used = true;
             e = dg::launch_stage_tc(c->prm.p, false, false, c->shape, sp, make_phys<float>(c->prm, vw), c->stream);
+        }
         else if (c->shape.variant == 2)
             e = dg::launch_stage_mixed2(c->prm.p, false, c->shape, sp, make_phys<float>(c->prm, vw), c->stream);
         else
@@ -298,12 +308,13 @@ dg_status dg_create(const dg_params *params, void *cuda_stream, dg_ctx **out)
     std::vector<float> o32(o64.begin(), o64.end());
     if (c->ops64.alloc(o64.size()) != cudaSuccess || c->ops32.alloc(o32.size()) != cudaSuccess ||
         c->Dr64.alloc(Np * Np) != cudaSuccess || c->Ds64.alloc(Np * Np) != cudaSuccess ||
-        c->fmask.alloc(NF) != cudaSuccess || c->flag.alloc(1) != cudaSuccess ||
+        c->fmask.alloc(NF) != cudaSuccess || c->flag.alloc(1) != cudaSuccess || c->bar_err.alloc(1) != cudaSuccess ||
         c->scal.alloc(4) != cudaSuccess || c->wface.alloc(c->ops.Nfp) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return DG_ECUDA;
     }
+    cudaMemset(c->bar_err.ptr, 0, sizeof(int));
     cudaMemcpy(c->ops64.ptr, o64.data(), o64.size() * sizeof(double), cudaMemcpyHostToDevice);
     cudaMemcpy(c->ops32.ptr, o32.data(), o32.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (dg::stage_tc_supported(p.p)) {
@@ -363,9 +374,7 @@ dg_status dg_set_fused_steps(dg_ctx *c, int on)
         return fail(c, DG_EUNSUPPORTED, "fused steps use the mixed-precision IIP kernels");
     if (on && !c->bar.ptr) {
         DG_CUDA(c, c->bar.alloc(2));
-        DG_CUDA(c, c->bar_err.alloc(1));
         DG_CUDA(c, cudaMemset(c->bar.ptr, 0, 2 * sizeof(unsigned)));
-        DG_CUDA(c, cudaMemset(c->bar_err.ptr, 0, sizeof(int)));
     }
     c->fused = on != 0;
     return DG_OK;
@@ -382,16 +391,15 @@ dg_status dg_barrier_status(dg_ctx *c)
 {
     if (!c) return DG_EINVAL;
     c->err.clear();
-    if (!c->bar_used) return DG_OK;
+    if (!c->bar_used && !c->copy_used) return DG_OK;
     int e = 0;
     DG_CUDA(c, cudaMemcpyAsync(&e, c->bar_err.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     DG_CUDA(c, cudaStreamSynchronize(c->stream));
     c->bar_used = false;
+    c->copy_used = false;
     if (e) {
         DG_CUDA(c, cudaMemset(c->bar_err.ptr, 0, sizeof(int)));
-        return fail(c, DG_ETIMEOUT,
-                    "a bounded device wait gave up (a fused step's grid barrier: the state is not valid; "
-                    "or the tcgen05 gradient kernel: its output is not valid)");
+        return fail(c, DG_ETIMEOUT, kWaitGaveUp);
     }
     return DG_OK;
 }
@@ -534,14 +542,28 @@ dg_status dg_get_state(dg_ctx *c, double *U, int on_device)
 {
     if (!c) return DG_EINVAL;
     c->err.clear();
-    {
+    if (on_device && c->bar_used) {
         dg_status bs = dg_barrier_status(c);
         if (bs != DG_OK) return bs;
     }
     if (!U || c->K < 1) return fail(c, DG_EINVAL, "null state or no mesh");
+    // host output: the error flag of the bounded device waits comes back with
+    // the state, under the one synchronisation (device output stays
+    // asynchronous after plain stage launches)
+    const bool check = !on_device && (c->bar_used || c->copy_used);
+    int e = 0;
+    if (check) DG_CUDA(c, cudaMemcpyAsync(&e, c->bar_err.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     DG_CUDA(c, cudaMemcpyAsync(U, c->cur(), ndof(c) * sizeof(double),
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     if (!on_device) DG_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (check) {
+        c->bar_used = false;
+        c->copy_used = false;
+        if (e) {
+            DG_CUDA(c, cudaMemset(c->bar_err.ptr, 0, sizeof(int)));
+            return fail(c, DG_ETIMEOUT, kWaitGaveUp);
+        }
+    }
     return DG_OK;
 }
 

@@ -6,9 +6,16 @@
 // stage of Algorithm 1, FP32 arithmetic with FP64 state, pressure recovery
 // and registers.  What changes is how the work is laid out:
 //
-// * Every warp owns a tile of WE = 2 elements from load to store.  It stages
-//   its own inputs with cp.async and synchronises with __syncwarp only, so the
-//   warps of a block run independently (no block barrier in the loop).
+// * Every warp owns a tile of WE = 2 elements from load to store and
+//   synchronises with __syncwarp only, so the warps of a block run
+//   independently (no block barrier in the loop).  It gathers its elements'
+//   neighbours with 16-byte cp.async by index; its own contiguous records
+//   (FP32 state, pressure, geometry, FP64 registers) arrive by bulk copies
+//   of the tensor memory accelerator on two per-warp mbarriers from p = 5 on
+//   (cp.async below: measured).  The block's operator fragments (Dr, Ds,
+//   LIFT) arrive by one bulk copy on an mbarrier in the prologue.  Every
+//   mbarrier wait is bounded; one that gives up raises the barrier error
+//   flag and the warp skips its remaining tiles.
 // * The contractions -- broken gradient [Dr; Ds] U, divergence Dr Fr + Ds Fs
 //   and lift LIFT (Fscale dH), all batched over the tile's elements as
 //   (16 x 16)(16 x 8) products -- run as mma.sync m16n8k8 TF32 with FP32
@@ -74,6 +81,10 @@ struct ShapeTC {
     static constexpr int NENT_ALL = NENT + 2 * MT * KD;          // with Wr, Ws
     static constexpr int NFRAG_ALL = NENT_ALL * 64;              // float4 in the table
     static constexpr bool FRAG_SMEM = MT == 1;    // staged in shared memory (else read through L1)
+    // the warp's own element records by bulk copies (else cp.async per
+    // lane): measured 3.5 % faster per step at p = 6 and 0.3 % at p = 5, 0.8 %
+    // slower at p = 4 on 128^2 quads (neutral on 512^2), so from p = 5 on
+    static constexpr bool TILE_BULK = MT > 1;
 };
 
 // operator table: the MMA fragments (ShapeTC<P>::NFRAG_ALL float4), then
@@ -89,7 +100,8 @@ struct TcLayout {
     static constexpr size_t hFrag = 0;                                      // float4 [NFRAG] if FRAG_SMEM
     static constexpr size_t hFm = hFrag + (S::FRAG_SMEM ? sizeof(float4) * NFRAG : 0);      // int [NF]
     static constexpr size_t hD = hFm + al(sizeof(int) * NF);                // float2 [Np][DS]: (Dr, Ds)
-    static constexpr size_t header = hD + al(sizeof(float2) * Np * S::DS);
+    static constexpr size_t hBar = hD + al(sizeof(float2) * Np * S::DS);   // mbarrier of the operator copy
+    static constexpr size_t header = hBar + 16;
     // one region per warp
     static constexpr size_t oConn = 0;                                      // int4 [WE]
     static constexpr size_t oGeo = oConn + al(16 * WE);                     // float [WE][16]
@@ -103,9 +115,45 @@ struct TcLayout {
     static constexpr size_t oF = oK1 + al(8 * WE * 4 * Np);                 // float [WE][FS]: node j: Fr[4], Fs[4]
     static constexpr size_t oDH = oF + al(4 * WE * S::FS);                  // float [WE][HS]: slot r: Fscale dH[4]
     static constexpr size_t oTH = oDH + al(4 * WE * S::HS);                 // theta: float [2][WE][HS]: x, y vectors
-    static constexpr size_t warp = oTH + (TH ? al(4 * 2 * WE * S::HS) : 0);
+    static constexpr size_t oBar = oTH + (TH ? al(4 * 2 * WE * S::HS) : 0);  // mbarriers: own tile, FP64 registers
+    static constexpr size_t warp = oBar + 16;
     static constexpr size_t bytes = header + S::NW * warp;
 };
+
+// Bulk copies (the tensor memory accelerator's 1-D form) into shared memory,
+// completing on an mbarrier: the warp's own tile and the operator table.
+__device__ __forceinline__ void mbar_init1(unsigned bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// 16-byte aligned addresses, a multiple of 16 bytes
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// bounded wait for phase `parity` of an mbarrier; false if it gave up
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, unsigned limit)
+{
+    for (unsigned it = 0;; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (it >= limit) return false;
+        __nanosleep(100);
+    }
+}
 
 __device__ __forceinline__ void mma_tf32(float c[4], const float4 &a, float b0, float b1)
 {
@@ -169,18 +217,40 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
     int *sFm = reinterpret_cast<int *>(smem_raw + L::hFm);
     const float2 *sD = reinterpret_cast<const float2 *>(smem_raw + L::hD);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const unsigned sbase = static_cast<unsigned>(__cvta_generic_to_shared(smem_raw));
+    const unsigned barOps = sbase + unsigned(L::hBar);
     {
-        // operator fragments (built on the host in fragment order), (Dr, Ds)
-        // rows, face node table
-        float4 *dst = reinterpret_cast<float4 *>(smem_raw + L::hFrag);
-        if constexpr (S::FRAG_SMEM)
-            for (int i = tid; i < L::NFRAG; i += S::NT) dst[i] = gFrag[i];
+        // the mbarriers; the operator fragments (built on the host in
+        // fragment order) by one bulk copy; (Dr, Ds) rows and the face node
+        // table (strided rows) by the threads
+        if (tid == 0) {
+            mbar_init1(barOps);
+            for (int w = 0; w < S::NW; ++w) {
+                mbar_init1(sbase + unsigned(L::header + w * L::warp + L::oBar));
+                mbar_init1(sbase + unsigned(L::header + w * L::warp + L::oBar + 8));
+            }
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            if constexpr (S::FRAG_SMEM) {
+                mbar_expect(barOps, unsigned(sizeof(float4) * L::NFRAG));
+                bulk_g2s(sbase + unsigned(L::hFrag), gFrag, unsigned(sizeof(float4) * L::NFRAG), barOps);
+            }
+        }
         const float2 *dtab = reinterpret_cast<const float2 *>(gFrag + S::NFRAG_ALL);
         float2 *dD = reinterpret_cast<float2 *>(smem_raw + L::hD);
         for (int i = tid; i < Np * Np; i += S::NT) dD[(i / Np) * S::DS + i % Np] = dtab[i];
         for (int i = tid; i < NF; i += S::NT) sFm[i] = sp.fmask[i];
     }
     __syncthreads();
+    // a copy wait that gives up marks the error flag; the warp (or, here,
+    // the block) then skips its tiles but still meets every grid barrier
+    bool failed = false;
+    if constexpr (S::FRAG_SMEM) {
+        failed = !__syncthreads_and(mbar_wait_bounded(barOps, 0u, sp.bar_limit));
+        if (failed && tid == 0) {
+            if (sp.bar_err) atomicExch(sp.bar_err, 1);
+            mbar_wait_bounded(barOps, 0u, sp.bar_limit);      // the copy still lands in this block's memory
+        }
+    }
     pdl_wait_then_release();
     // fragment `h` (0 hi, 1 lo) of entry `ent` of the operator table
     auto frag = [&](int ent, int h) -> float4 {
@@ -195,6 +265,19 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
 
     unsigned char *wb = smem_raw + L::header + wid * L::warp;
     const unsigned wsh = static_cast<unsigned>(__cvta_generic_to_shared(wb));
+    const unsigned barA = wsh + unsigned(L::oBar), barB = barA + 8u;
+    unsigned wit = 0;        // tiles this warp has started: the parity of its mbarriers' phases
+    // a bounded copy wait gave up: raise the error flag, wait (bounded) for
+    // the copies still landing in this warp's shared memory, skip the rest
+    auto copy_wait_failed = [&](unsigned a, unsigned b, unsigned ph_) {
+        failed = true;
+        if (lane == 0) {
+            if (sp.bar_err) atomicExch(sp.bar_err, 1);
+            mbar_wait_bounded(a, ph_, sp.bar_limit);
+            mbar_wait_bounded(b, ph_, sp.bar_limit);
+        }
+        __syncwarp();
+    };
     int4 *sConn = reinterpret_cast<int4 *>(wb + L::oConn);
     const float *sGeo = reinterpret_cast<const float *>(wb + L::oGeo);
     const float *sNGeo = reinterpret_cast<const float *>(wb + L::oNGeo);
@@ -245,18 +328,40 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
             ph.vw2 = static_cast<float>(cs.vb);
             dtr = static_cast<float>(cs.dt);
         }
+        if (failed) continue;                    // a copy wait gave up: the flag is set
         if (lane < ne) sConn[lane] = sp.conn[k0 + lane];
         __syncwarp();
-        // ---- group A: FP32 state, pressure and geometry of the tile and of the
-        // three face neighbours of every element (a boundary face names its own
-        // element, so its slot holds the element itself)
-        for (int c = lane; c < ne * Np; c += 32) {
-            const int e = c / Np, j = c - (c / Np) * Np;
-            cp_async16(wsh + L::oU + 16u * (e * US + j), sp.Sin + (k0 + e) * Np + j);
+        // ---- the tile's own records, contiguous in memory -- A: FP32 state,
+        // pressure and geometry; B: the FP64 registers, needed only by the
+        // update.  TILE_BULK: bulk copies issued by lane 0 on the warp's two
+        // mbarriers (one copy per element for the state: the staged rows are
+        // padded); else 16-byte cp.async per lane in two commit groups.
+        const unsigned par = wit & 1u;
+        ++wit;
+        if constexpr (S::TILE_BULK) {
+            if (lane == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect(barA, unsigned(ne) * (16u * Np + 4u * NpP + 64u));
+                for (int e = 0; e < ne; ++e)
+                    bulk_g2s(wsh + L::oU + 16u * (e * US), sp.Sin + (k0 + e) * Np, 16u * Np, barA);
+                bulk_g2s(wsh + L::oPo, sp.Pin + k0 * NpP, 4u * NpP * ne, barA);
+                bulk_g2s(wsh + L::oGeo, geo + k0 * 16, 64u * ne, barA);
+                mbar_expect(barB, unsigned(ne) * 32u * Np * (need_k1 ? 2u : 1u));
+                bulk_g2s(wsh + L::oRaw, sp.K0in + k0 * 4 * Np, 32u * Np * ne, barB);
+                if (need_k1) bulk_g2s(wsh + L::oK1, sp.K1 + k0 * 4 * Np, 32u * Np * ne, barB);
+            }
+        } else {
+            for (int c = lane; c < ne * Np; c += 32) {
+                const int e = c / Np, j = c - (c / Np) * Np;
+                cp_async16(wsh + L::oU + 16u * (e * US + j), sp.Sin + (k0 + e) * Np + j);
+            }
+            for (int c = lane; c < ne * (NpP / 4); c += 32)
+                cp_async16(wsh + L::oPo + 16u * c, sp.Pin + k0 * NpP + 4 * c);
+            for (int c = lane; c < ne * 4; c += 32) cp_async16(wsh + L::oGeo + 16u * c, geo + k0 * 16 + 4 * c);
         }
-        for (int c = lane; c < ne * (NpP / 4); c += 32)
-            cp_async16(wsh + L::oPo + 16u * c, sp.Pin + k0 * NpP + 4 * c);
-        for (int c = lane; c < ne * 4; c += 32) cp_async16(wsh + L::oGeo + 16u * c, geo + k0 * 16 + 4 * c);
+        // ---- the three face neighbours of every element (a boundary face
+        // names its own element, so its slot holds the element itself):
+        // gathers by index, 16-byte cp.async per lane
         {
             // LPS lanes per neighbour slot: one connectivity lookup per lane
             constexpr int LPS = 32 / (3 * WE);
@@ -274,15 +379,26 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
             }
         }
         asm volatile("cp.async.commit_group;\n" ::);
-        // ---- group B: the FP64 registers, needed only by the update
-        for (int c = lane; c < ne * 2 * Np; c += 32) cp_async16(wsh + L::oRaw + 16u * c, sp.K0in + k0 * 4 * Np + 2 * c);
-        if (need_k1)
-            for (int c = lane; c < ne * 2 * Np; c += 32) cp_async16(wsh + L::oK1 + 16u * c, sp.K1 + k0 * 4 * Np + 2 * c);
-        asm volatile("cp.async.commit_group;\n" ::);
-        if constexpr (TH)
-            asm volatile("cp.async.wait_group 0;\n" ::);   // the face pass forms FP64 jumps
-        else
-            asm volatile("cp.async.wait_group 1;\n" ::);
+        if constexpr (S::TILE_BULK) {
+            asm volatile("cp.async.wait_group 0;\n" ::);
+            bool ok = mbar_wait_bounded(barA, par, sp.bar_limit);
+            if constexpr (TH) ok = ok && mbar_wait_bounded(barB, par, sp.bar_limit);   // FP64 jumps in the face pass
+            if (!__all_sync(0xffffffffu, ok)) {
+                copy_wait_failed(barA, barB, par);
+                continue;
+            }
+        } else {
+            for (int c = lane; c < ne * 2 * Np; c += 32)
+                cp_async16(wsh + L::oRaw + 16u * c, sp.K0in + k0 * 4 * Np + 2 * c);
+            if (need_k1)
+                for (int c = lane; c < ne * 2 * Np; c += 32)
+                    cp_async16(wsh + L::oK1 + 16u * c, sp.K1 + k0 * 4 * Np + 2 * c);
+            asm volatile("cp.async.commit_group;\n" ::);
+            if constexpr (TH)
+                asm volatile("cp.async.wait_group 0;\n" ::);   // the face pass forms FP64 jumps
+            else
+                asm volatile("cp.async.wait_group 1;\n" ::);
+        }
         __syncwarp();
 
         // ---- V: broken gradient (MMA) and total flux of every volume node
@@ -512,7 +628,14 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
                 }
             }
         }
-        asm volatile("cp.async.wait_group 0;\n" ::);
+        if constexpr (S::TILE_BULK && !TH) {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(barB, par, sp.bar_limit))) {
+                copy_wait_failed(barA, barB, par);
+                continue;
+            }
+        } else if constexpr (!S::TILE_BULK) {
+            asm volatile("cp.async.wait_group 0;\n" ::);
+        }
         __syncwarp();
 
         // ---- U: R = -(Dr Fr + Ds Fs) + LIFT (Fscale dH) (MMA), then the stage

@@ -114,3 +114,37 @@ def test_fused_rejected_on_fp64(dg):
     with pytest.raises(dg.DGError) as e:
         s.set_fused(True)
     assert e.value.status == -6
+
+
+def test_tc_copy_wait_limit_reports_or_completes(dg):
+    """The tensor-core stage kernel stages its operator table and each warp's
+    own element records with bulk copies on mbarriers, and every wait on them
+    is bounded by the same limit as the grid barriers.  With a zero limit a
+    wait gives up unless its copy has already landed, so the run either
+    completes with the reference state or reports DG_ETIMEOUT from the
+    synchronising state read; either way nothing hangs, and with the limit
+    restored the context reproduces the reference bit for bit."""
+    mesh, p, kw, vw = vortex_case()
+    ref = dg.Solver(mesh, p, "mixed", stream=stream(), **kw)
+    ref.set_variant(3)
+    U0 = start(ref, kw)
+    ref.set_state(U0)
+    dt = ref.dt(0.3)
+    ref.steps(0.0, dt, 2)
+    want = ref.get_state()
+
+    s = dg.Solver(mesh, p, "mixed", stream=stream(), **kw)
+    s.set_variant(3)
+    s.set_state(U0)
+    dg.dg_set_barrier_limit(s.ctx, 0)
+    s.steps(0.0, dt, 2)
+    try:
+        got = s.get_state()
+        assert np.array_equal(got, want)
+    except dg.DGError as e:
+        assert e.status == -5
+    dg.dg_barrier_status(s.ctx)                  # nothing left to report
+    dg.dg_set_barrier_limit(s.ctx, 1 << 24)
+    s.set_state(U0)
+    s.steps(0.0, dt, 2)
+    assert np.array_equal(s.get_state(), want)
