@@ -21,7 +21,13 @@
 //     A_hi B_lo and A_lo B_hi into one FP32 accumulator in tensor memory
 //     (128 lanes x N columns), then tcgen05.commit to an mbarrier.
 //   * Warp w reads lanes 32 w .. 32 w + 31 (its rows) with tcgen05.ld and
-//     applies the metric terms: Ux = rx Ur + sx Us, Uy = ry Ur + sy Us.
+//     applies the metric terms: Ux = rx Ur + sx Us, Uy = ry Ur + sy Us.  The
+//     rows are written to shared memory in the output layout (gx over the
+//     consumed state tile, gy over the operand slices) and one thread stores
+//     both tiles with two bulk copies (cp.async.bulk shared -> global); row
+//     stores by every thread, 120 bytes apart, left the store path issuing
+//     one 32-byte sector per lane.  Outputs that are not 16-byte aligned
+//     take the row stores.
 // Every wait is bounded; a wait that gives up raises the error flag and the
 // CTA skips the rest of its work (the tensor memory it holds is released
 // only once the product it issued has completed).
@@ -64,6 +70,7 @@ struct GradShape {
     static constexpr size_t oBar = oBlo + KS * B_SLICE;   // two mbarriers (8 B each), then the tmem slot
     static constexpr size_t bytes = oBar + 32 + 1024;    // + room to align the base
     static_assert(N % 16 == 0 && N <= 256, "tcgen05 M = 128 needs N a multiple of 16");
+    static_assert(2 * KS * A_SLICE >= TILE, "the gy tile is staged over the operand slices");
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
@@ -119,7 +126,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsign
 template <int P>
 __global__ void __launch_bounds__(NTH, 1)
 grad_tc05_kernel(const __grid_constant__ CUtensorMap tmap, const float *bimg, const double *geo, long long K,
-                 double *gx, double *gy, int *err, unsigned wait_limit)
+                 double *gx, double *gy, int *err, unsigned wait_limit, int bulk_out)
 {
     using S = GradShape<P>;
     constexpr int Np = S::Np, NR = S::NR, KS = S::KS;
@@ -236,16 +243,37 @@ grad_tc05_kernel(const __grid_constant__ CUtensorMap tmap, const float *bimg, co
             for (int q = 0; q < 16; ++q) d[c0 + q] = __uint_as_float(r[q]);
         }
         const long long k = k0 + e;
+        // bulk_out: the rows go to shared memory in the output layout -- gx
+        // over the consumed state tile, gy over the operand slices, whose
+        // product has completed -- and leave by two bulk copies; otherwise
+        // (outputs not 16-byte aligned) every thread stores its row
+        double *ox = bulk_out ? reinterpret_cast<double *>(sm + S::oTile) + (e * 4 + c) * Np : gx + (k * 4 + c) * Np;
+        double *oy = bulk_out ? reinterpret_cast<double *>(sm + S::oAhi) + (e * 4 + c) * Np : gy + (k * 4 + c) * Np;
         if (k < K) {
             // metric terms in FP32 (the products are FP32-accurate), widened exactly
             const double *g = geo + k * 16;
             const float rx = cvt_d2f(g[G_RX]), ry = cvt_d2f(g[G_RY]), sx = cvt_d2f(g[G_SX]), sy = cvt_d2f(g[G_SY]);
-            double *ox = gx + (k * 4 + c) * Np, *oy = gy + (k * 4 + c) * Np;
 #pragma unroll
             for (int j = 0; j < Np; ++j) {
                 const float ur = d[j], us = d[NR + j];
                 ox[j] = cvt_f2d(fmaf(rx, ur, sx * us));
                 oy[j] = cvt_f2d(fmaf(ry, ur, sy * us));
+            }
+        }
+        if (bulk_out) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                const unsigned nb = static_cast<unsigned>((K - k0) < TE ? (K - k0) : TE) * 4u * Np * 8u;
+                asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gx + k0 * 4 * Np),
+                             "r"(smem_u32(sm + S::oTile)), "r"(nb)
+                             : "memory");
+                asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gy + k0 * 4 * Np),
+                             "r"(smem_u32(sm + S::oAhi)), "r"(nb)
+                             : "memory");
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                // the copies have read shared memory before the CTA releases it
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
             }
         }
     } else if (tid == 0) {
@@ -343,7 +371,10 @@ cudaError_t grad_tc05_p(const GradTc05Args &a, cudaStream_t st)
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(S::bytes));
     if (e != cudaSuccess) return e;
     const unsigned grid = static_cast<unsigned>((a.K + TE - 1) / TE);
-    kern<<<grid, NTH, S::bytes, st>>>(tmap, a.bimg, a.geo, a.K, a.gx, a.gy, a.err, a.wait_limit);
+    // tile stores by bulk copies need 16-byte aligned outputs (any cudaMalloc
+    // or torch allocation; tile offsets are multiples of 1 KB)
+    const int bulk_out = ((reinterpret_cast<uintptr_t>(a.gx) | reinterpret_cast<uintptr_t>(a.gy)) & 15u) == 0;
+    kern<<<grid, NTH, S::bytes, st>>>(tmap, a.bimg, a.geo, a.K, a.gx, a.gy, a.err, a.wait_limit, bulk_out);
     return cudaGetLastError();
 }
 

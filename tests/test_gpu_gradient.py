@@ -119,3 +119,24 @@ def test_gradient_many_tiles_ragged(dg, p, n):
         gx.fill_(float("nan"))
         gy.fill_(float("nan"))
 
+
+
+def test_gradient_unaligned_device_outputs(dg):
+    """Device outputs that start 8 bytes past a 16-byte boundary cannot take
+    the bulk tile stores; the kernel stores rows instead, with the same
+    results."""
+    import torch
+    mesh = dg_inputs.periodic_square(5)
+    P = oracle.Problem(mesh, 4, mu=1e-3)
+    U = vortex(P, 3)
+    rx, ry = P.broken_gradient(U)
+    s = dg.Solver(mesh, 4, "mixed", stream=stream(), mu=1e-3)
+    s.set_state(U)
+    n = U.size
+    buf = torch.full((2 * n + 2,), float("nan"), dtype=torch.float64, device="cuda")
+    gx, gy = buf[1:n + 1], buf[n + 2:]               # 8-byte and 16-byte aligned
+    assert gx.data_ptr() % 16 == 8
+    dg.dg_broken_gradient(s.ctx, gx, gy, 1)
+    dg.dg_barrier_status(s.ctx)
+    assert np.all(field_err(gx.cpu().numpy().reshape(U.shape), rx) <= TOL[1])
+    assert np.all(field_err(gy.cpu().numpy().reshape(U.shape), ry) <= TOL[1])
