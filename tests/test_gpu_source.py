@@ -9,6 +9,10 @@ G blocks of Sec. 2.1.
   the increment U_n - U_0 per field;
 * the benchmark workload (128 x 128 quads, p = 4, K = 32,768) with the
   source for 20 steps, state and increment per field, both precisions.
+
+The mixed path runs twice, with the single-node and with the tensor-core
+tile shape; the source kernel fills an array for the five stage times (one
+launch per step) that every stage kernel reads.
 """
 import numpy as np
 import pytest
@@ -40,17 +44,27 @@ def stream():
     return torch.cuda.current_stream().cuda_stream
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+CASES = [("fp64", 0), ("mixed", 1), ("mixed", 3)]
+
+
+def solver(dg, mesh, p, precision, variant, mu):
+    s = dg.Solver(mesh, p, precision, stream=stream(), mu=mu)
+    if variant:
+        s.set_variant(variant)
+    s.set_source(dg.DG_SOURCE_VORTEX, SRC)
+    return s
+
+
+@pytest.mark.parametrize("precision,variant", CASES)
 @pytest.mark.parametrize("p", [2, 4])
-def test_rhs_with_vortex_source(dg, p, precision):
+def test_rhs_with_vortex_source(dg, p, precision, variant):
     mu = 2e-2
     mesh = dg_inputs.periodic_square(6)
     P = oracle.Problem(mesh, p, mu=mu, source=("vortex",) + SRC)
     t = 0.7
     U = to_kcn(dg_inputs.isentropic_vortex(P.x, P.y, t))
     ref = P.rhs(U, t)
-    s = dg.Solver(mesh, p, precision, stream=stream(), mu=mu)
-    s.set_source(dg.DG_SOURCE_VORTEX, SRC)
+    s = solver(dg, mesh, p, precision, variant, mu)
     s.set_state(U)
     got = s.rhs(t)
     check_rhs(P, U, got, precision, t, (0.0, 0.0), ref)
@@ -59,16 +73,15 @@ def test_rhs_with_vortex_source(dg, p, precision):
     assert np.abs(ref - P0.rhs(U, t)).max() > 1e3 * np.abs(got - ref).max()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_vortex_source_100_steps(dg, precision):
+@pytest.mark.parametrize("precision,variant", CASES)
+def test_vortex_source_100_steps(dg, precision, variant):
     mu = 1e-3
     mesh = dg_inputs.periodic_square(16)
     P = oracle.Problem(mesh, 2, mu=mu, source=("vortex",) + SRC)
     U0 = dg_inputs.perturb(to_kcn(dg_inputs.isentropic_vortex(P.x, P.y)), seed=0, amp=1e-3)
     dt, _ = P.dt(U0, 0.3)
     ref = P.run(U0, 0.0, dt, 100)
-    s = dg.Solver(mesh, 2, precision, stream=stream(), mu=mu)
-    s.set_source(dg.DG_SOURCE_VORTEX, SRC)
+    s = solver(dg, mesh, 2, precision, variant, mu)
     s.set_state(U0)
     s.steps(0.0, dt, 100)
     got = s.get_state()
@@ -90,13 +103,15 @@ def full_size():
     return _FULL
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_vortex_source_full_size_20_steps(dg, precision):
+@pytest.mark.parametrize("precision,variant", CASES)
+def test_vortex_source_full_size_20_steps(dg, precision, variant):
     f = full_size()
-    s = dg.Solver(f["mesh"], 4, precision, stream=stream(), mu=1e-3)
-    s.set_source(dg.DG_SOURCE_VORTEX, SRC)
+    s = solver(dg, f["mesh"], 4, precision, variant, 1e-3)
     s.set_state(f["U0"])
+    n0 = s.launches
     s.steps(0.0, f["dt"], 20)
+    # one source launch per step, then the five stages
+    assert s.launches - n0 == 20 * 6
     got = s.get_state()
     P, ref, U0 = f["P"], f["ref"], f["U0"]
     assert np.all(rel_l2(P, got - ref, ref) <= STATE_TOL[precision])
