@@ -151,9 +151,9 @@ stage_mixed2_kernel(StageParams sp, Phys<float> ph)
         tile_at(tile, k0, ne);
         if constexpr (BATCH) {
             const BatchCase &cs = sp.cases[sp.tiles[tile].z];
-            ph.mu = static_cast<float>(cs.mu);
-            ph.vw2 = static_cast<float>(cs.vb);
-            dtr = static_cast<float>(cs.dt);
+            ph.mu = cvt_d2f(cs.mu);           // integer conversions: no FP64-pipe work per tile
+            ph.vw2 = cvt_d2f(cs.vb);
+            dtr = cvt_d2f(cs.dt);
         }
         const int4 *cnb = sConn + buf * E;
         int4 *cnx = sConn + (buf ^ 1) * E;

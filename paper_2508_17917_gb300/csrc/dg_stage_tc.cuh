@@ -324,9 +324,9 @@ stage_tc_kernel(StageParams sp, Phys<float> ph)
             k0 = td.x;
             ne = td.y;
             const BatchCase &cs = sp.cases[td.z];
-            ph.mu = static_cast<float>(cs.mu);
-            ph.vw2 = static_cast<float>(cs.vb);
-            dtr = static_cast<float>(cs.dt);
+            ph.mu = cvt_d2f(cs.mu);           // integer conversions: no FP64-pipe work per tile
+            ph.vw2 = cvt_d2f(cs.vb);
+            dtr = cvt_d2f(cs.dt);
         }
         if (failed) continue;                    // a copy wait gave up: the flag is set
         if (lane < ne) sConn[lane] = sp.conn[k0 + lane];
