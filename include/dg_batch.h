@@ -83,11 +83,19 @@ int64_t dg_batch_kernel_launches(const dg_batch *b);
  * Drops captured graphs.  Errors: DG_EINVAL. */
 dg_status dg_batch_set_stage_variant(dg_batch *b, int variant);
 
-/* Fused steps for the batch: on != 0 replaces the five stage launches of
- * each degree group by one cooperative launch with grid barriers between the
- * stages (as dg_set_fused_steps; every barrier wait is bounded and a wait
- * that gives up makes dg_batch_run return DG_ETIMEOUT).  Drops captured
- * graphs.  Errors: DG_EINVAL, DG_ECUDA. */
+/* Fused steps for the batch (no counterpart in the paper, whose solver runs
+ * one case per MPI job).  on = 1 replaces the five stage launches of each
+ * degree group by one cooperative launch with grid barriers between the
+ * stages (as dg_set_fused_steps); on = 2 runs the five stages of every
+ * degree group in a single cooperative launch: each group takes a share of
+ * the grid (sized on the first step in proportion to the tuner's time of its
+ * tensor-core shape) and runs the tensor-core shape's fused body on it, with
+ * grid barriers among its own blocks only, so one persistent launch per step
+ * advances all cases through Algorithm 1's stages (Algorithm 3's force,
+ * time-step and Newmark launches stay around it).  Every barrier wait is
+ * bounded and a wait that gives up makes dg_batch_run return DG_ETIMEOUT.
+ * 0 returns to five launches per group.  Drops captured graphs.
+ * Errors: DG_EINVAL (on outside 0..2), DG_ECUDA. */
 dg_status dg_batch_set_fused_steps(dg_batch *b, int on);
 
 /* Fixed time steps: dt[ncases] (host, copied) replaces step 1's

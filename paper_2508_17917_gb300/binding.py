@@ -447,7 +447,8 @@ def dg_batch_stage_variant(b, i):
 
 
 def dg_batch_set_fused_steps(b, on):
-    _bcheck(lib().dg_batch_set_fused_steps(b, int(bool(on))), b)
+    """0 off, 1 (or True) one cooperative launch per degree group, 2 one for all groups."""
+    _bcheck(lib().dg_batch_set_fused_steps(b, int(on)), b)
 
 
 def dg_batch_set_fixed_dt(b, dt):
@@ -581,8 +582,9 @@ class BatchSolver:
         return dg_batch_stage_variant(self.b, i)
 
     def set_fused(self, on):
-        """One cooperative launch per degree group and step."""
-        dg_batch_set_fused_steps(self.b, on)
+        """Fused steps: 1 = one cooperative launch per degree group and step,
+        2 = one cooperative launch for all degree groups, 0 = off."""
+        dg_batch_set_fused_steps(self.b, int(on))
 
     def set_fixed_dt(self, dt):
         """Per-case fixed steps (None: back to the CFL bound)."""

@@ -41,9 +41,10 @@ struct Group {
     dg::LaunchShape shape3;          // tensor-core warp tiles (p <= 6)
     bool has_tc = false;
     int variant = 1;
+    float t_tc = 0.f;                // the tuner's time of the tensor-core shape (ms, 3 launches), 0 if not timed
     dg::LaunchShape fshape;          // fused steps: cooperative launch of the chosen shape
     int fshape_variant = 0;
-    DevBuf<unsigned> bar;            // fused steps: barrier counters of this group
+    DevBuf<unsigned> bar;            // fused steps: barrier words of this group (+ tile counters)
     DevBuf<double> K0a, K0b, K1, geo64, Dr64, Ds64, wface, fxy;
     DevBuf<float> geo32, ops32, P0a, P0b;
     DevBuf<float4> S0a, S0b;
@@ -84,6 +85,9 @@ struct dg_batch {
     int variant_req = 0;             // 0: tuned per degree group on the first run; 1, 2: forced
     bool tuned = false;
     bool fused = false;              // one cooperative launch per degree group and step
+    bool fused_all = false;          // ... or one cooperative launch for all degree groups
+    std::vector<unsigned> all_nblk;  // fused_all: blocks of each group (empty until sized)
+    size_t all_smem = 0;
     DevBuf<int> bar_err;
     unsigned bar_limit = 1u << 24;
     // graphs: [0] starts from buffers a, [1] from buffers b
@@ -196,6 +200,79 @@ dg_status enqueue_forces(dg_batch *b, double *hist = nullptr, int rows = 0)
     return DG_OK;
 }
 
+// The five stages of every degree group in one cooperative launch: each
+// group runs the fused tensor-core body on its own share of the blocks, with
+// grid barriers among those blocks only.  The first call sizes the shares in
+// proportion to the tuner's time of each group's tensor-core shape (or, if
+// the shapes were not timed, to its tiles times its nodes per element).
+dg_status enqueue_stages_all(dg_batch *b, const dg::Phys<float> &ph32, double sf)
+{
+    const int ng = static_cast<int>(b->groups.size());
+    std::vector<int> ps(ng);
+    std::vector<dg::StageParams> sps(ng);
+    for (int i = 0; i < ng; ++i) {
+        Group &g = b->groups[i];
+        if (!g.has_tc) return bfail(b, DG_EUNSUPPORTED, "one launch for all groups needs the tensor-core shape (p <= 6)");
+        ps[i] = g.p;
+        dg::StageParams &sp = sps[i];
+        const bool a = b->cur_is_a;
+        sp.K0in = a ? g.K0a.ptr : g.K0b.ptr;
+        sp.K0out = a ? g.K0b.ptr : g.K0a.ptr;
+        sp.K1 = g.K1.ptr;
+        sp.geo = g.geo32.ptr;
+        sp.conn = g.conn.ptr;
+        sp.ops = g.tcfrag.ptr;
+        sp.fmask = g.fmask.ptr;
+        sp.Sin = a ? g.S0a.ptr : g.S0b.ptr;
+        sp.Pin = a ? g.P0a.ptr : g.P0b.ptr;
+        sp.Sout = a ? g.S0b.ptr : g.S0a.ptr;
+        sp.Pout = a ? g.P0b.ptr : g.P0a.ptr;
+        sp.K = g.K;
+        sp.gm1 = b->prm.gamma - 1.0;
+        sp.sig_fac = sf;
+        sp.mode = dg::STAGE_UPDATE;
+        sp.first_stage = 1;
+        sp.cases = b->dcases.ptr;
+        sp.bar_err = b->bar_err.ptr;
+        sp.bar_limit = b->bar_limit;
+        sp.tiles = g.tiles3.ptr;
+        sp.ntiles = g.ntiles3;
+        for (int s = 0; s < 5; ++s) {
+            sp.A5[s] = dg::kRkA[s];
+            sp.B5[s] = dg::kRkB[s];
+        }
+        sp.bar = g.bar.ptr;          // [0, 1] barrier, [2 .. 6] tile counters of the five stages
+        B_CUDA(b, cudaMemsetAsync(g.bar.ptr, 0, 8 * sizeof(unsigned), b->stream));
+    }
+    if (b->all_nblk.size() != static_cast<size_t>(ng)) {
+        int cap = 0;
+        B_CUDA(b, dg::stage_tc_multi_capacity(ps.data(), ng, cap, b->all_smem));
+        std::vector<double> w(ng);
+        double wsum = 0.0;
+        for (int i = 0; i < ng; ++i) {
+            const Group &g = b->groups[i];
+            w[i] = g.t_tc > 0.f ? static_cast<double>(g.t_tc) : static_cast<double>(g.ntiles3) * g.ops.Np;
+            wsum += w[i];
+        }
+        b->all_nblk.assign(ng, 1u);
+        int left = cap - ng;
+        for (int i = 0; i < ng; ++i) {
+            // at most one block per four warp tiles: a block runs four warps
+            const long long most = (b->groups[i].ntiles3 + 3) / 4;
+            long long extra = static_cast<long long>(w[i] / wsum * (cap - ng));
+            if (extra > most - 1) extra = most - 1;
+            if (extra > left) extra = left;
+            if (extra < 0) extra = 0;
+            b->all_nblk[i] += static_cast<unsigned>(extra);
+            left -= static_cast<int>(extra);
+        }
+    }
+    B_CUDA(b, dg::launch_stage_tc_multi(ng, ps.data(), sps.data(), b->all_nblk.data(), b->all_smem, ph32,
+                                        b->stream));
+    b->launches += 1;
+    return DG_OK;
+}
+
 // one time step of every case (Algorithm 3), queued on the batch stream
 dg_status enqueue_step(dg_batch *b, double cfl, double *hist, int rows)
 {
@@ -226,6 +303,12 @@ dg_status enqueue_step(dg_batch *b, double cfl, double *hist, int rows)
     B_CUDA(b, dg::launch_batch_dt_newmark(b->lam.ptr, b->seg.ptr, b->dcases.ptr, n, cfl,
                                           b->use_fixed ? b->fixed_dt.ptr : nullptr, b->stream));
     b->launches += 1;
+    if (b->fused_all) {
+        dg_status st = enqueue_stages_all(b, ph32, sf);
+        if (st != DG_OK) return st;
+        b->cur_is_a = !b->cur_is_a;
+        return enqueue_forces(b, hist, rows);
+    }
     for (int s = 0; s < (b->fused ? 1 : 5); ++s) {
         for (auto &g : b->groups) {
             dg::StageParams sp{};
@@ -365,6 +448,7 @@ dg_status tune_groups(dg_batch *b)
             B_CUDA(b, cudaEventRecord(e1, b->stream));
             B_CUDA(b, cudaEventSynchronize(e1));
             B_CUDA(b, cudaEventElapsedTime(&ms, e0, e1));
+            if (v == 3) g.t_tc = ms;
             if (v == 1 || ms < best) {
                 best = ms;
                 g.variant = v;
@@ -648,14 +732,17 @@ dg_status dg_batch_set_fused_steps(dg_batch *b, int on)
 {
     if (!b) return DG_EINVAL;
     b->err.clear();
+    if (on < 0 || on > 2) return bfail(b, DG_EINVAL, "fused steps: 0 (off), 1 (per degree group) or 2 (all groups)");
     if (on) {
         for (auto &g : b->groups) {
             if (g.bar.ptr) continue;
-            B_CUDA(b, g.bar.alloc(2));
-            B_CUDA(b, cudaMemset(g.bar.ptr, 0, 2 * sizeof(unsigned)));
+            B_CUDA(b, g.bar.alloc(8));
+            B_CUDA(b, cudaMemset(g.bar.ptr, 0, 8 * sizeof(unsigned)));
         }
     }
     b->fused = on != 0;
+    b->fused_all = on == 2;
+    b->all_nblk.clear();
     b->drop_graphs();
     b->graph_cfl = 0.0;
     return DG_OK;
@@ -790,7 +877,8 @@ dg_status dg_batch_run(dg_batch *b, double cfl, int nsteps, int use_graph, doubl
                 // per group, wall forces of all groups, force sums (+ history)
                 bool walls = false;
                 for (auto &g : b->groups) walls |= g.nwall > 0;
-                int64_t per = 1 + 1 + static_cast<int64_t>(b->groups.size()) * (b->fused ? 1 : 5) + (walls ? 1 : 0) + 1;
+                const int64_t stages = b->fused_all ? 1 : static_cast<int64_t>(b->groups.size()) * (b->fused ? 1 : 5);
+                int64_t per = 1 + 1 + stages + (walls ? 1 : 0) + 1;
                 b->graph_launches = per;
             }
             B_CUDA(b, cudaGraphLaunch(b->graph[which], b->stream));

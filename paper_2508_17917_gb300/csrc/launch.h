@@ -87,6 +87,12 @@ int stage_tile_elems_tc();
 // fused: five stages per cooperative launch with grid barriers
 // theta: the SIP / NIPG variant (single mesh, stage-wise launches only)
 cudaError_t stage_shape_tc(int p, long long units, bool batch, bool fused, LaunchShape &out, bool theta = false);
+// the fused batch body of every degree group in one cooperative launch:
+// blocks that fit the GPU at once and the shared memory per block (the
+// largest group's layout), then the launch with nblk[g] blocks for group g
+cudaError_t stage_tc_multi_capacity(const int *ps, int ngroups, int &blocks, size_t &smem);
+cudaError_t launch_stage_tc_multi(int ngroups, const int *ps, const StageParams *sps, const unsigned *nblk,
+                                  size_t smem, const Phys<float> &ph, cudaStream_t st);
 cudaError_t launch_stage_tc(int p, bool batch, bool fused, const LaunchShape &ls, const StageParams &sp,
                             const Phys<float> &ph, cudaStream_t st);
 // Dr, Ds [Np][Np], LIFT [Np][NF], Wr, Ws [Np][Np] (FP64, row-major) -> the kernel's

@@ -89,6 +89,54 @@ cudaError_t launch_tc_any(bool batch, bool fused, const LaunchShape &ls, const S
     return fused ? launch_tc_p<P, false, true>(ls, sp, ph, st) : launch_tc_p<P, false, false>(ls, sp, ph, st);
 }
 
+// The degree groups of a batch in one launch: group g owns blocks
+// [first[g], first[g] + nblk[g]) and its own stage parameters (buffers, tile
+// table, barrier words); the groups never wait on one another.
+constexpr int kMaxMultiGroups = 8;
+struct TcMulti {
+    StageParams sp[kMaxMultiGroups];
+    int p[kMaxMultiGroups];
+    unsigned first[kMaxMultiGroups], nblk[kMaxMultiGroups];
+    int ngroups;
+};
+
+// Four blocks per SM (128 registers): the p = 5, 6 bodies need them, and one
+// kernel has one register budget.
+__global__ void __launch_bounds__(128, 4) stage_tc_multi_kernel(const __grid_constant__ TcMulti m, Phys<float> ph)
+{
+    int g = 0;
+    while (g + 1 < m.ngroups && blockIdx.x >= m.first[g + 1]) ++g;
+    const unsigned bid = blockIdx.x - m.first[g], nb = m.nblk[g];
+    switch (m.p[g]) {
+    case 1: stage_tc_group_body<1, true, true, false>(m.sp[g], ph, bid, nb); break;
+    case 2: stage_tc_group_body<2, true, true, false>(m.sp[g], ph, bid, nb); break;
+    case 3: stage_tc_group_body<3, true, true, false>(m.sp[g], ph, bid, nb); break;
+    case 4: stage_tc_group_body<4, true, true, false>(m.sp[g], ph, bid, nb); break;
+    case 5: stage_tc_group_body<5, true, true, false>(m.sp[g], ph, bid, nb); break;
+    case 6: stage_tc_group_body<6, true, true, false>(m.sp[g], ph, bid, nb); break;
+    default: break;
+    }
+}
+
+template <int P>
+size_t tc_group_smem()
+{
+    return TcLayout<P, false>::bytes;
+}
+
+size_t tc_group_smem_any(int p)
+{
+    switch (p) {
+    case 1: return tc_group_smem<1>();
+    case 2: return tc_group_smem<2>();
+    case 3: return tc_group_smem<3>();
+    case 4: return tc_group_smem<4>();
+    case 5: return tc_group_smem<5>();
+    case 6: return tc_group_smem<6>();
+    default: return 0;
+    }
+}
+
 // x rounded to TF32 (10 explicit mantissa bits), ties away from zero; the
 // operators are finite and far from the FP32 overflow threshold
 float tf32_round(float x)
@@ -117,6 +165,57 @@ cudaError_t stage_shape_tc(int p, long long units, bool batch, bool fused, Launc
     case 6: return shape_tc_any<6>(units, batch, fused, theta, out);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t stage_tc_multi_capacity(const int *ps, int ngroups, int &blocks, size_t &smem)
+{
+    if (ngroups < 1 || ngroups > kMaxMultiGroups) return cudaErrorInvalidValue;
+    smem = 0;
+    for (int g = 0; g < ngroups; ++g) {
+        const size_t b = tc_group_smem_any(ps[g]);
+        if (b == 0) return cudaErrorInvalidValue;
+        smem = b > smem ? b : smem;
+    }
+    cudaError_t e = cudaFuncSetAttribute(stage_tc_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(stage_tc_multi_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_tc_multi_kernel, 128, smem);
+    if (e != cudaSuccess) return e;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    blocks = per_sm * sms;
+    return blocks >= ngroups ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
+cudaError_t launch_stage_tc_multi(int ngroups, const int *ps, const StageParams *sps, const unsigned *nblk,
+                                  size_t smem, const Phys<float> &ph, cudaStream_t st)
+{
+    if (ngroups < 1 || ngroups > kMaxMultiGroups) return cudaErrorInvalidValue;
+    TcMulti m{};
+    m.ngroups = ngroups;
+    unsigned total = 0;
+    for (int g = 0; g < ngroups; ++g) {
+        if (nblk[g] < 1) return cudaErrorInvalidValue;
+        m.sp[g] = sps[g];
+        m.p[g] = ps[g];
+        m.first[g] = total;
+        m.nblk[g] = nblk[g];
+        total += nblk[g];
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(total);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, stage_tc_multi_kernel, m, ph);
 }
 
 cudaError_t launch_stage_tc(int p, bool batch, bool fused, const LaunchShape &ls, const StageParams &sp,

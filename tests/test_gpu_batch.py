@@ -88,9 +88,11 @@ def rel_err(got, ref):
 
 
 # (launch mode, tile shape; 0 = tuned); "fused": one cooperative launch per
-# degree group and step, replayed from the graph
+# degree group and step, "all": one cooperative launch for all degree groups
+# (the tensor-core shape's fused body on each group's share of the grid,
+# shares sized by the tuner's timings when tuned), replayed from the graph
 RUNS = [("graph", 1), ("plain", 1), ("graph", 2), ("graph", 3), ("graph", 0), ("fused", 1), ("fused", 2),
-        ("fused", 3)]
+        ("fused", 3), ("all", 0), ("all", 3)]
 
 
 @pytest.fixture(scope="module")
@@ -102,7 +104,7 @@ def small_run(dg):
     for mode, variant in RUNS:
         b = dg.BatchSolver(cases, **FAR)
         b.set_variant(variant)
-        b.set_fused(mode == "fused")
+        b.set_fused({"fused": 1, "all": 2}.get(mode, 0))
         states = []
         for i in range(len(cases)):
             x, y = b.node_coords(i)
@@ -128,7 +130,7 @@ def test_batch_graph_replay_is_bit_identical(small_run):
 
 
 @pytest.mark.parametrize("run", [("graph", 1), ("graph", 2), ("graph", 3), ("graph", 0), ("fused", 2),
-                                 ("fused", 3)])
+                                 ("fused", 3), ("all", 0)])
 @pytest.mark.parametrize("i", range(len(SMALL)))
 def test_batch_case_matches_oracle_loop(small_run, i, run):
     cases, states, nsteps, res = small_run
@@ -164,6 +166,18 @@ def test_batch_fused_matches_five_launches(small_run, variant):
     assert np.abs(hf - hg).max() <= 1e-9 * np.abs(hg).max()
 
 
+@pytest.mark.parametrize("run", [("all", 0), ("all", 3)])
+def test_batch_single_launch_matches_five_launches(small_run, run):
+    """One launch for all degree groups gives the tensor-core shape's result
+    up to the last bit of a separately compiled kernel."""
+    cases, states, nsteps, res = small_run
+    hg, Ug, _, _, _ = res[("graph", 3)]
+    ha, Ua, _, _, _ = res[run]
+    for a, b in zip(Ug, Ua):
+        assert np.abs(a - b).max() <= 1e-9 * np.abs(a).max()
+    assert np.abs(ha - hg).max() <= 1e-9 * np.abs(hg).max()
+
+
 def test_batch_launch_count(small_run):
     cases, states, nsteps, res = small_run
     groups = len({c["p"] for c in cases})
@@ -173,7 +187,7 @@ def test_batch_launch_count(small_run):
     # groups, force sums with the history record; the tuned run adds five
     # residual-only launches per shape (three) and group
     for run in RUNS:
-        stage = groups if run[0] == "fused" else 5 * groups
+        stage = {"fused": groups, "all": 1}.get(run[0], 5 * groups)
         per_step = 1 + 1 + stage + 1 + 1
         launches = res[run][3]
         tune = 15 * groups if run[1] == 0 else 0
