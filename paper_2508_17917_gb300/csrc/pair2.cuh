@@ -3,7 +3,9 @@
 // 64-bit register pair).  The formula of penalty_norm in dg_device.cuh, term
 // by term; where a product and a sum are contracted into one fused
 // multiply-add may differ, so the results agree to FP32 rounding, not bit for
-// bit.  The square roots, reciprocals, arccosine and cosine stay scalar.
+// bit.  The square roots and reciprocals stay scalar; the trigonometric step
+// of the eigenvalue, cos(acos(r) / 3), is a polynomial evaluated in pairs
+// (2 % faster per step at p = 4 than the arccosine and cosine).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -39,11 +41,22 @@ __device__ __forceinline__ pf2 sym3_max_eig2(pf2 a11, pf2 a12, pf2 a13, pf2 a22,
     const pf2 m1 = b22 * b33 - c23 * c23, m2 = c12 * b33 - c23 * c13, m3 = c12 * c23 - b22 * c13;
     const pf2 det = fma2(c13, m3, b11 * m1 - c12 * m2);
     const pf2 r = det * sp(0.5f);
-    const float rx = fminf(fmaxf(r.v.x, -1.0f), 1.0f), ry = fminf(fmaxf(r.v.y, -1.0f), 1.0f);
-    const float lx = q.v.x + 2.0f * ppx * cosf(acosf(rx) * (1.0f / 3.0f));
-    const float ly = q.v.y + 2.0f * ppy * cosf(acosf(ry) * (1.0f / 3.0f));
+    // cos(acos(r) / 3) = cos(2/3 acos(w)) with w = cos(acos(r) / 2) =
+    // sqrt((1 + r) / 2) in [0, 1], where it is analytic: a polynomial of
+    // degree 7 in w, interpolated at the 8 Chebyshev nodes of [0, 1]
+    // (|error| < 3e-8; 1.2e-7 with FP32 Horner steps)
+    const pf2 w2 = fma2(sp(0.5f), r, sp(0.5f));
+    const pf2 w = mk(sqrtf(fminf(fmaxf(w2.v.x, 0.0f), 1.0f)), sqrtf(fminf(fmaxf(w2.v.y, 0.0f), 1.0f)));
+    pf2 c = fma2(sp(0.0011276363f), w, sp(-0.0060893456f));
+    c = fma2(c, w, sp(0.016047280f));
+    c = fma2(c, w, sp(-0.030235397f));
+    c = fma2(c, w, sp(0.052841410f));
+    c = fma2(c, w, sp(-0.11103851f));
+    c = fma2(c, w, sp(0.57734692f));
+    c = fma2(c, w, sp(0.5f));
+    const pf2 l = fma2(mk(2.0f * ppx, 2.0f * ppy), c, q);
     // a matrix with p2 = 0 is a multiple of the identity
-    return mk(p2.v.x > 0.0f ? lx : q.v.x, p2.v.y > 0.0f ? ly : q.v.y);
+    return mk(p2.v.x > 0.0f ? l.v.x : q.v.x, p2.v.y > 0.0f ? l.v.y : q.v.y);
 }
 
 // penalty_norm of two states (rho, v1, v2, e) with one normal
